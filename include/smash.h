@@ -1,0 +1,158 @@
+/*
+ * smash.h -- C ABI of a GB300 (sm_103a) row-wise hash SpGEMM library.
+ *
+ * Operation: C = A * B for sparse A (m x k) and B (k x n) in CSR, computed
+ * row by row (Eq. row_wise: C[i,:] = sum_{k in A_i} A[i,k] * B[k,:]) with the
+ * partial products of each row merged as they are produced in an
+ * open-addressing hash table (atomic compare-and-swap on the column tag,
+ * atomic add on the value), as in the "Hashing Phase" of SMASH Version 1 and
+ * the low-order-bit hashing of Version 2.
+ *
+ * Conventions shared by every call:
+ *  - All matrix arrays are DEVICE pointers on the handle's device:
+ *    row_ptr int64[rows+1], col_idx int32[nnz], val (float or double)[nnz].
+ *  - Input rows may hold unsorted and duplicate column indices; duplicates
+ *    are separate terms of the sum. Output rows are sorted ascending with
+ *    unique columns. A value that cancels to zero is kept as a stored entry:
+ *    the structure of C is every (i, j) reached by at least one product.
+ *  - rows == 0 and nnz == 0 are legal. A.cols must equal B.rows.
+ *  - Limits: rows, cols < 2^31; every row of B holds fewer than 2^21
+ *    entries. Violations, out-of-range indices and malformed row pointers are
+ *    detected by the kernels' bounds checks and reported as
+ *    SMASH_ERR_INVALID_ARG; no out-of-range access is made.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - No C++ exception crosses this interface; every call returns a status.
+ *  - The library never frees memory it did not allocate. Scratch memory is
+ *    owned by the handle (grown on demand through the handle's allocator).
+ *  - A handle is not thread-safe: one host thread per handle at a time.
+ */
+#ifndef SMASH_H
+#define SMASH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+    SMASH_OK = 0,
+    SMASH_ERR_INVALID_ARG = 1,     /* null pointer, negative size, bad index in the data */
+    SMASH_ERR_SHAPE_MISMATCH = 2,  /* A.cols != B.rows, or C's shape is not A.rows x B.cols */
+    SMASH_ERR_UNSUPPORTED = 3,     /* dtype or size outside the stated limits */
+    SMASH_ERR_ALLOC = 4,           /* the allocator returned NULL */
+    SMASH_ERR_CUDA = 5,            /* a CUDA runtime call failed */
+    SMASH_ERR_TIMEOUT = 6,         /* a bounded in-kernel wait gave up */
+    SMASH_ERR_INTERNAL = 7         /* an internal consistency check failed */
+};
+
+typedef enum { SMASH_F32 = 0, SMASH_F64 = 1 } smash_dtype;
+
+/* CSR matrix view. The library reads (A, B) or fills (C) the arrays. */
+typedef struct {
+    int64_t rows;
+    int64_t cols;
+    int64_t nnz;
+    int64_t *row_ptr; /* device, rows+1 entries, row_ptr[0] = 0, row_ptr[rows] = nnz */
+    int32_t *col_idx; /* device, nnz entries */
+    void *val;        /* device, nnz entries of the call's dtype (may be NULL in symbolic calls) */
+} smash_csr;
+
+/* Tuning parameters. None of them changes the result, only the speed.
+ * smash_default_params() fills the defaults; the autotuner overwrites them. */
+typedef struct {
+    int32_t hash_kind;      /* 0: low-order bits j & (T-1) (Version 2, default);
+                               1: multiplicative (Fibonacci) hashing;
+                               2: high-order bits j >> shift (Version 1, order preserving) */
+    float max_load;         /* table sized to next_pow2(bound / max_load) slots; (0.05, 0.95]; default 0.5 */
+    int32_t sym_max_tbits;  /* largest shared-memory symbolic table, log2 slots; [5, 15]; default 15 */
+    int32_t num_max_tbits;  /* largest shared-memory numeric table, log2 slots; [5, 14]; default 14 */
+    int32_t group_shift;    /* threads per row = clamp(T >> group_shift, 32, 1024); [0, 10]; default 3 */
+    int32_t dense_ratio;    /* a row whose bound b satisfies b * dense_ratio >= cols(B) uses the dense
+                               accumulator (the paper's "dense row"); 0 disables; default 4 */
+    int32_t bitmap_ratio;   /* numeric write-out ranks by a column bitmap when cols(B)/32 <=
+                               bitmap_ratio * nnz(row); 0 disables; default 4 */
+    int32_t spill_blocks_per_sm; /* resident blocks per SM of the spill and dense kernels; default 1 */
+    int32_t reserved[8];
+} smash_params;
+
+/* Per-call statistics (the last symbolic or numeric call of the handle). */
+typedef struct {
+    int64_t rows_per_bin[16]; /* 0: empty rows; 1..12: shared-memory tables of 2^(bin+4) slots;
+                                 13: dense accumulator; 14: global-memory hash (spill) */
+    int64_t products;         /* sum over rows of the product count flop_i (symbolic calls) */
+    int64_t max_row_products;
+    int64_t c_nnz;
+} smash_stats;
+
+typedef struct smash_handle smash_handle;
+
+/* Device allocator: alloc(bytes, ctx) returns a device pointer or NULL;
+ * free(ptr, ctx) releases it. Default: cudaMalloc / cudaFree. */
+typedef void *(*smash_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*smash_free_fn)(void *ptr, void *ctx);
+
+/* Fill *p with the default parameters. */
+int smash_default_params(smash_params *p);
+
+/* Create a handle bound to CUDA device `device`. params may be NULL (defaults).
+ * Writes the handle to *out. */
+int smash_create(smash_handle **out, int device, const smash_params *params);
+
+/* Destroy the handle and release its scratch memory (synchronises the device). */
+int smash_destroy(smash_handle *h);
+
+/* Replace / read the tuning parameters. Out-of-range values: SMASH_ERR_INVALID_ARG. */
+int smash_set_params(smash_handle *h, const smash_params *params);
+int smash_get_params(const smash_handle *h, smash_params *params);
+
+/* Route the handle's scratch allocations through (alloc, free, ctx). Frees
+ * the current scratch first (synchronising the device). */
+int smash_set_allocator(smash_handle *h, smash_alloc_fn alloc, smash_free_fn free_fn, void *ctx);
+
+/*
+ * Symbolic phase: the number of distinct columns of every row of C = A*B,
+ * and C's row pointer. This is the "memory required to allocate the output"
+ * count of the Window Distribution Phase, computed exactly with key-only
+ * hash tables (Hashing Phase without values).
+ *   A, B:       inputs (val unused, may be NULL).
+ *   c_row_ptr:  device int64[A.rows+1], caller-allocated; receives the
+ *               exclusive prefix sum of the row counts (c_row_ptr[0] = 0).
+ *   c_nnz:      host int64*, receives nnz(C).
+ * Synchronises `stream` before returning.
+ */
+int spgemm_symbolic(smash_handle *h, const smash_csr *A, const smash_csr *B, int64_t *c_row_ptr,
+                    int64_t *c_nnz, void *stream);
+
+/*
+ * Numeric phase: fills C.col_idx and C.val of C = A*B (Hashing Phase with
+ * values, then the Write-back Phase: each row's table is compacted, sorted by
+ * column and streamed to C).
+ *   C: C.rows = A.rows, C.cols = B.cols, C.row_ptr = the symbolic phase's
+ *      output, C.nnz = its c_nnz, C.col_idx / C.val caller-allocated device
+ *      arrays of C.nnz entries.
+ *   dtype: element type of A.val, B.val and C.val.
+ * Synchronises `stream` once, after binning the rows, to size its launches.
+ * Faults detected by the kernels (bad indices, a row count that does not
+ * match C.row_ptr) are returned by the next smash_check() call.
+ */
+int spgemm_numeric(smash_handle *h, const smash_csr *A, const smash_csr *B, smash_dtype dtype,
+                   smash_csr *C, void *stream);
+
+/* Synchronise `stream` and return the status recorded by the kernels of the
+ * handle's previous calls (then clear it). */
+int smash_check(smash_handle *h, void *stream);
+
+/* Statistics of the handle's last symbolic or numeric call. */
+int smash_get_stats(const smash_handle *h, smash_stats *out);
+
+/* Human-readable name of a status code (static string). */
+const char *smash_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMASH_H */

@@ -1,0 +1,421 @@
+// Device-side building blocks shared by the SpGEMM kernels (sm_103a).
+//
+//  * warp / group scans and reductions; a "group" is GS consecutive threads of
+//    a block that work on one row (GS = 32: a warp; GS = NT: the whole block;
+//    otherwise a named barrier per group);
+//  * the hash slot functions (Eq. hashing and the low-order-bit variant of
+//    SMASH Version 2);
+//  * product enumeration: every product a_ik * b_kj of one row of A, handed
+//    out to the threads of a group so that consecutive lanes read consecutive
+//    entries of B (coalesced), whatever the lengths of the rows of B.
+//  * bounds checks on every index read from the inputs, recorded in an error
+//    word instead of faulting.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace smash {
+
+constexpr int kEmpty = -1;             // tag of an unused slot (Algorithm SETUP's EMPTY = -1)
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxBRow = 1 << 21;      // longest supported row of B
+
+// Error word indices.
+enum : int {
+    kErrBadIndex = 0,      // column index out of range
+    kErrBadRowPtr = 1,     // row pointer not monotone / out of range
+    kErrBRowTooLong = 2,   // a row of B with >= 2^21 entries
+    kErrTableFull = 3,     // a hash table ran out of slots (internal)
+    kErrCountMismatch = 4, // numeric row count differs from C.row_ptr
+    kErrTimeout = 5,
+    kNumErr = 8
+};
+
+// Bins. 0: empty rows; 1..12: shared-memory tables with 2^(bin+4) slots;
+// 13: dense accumulator; 14: global-memory hash.
+constexpr int kMinTBits = 5;
+constexpr int kMaxTBits = 16;
+constexpr int kBinEmpty = 0;
+constexpr int kBinDense = 13;
+constexpr int kBinSpill = 14;
+constexpr int kNumBins = 15;
+__host__ __device__ constexpr int bin_of_tbits(int tbits) { return 1 + tbits - kMinTBits; }
+__host__ __device__ constexpr int tbits_of_bin(int bin) { return bin - 1 + kMinTBits; }
+
+__device__ __forceinline__ void raise_err(int *err, int code) {
+    if (err) atomicOr(err + code, 1);
+}
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(kFull, v, o);
+        if (lane_id() >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ long long warp_incl_scan64(long long v) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long t = __shfl_up_sync(kFull, v, o);
+        if (lane_id() >= o) v += t;
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        T t = __shfl_xor_sync(kFull, v, o);
+        v = t > v ? t : v;
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_min(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        T t = __shfl_xor_sync(kFull, v, o);
+        v = t < v ? t : v;
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Groups of GS threads inside a block of NT threads.
+template <int GS, int NT>
+struct Group {
+    static_assert(GS % 32 == 0 && NT % GS == 0 && GS <= NT && NT <= 1024, "group shape");
+    static_assert(NT / GS <= 15 || GS == 32, "named barriers: at most 15 groups");
+    static constexpr int kWarps = GS / 32;
+    static constexpr int kGroups = NT / GS;
+
+    __device__ __forceinline__ static int gid() { return threadIdx.x / GS; }
+    __device__ __forceinline__ static int tid() { return threadIdx.x % GS; }
+    __device__ __forceinline__ static int wid() { return (threadIdx.x % GS) >> 5; }
+
+    __device__ __forceinline__ static void sync() {
+        if constexpr (GS == 32) {
+            __syncwarp();
+        } else if constexpr (GS == NT) {
+            __syncthreads();
+        } else {
+            asm volatile("bar.sync %0, %1;" ::"r"(gid() + 1), "n"(GS) : "memory");
+        }
+    }
+
+    // Exclusive scan of v over the group; *total receives the sum.
+    // scratch: kWarps ints private to the group (unused for GS = 32).
+    template <typename T>
+    __device__ __forceinline__ static T excl_scan(T v, T *scratch, T *total) {
+        T incl;
+        if constexpr (sizeof(T) == 8) incl = (T)warp_incl_scan64((long long)v);
+        else incl = (T)warp_incl_scan((int)v);
+        if constexpr (GS == 32) {
+            *total = __shfl_sync(kFull, incl, 31);
+            return incl - v;
+        } else {
+            if (lane_id() == 31) scratch[wid()] = incl;
+            sync();
+            T off = 0, tot = 0;
+            const int w = wid();
+#pragma unroll 4
+            for (int i = 0; i < kWarps; ++i) {
+                T x = scratch[i];
+                if (i < w) off += x;
+                tot += x;
+            }
+            *total = tot;
+            sync();
+            return off + incl - v;
+        }
+    }
+
+    template <typename T>
+    __device__ __forceinline__ static T sum(T v, T *scratch) {
+        T tot;
+        excl_scan<T>(v, scratch, &tot);
+        return tot;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Hash slot of column j in a table of 2^tbits slots.
+struct HashCfg {
+    int kind;     // 0 low bits, 1 multiplicative, 2 high bits
+    int colbits;  // ceil(log2(cols of B)), for the order-preserving high-bit hash
+};
+
+__device__ __forceinline__ uint32_t hash_slot(int j, int tbits, HashCfg hc) {
+    if (hc.kind == 0) return (uint32_t)j & ((1u << tbits) - 1u);
+    if (hc.kind == 1) return ((uint32_t)j * 2654435769u) >> (32 - tbits);
+    int sh = hc.colbits - tbits;
+    return sh > 0 ? ((uint32_t)j >> sh) : (uint32_t)j;
+}
+
+// ---------------------------------------------------------------------------
+// Inputs of one product C = A*B as the kernels see them.
+template <typename V>
+struct Operands {
+    const int64_t *a_rp;
+    const int32_t *a_ci;
+    const V *a_val;
+    const int64_t *b_rp;
+    const int32_t *b_ci;
+    const V *b_val;
+    int64_t a_nnz;
+    int64_t b_nnz;
+    int32_t b_rows;
+    int32_t ncols;
+};
+
+// Row range of A, checked.
+template <typename V>
+__device__ __forceinline__ bool a_row_range(const Operands<V> &op, int64_t i, int64_t &ab,
+                                            int64_t &ae, int *err) {
+    ab = __ldg(op.a_rp + i);
+    ae = __ldg(op.a_rp + i + 1);
+    if (ab < 0 || ae < ab || ae > op.a_nnz) {
+        raise_err(err, kErrBadRowPtr);
+        ab = ae = 0;
+        return false;
+    }
+    return true;
+}
+
+// Loads the A entry e and the range of the row of B it selects (checked).
+template <typename V, bool NUM>
+__device__ __forceinline__ void load_a_entry(const Operands<V> &op, int64_t e, int &len,
+                                             int64_t &bs, V &av, int *err) {
+    len = 0;
+    bs = 0;
+    av = V(0);
+    int k = __ldg(op.a_ci + e);
+    if ((unsigned)k < (unsigned)op.b_rows) {
+        int64_t s = __ldg(op.b_rp + k), t = __ldg(op.b_rp + k + 1);
+        if (s >= 0 && t >= s && t <= op.b_nnz) {
+            if (t - s < kMaxBRow) {
+                bs = s;
+                len = (int)(t - s);
+            } else {
+                raise_err(err, kErrBRowTooLong);
+            }
+        } else {
+            raise_err(err, kErrBadRowPtr);
+        }
+    } else {
+        raise_err(err, kErrBadIndex);
+    }
+    if constexpr (NUM) av = op.a_val[e];
+}
+
+template <typename V>
+__device__ __forceinline__ V shfl_v(V v, int src) {
+    return __shfl_sync(kFull, v, src);
+}
+
+// Every product of A entries [ab, ae) with their rows of B, enumerated by one
+// warp: lane l takes products l, l+32, ... of each batch of 32 A entries.
+// f(j, v) is called for each product (v = a_ik * b_kj; 0 when !NUM).
+template <typename V, bool NUM, typename F>
+__device__ __forceinline__ void warp_products(const Operands<V> &op, int64_t ab, int64_t ae,
+                                              int *err, F &&f) {
+    const int lane = lane_id();
+    for (int64_t base = ab; base < ae; base += 32) {
+        int len = 0;
+        int64_t bs = 0;
+        V av = V(0);
+        if (base + lane < ae) load_a_entry<V, NUM>(op, base + lane, len, bs, av, err);
+        const int incl = warp_incl_scan(len);
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int64_t start = bs - (incl - len);   // product p of this entry reads b[start + p]
+        for (int p0 = 0; p0 < total; p0 += 32) {
+            const int p = p0 + lane;
+            int o = 0;
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                int c = __shfl_sync(kFull, incl, o + s - 1);
+                if (c <= p) o += s;
+            }
+            const int64_t st = __shfl_sync(kFull, start, o);
+            V a = V(0);
+            if constexpr (NUM) a = shfl_v(av, o);
+            if (p < total) {
+                const int64_t idx = st + p;
+                const int j = __ldg(op.b_ci + idx);
+                if ((unsigned)j < (unsigned)op.ncols) {
+                    if constexpr (NUM) f(j, a * __ldg(op.b_val + idx));
+                    else f(j, V(0));
+                } else {
+                    raise_err(err, kErrBadIndex);
+                }
+            }
+        }
+    }
+}
+
+// Shared scratch of a group for group_products (GS entries each).
+template <typename V>
+struct ProdScratch {
+    int *incl;       // [GS]
+    int64_t *start;  // [GS]
+    V *av;           // [GS]
+    int *red;        // [GS/32] scan scratch
+    int64_t *red64;  // [GS/32]
+};
+
+template <typename V, int GS>
+__host__ __device__ constexpr size_t prod_scratch_bytes() {
+    return (size_t)GS * (4 + 8 + sizeof(V)) + (GS / 32) * (4 + 8) + 16;
+}
+
+// The scratch starts at the first 16-byte boundary at or after p; the size
+// from prod_scratch_bytes() includes the 16 bytes this may skip.
+template <typename V, int GS>
+__device__ __forceinline__ ProdScratch<V> carve_prod_scratch(unsigned char *p) {
+    p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    ProdScratch<V> s;
+    s.start = (int64_t *)p;
+    p += GS * 8;
+    s.red64 = (int64_t *)p;
+    p += (GS / 32) * 8;
+    s.av = (V *)p;
+    p += GS * sizeof(V);
+    s.incl = (int *)p;
+    p += GS * 4;
+    s.red = (int *)p;
+    return s;
+}
+
+// Every product of A entries [ab, ae), enumerated by a group of GS >= 64
+// threads: batches of GS A entries are staged in shared memory (entries with
+// an empty row of B dropped), then warp w takes products w*32 .. w*32+31,
+// w*32+GS .., each lane finding its entry by a binary search over a window of
+// 32 staged prefix sums.
+template <typename V, bool NUM, int GS, int NT, typename F>
+__device__ __forceinline__ void group_products(const Operands<V> &op, int64_t ab, int64_t ae,
+                                               const ProdScratch<V> &sc, int *err, F &&f) {
+    using G = Group<GS, NT>;
+    const int t = G::tid();
+    const int lane = lane_id();
+    for (int64_t base = ab; base < ae; base += GS) {
+        int len = 0;
+        int64_t bs = 0;
+        V av = V(0);
+        if (base + t < ae) load_a_entry<V, NUM>(op, base + t, len, bs, av, err);
+        const int flag = len > 0 ? 1 : 0;
+        int nf, total;
+        const int cidx = G::template excl_scan<int>(flag, sc.red, &nf);
+        const int excl = G::template excl_scan<int>(len, sc.red, &total);
+        if (flag) {
+            sc.incl[cidx] = excl + len;
+            sc.start[cidx] = bs - excl;
+            if constexpr (NUM) sc.av[cidx] = av;
+        }
+        G::sync();
+        for (int pb = G::wid() * 32; pb < total; pb += GS) {
+            // first staged entry whose inclusive prefix exceeds pb
+            int lo = 0, hi = nf;
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (sc.incl[mid] <= pb) lo = mid + 1;
+                else hi = mid;
+            }
+            const int c0 = lo;
+            const int wi = min(c0 + lane, nf - 1);
+            const int w_incl = sc.incl[wi];
+            const int p = pb + lane;
+            int o = 0;
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                int c = __shfl_sync(kFull, w_incl, o + s - 1);
+                if (c <= p) o += s;
+            }
+            if (p < total) {
+                const int ci = c0 + o;
+                const int64_t idx = sc.start[ci] + p;
+                const int j = __ldg(op.b_ci + idx);
+                if ((unsigned)j < (unsigned)op.ncols) {
+                    if constexpr (NUM) f(j, sc.av[ci] * __ldg(op.b_val + idx));
+                    else f(j, V(0));
+                } else {
+                    raise_err(err, kErrBadIndex);
+                }
+            }
+        }
+        G::sync();
+    }
+}
+
+// Dispatch: warp or group enumeration.
+template <typename V, bool NUM, int GS, int NT, typename F>
+__device__ __forceinline__ void row_products(const Operands<V> &op, int64_t ab, int64_t ae,
+                                             const ProdScratch<V> &sc, int *err, F &&f) {
+    if constexpr (GS == 32) warp_products<V, NUM>(op, ab, ae, err, f);
+    else group_products<V, NUM, GS, NT>(op, ab, ae, sc, err, f);
+}
+
+// ---------------------------------------------------------------------------
+// Hash table operations. keys: int tags (kEmpty = free); probing is linear,
+// +1 slot per collision with wrap-around (Hashing Phase, collision
+// resolution). Returns the slot, or -1 if the table is full.
+template <bool GLOBAL>
+__device__ __forceinline__ int ld_key(const int *k) {
+    if constexpr (GLOBAL) {
+        int v;
+        asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(k) : "memory");
+        return v;
+    } else {
+        return *(volatile const int *)k;
+    }
+}
+
+template <bool GLOBAL>
+__device__ __forceinline__ int hash_find_or_insert(int *keys, int tbits, HashCfg hc, int j,
+                                                   bool &inserted) {
+    const uint32_t mask = (1u << tbits) - 1u;
+    uint32_t h = hash_slot(j, tbits, hc) & mask;
+    inserted = false;
+    for (uint32_t n = 0; n <= mask; ++n) {
+        int k = ld_key<GLOBAL>(keys + h);
+        if (k == j) return (int)h;
+        if (k == kEmpty) {
+            int old = atomicCAS(keys + h, kEmpty, j);
+            if (old == kEmpty) {
+                inserted = true;
+                return (int)h;
+            }
+            if (old == j) return (int)h;
+        }
+        h = (h + 1u) & mask;
+    }
+    return -1;
+}
+
+// Ceil-power-of-two table size for `bound` entries at load `inv_load`.
+__host__ __device__ inline int table_bits(int64_t bound, float inv_load) {
+    double want = (double)bound * (double)inv_load;
+    int b = kMinTBits;
+    while (b < 40 && (double)(1ll << b) < want) ++b;
+    return b;
+}
+
+}  // namespace smash

@@ -1,0 +1,638 @@
+// Numeric phase: values of C = A*B, rows sorted by column.
+//
+// Hashing Phase with values: each product a_ik*b_kj is merged into the row's
+// table as it is produced: compare-and-swap claims the tag's slot (EMPTY = -1,
+// +1 linear probing), an atomic add accumulates the value (the "atomic fetch
+// and add" merge). Write-back Phase: the occupied slots are gathered, ordered
+// by column and streamed to C's row (Version 1 sorts the table before
+// streaming it out; the sort here is one of three, chosen per row):
+//   - warp rank:   rows of <= 32 entries held by one warp; each entry's rank is
+//                  the number of smaller tags (register shuffles);
+//   - bitmap rank: a bitmap over the columns of B plus a prefix count per
+//                  32-bit word gives every tag its position directly;
+//   - bitonic:     the compacted entries are sorted in shared memory.
+// Table placements as in the symbolic phase: shared memory (k_num_hash),
+// dense accumulator for dense rows (k_num_dense: values indexed by column,
+// in shared memory when cols(B) is small, else a global-memory row buffer,
+// occupancy in a shared bitmap), and a global-memory hash table (k_num_spill;
+// Version 3's table in DRAM).
+#include <climits>
+
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace smash {
+
+template <typename V>
+struct NumOutT {
+    const int64_t *c_rp;
+    int32_t *c_ci;
+    V *c_val;
+    int64_t c_nnz;
+};
+
+template <typename V>
+__device__ __forceinline__ bool out_range(const NumOutT<V> &o, int64_t i, int64_t &c0, int &n, int *err) {
+    const int64_t s = o.c_rp[i], t = o.c_rp[i + 1];
+    if (s < 0 || t < s || t > o.c_nnz || t - s > INT_MAX) {
+        raise_err(err, kErrBadRowPtr);
+        c0 = 0;
+        n = 0;
+        return false;
+    }
+    c0 = s;
+    n = (int)(t - s);
+    return true;
+}
+
+// ----- write-out: warp rank (GS = 32, at most 32 entries) --------------------
+template <typename V>
+__device__ __forceinline__ void writeout_warp_rank(int *keys, V *vals, int T, int tot, int n_exp,
+                                                   const NumOutT<V> &out, int64_t c0) {
+    const int lane = lane_id();
+    int filled = 0;
+    for (int s0 = 0; s0 < T; s0 += 32) {
+        const int k = keys[s0 + lane];
+        const V v = vals[s0 + lane];
+        const bool occ = k != kEmpty;
+        const unsigned b = __ballot_sync(kFull, occ);
+        __syncwarp();
+        if (occ) {
+            const int pos = filled + __popc(b & lanemask_lt());
+            keys[pos] = k;
+            vals[pos] = v;
+        }
+        filled += __popc(b);
+        __syncwarp();
+    }
+    const int k = lane < tot ? keys[lane] : INT_MAX;
+    const V v = lane < tot ? vals[lane] : V(0);
+    int rank = 0;
+    for (int m = 0; m < tot; ++m) rank += (__shfl_sync(kFull, k, m) < k) ? 1 : 0;
+    if (lane < tot && rank < n_exp) {
+        out.c_ci[c0 + rank] = k;
+        out.c_val[c0 + rank] = v;
+    }
+    __syncwarp();
+}
+
+// ----- write-out: compaction + bitonic sort in shared memory ------------------
+template <typename V, int GS, int NT>
+__device__ __forceinline__ void writeout_bitonic(int *keys, V *vals, int T, int n_exp, const NumOutT<V> &out,
+                                                 int64_t c0, int *red) {
+    using G = Group<GS, NT>;
+    const int t = G::tid();
+    int n = 0;
+    for (int s0 = 0; s0 < T; s0 += GS) {
+        const int s = s0 + t;
+        const int k = keys[s];
+        const V v = vals[s];
+        const int occ = k != kEmpty ? 1 : 0;
+        int ct;
+        const int pos = n + G::template excl_scan<int>(occ, red, &ct);
+        if (occ) {
+            keys[pos] = k;
+            vals[pos] = v;
+        }
+        n += ct;
+    }
+    int P = 1;
+    while (P < n) P <<= 1;
+    G::sync();
+    for (int s = n + t; s < P; s += GS) keys[s] = INT_MAX;
+    G::sync();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int idx = t; idx < (P >> 1); idx += GS) {
+                const int lo = 2 * idx - (idx & (j - 1));
+                const int hi = lo + j;
+                const int a = keys[lo], b = keys[hi];
+                const bool asc = (lo & k) == 0;
+                if ((a > b) == asc) {
+                    keys[lo] = b;
+                    keys[hi] = a;
+                    const V x = vals[lo];
+                    vals[lo] = vals[hi];
+                    vals[hi] = x;
+                }
+            }
+            G::sync();
+        }
+    }
+    const int nw = n < n_exp ? n : n_exp;
+    for (int s = t; s < nw; s += GS) {
+        out.c_ci[c0 + s] = keys[s];
+        out.c_val[c0 + s] = vals[s];
+    }
+}
+
+// Exclusive prefix of popcounts over words [0, nwords) of bm (contiguous
+// chunk per thread); returns the total.
+template <int GS, int NT>
+__device__ __forceinline__ int bitmap_prefix(const unsigned *bm, int *pre, int nwords, int *red) {
+    using G = Group<GS, NT>;
+    const int t = G::tid();
+    const int wpt = (nwords + GS - 1) / GS;
+    const int w0 = t * wpt;
+    const int w1 = min(w0 + wpt, nwords);
+    int loc = 0;
+    for (int w = w0; w < w1; ++w) loc += __popc(bm[w]);
+    int tot;
+    int run = G::template excl_scan<int>(loc, red, &tot);
+    for (int w = w0; w < w1; ++w) {
+        pre[w] = run;
+        run += __popc(bm[w]);
+    }
+    return tot;
+}
+
+// ----- write-out: bitmap rank over the columns of B ---------------------------
+template <typename V, int GS, int NT>
+__device__ __forceinline__ void writeout_bitmap(const int *keys, const V *vals, int T, unsigned *bm, int *pre,
+                                                int words, int n_exp, const NumOutT<V> &out, int64_t c0,
+                                                int *red) {
+    using G = Group<GS, NT>;
+    const int t = G::tid();
+    for (int s = t; s < T; s += GS) {
+        const int k = keys[s];
+        if (k != kEmpty) atomicOr(bm + (k >> 5), 1u << (k & 31));
+    }
+    G::sync();
+    bitmap_prefix<GS, NT>(bm, pre, words, red);
+    G::sync();
+    for (int s = t; s < T; s += GS) {
+        const int k = keys[s];
+        if (k != kEmpty) {
+            const int w = k >> 5;
+            const int pos = pre[w] + __popc(bm[w] & ((1u << (k & 31)) - 1u));
+            if (pos < n_exp) {
+                out.c_ci[c0 + pos] = k;
+                out.c_val[c0 + pos] = vals[s];
+            }
+        }
+    }
+}
+
+template <typename V, int GS>
+__host__ __device__ constexpr size_t num_scratch_bytes() {
+    return (prod_scratch_bytes<V, GS>() + 15) & ~size_t(15);
+}
+
+// ----- shared-memory hash rows -----------------------------------------------
+template <typename V, int GS, int NT>
+__global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows, int count, int *token,
+                                                 int tbits, HashCfg hc, int bm_words, int bitmap_ratio,
+                                                 NumOutT<V> out, int *err) {
+    using G = Group<GS, NT>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_row[G::kGroups];
+    const int T = 1 << tbits;
+    const size_t tab_bytes = (size_t)T * (4 + sizeof(V));
+    unsigned char *gb = smem + (size_t)G::gid() * tab_bytes;
+    int *keys = (int *)gb;
+    V *vals = (V *)(gb + (size_t)T * 4);
+    unsigned char *scr = smem + (size_t)G::kGroups * tab_bytes + (size_t)G::gid() * num_scratch_bytes<V, GS>();
+    const ProdScratch<V> sc = carve_prod_scratch<V, GS>(scr);
+    unsigned *bm = (unsigned *)(smem + (size_t)G::kGroups * (tab_bytes + num_scratch_bytes<V, GS>()));
+    int *pre = (int *)(bm + bm_words);
+    const int t = G::tid();
+    for (;;) {
+        int r;
+        if constexpr (GS == 32) {
+            r = 0;
+            if (t == 0) r = atomicAdd(token, 1);
+            r = __shfl_sync(kFull, r, 0);
+        } else {
+            if (t == 0) s_row[G::gid()] = atomicAdd(token, 1);
+            G::sync();
+            r = s_row[G::gid()];
+        }
+        if (r >= count) break;
+        const int i = rows[r];
+        int64_t c0;
+        int n_exp;
+        const bool ok = out_range(out, i, c0, n_exp, err);
+        const bool use_bm = (GS == NT) && bm_words > 0 && (long long)bm_words <= (long long)bitmap_ratio * n_exp;
+        for (int s = t; s < T; s += GS) {
+            keys[s] = kEmpty;
+            vals[s] = V(0);
+        }
+        if (use_bm)
+            for (int w = t; w < bm_words; w += GS) bm[w] = 0u;
+        G::sync();
+        int64_t ab = 0, ae = 0;
+        if (ok) a_row_range(op, i, ab, ae, err);
+        int cnt = 0;
+        row_products<V, true, GS, NT>(op, ab, ae, sc, err, [&](int j, V v) {
+            bool ins;
+            const int h = hash_find_or_insert<false>(keys, tbits, hc, j, ins);
+            if (h >= 0) {
+                atomicAdd(vals + h, v);
+                cnt += ins ? 1 : 0;
+            } else {
+                raise_err(err, kErrTableFull);
+            }
+        });
+        int tot;
+        if constexpr (GS == 32) {
+            tot = warp_sum(cnt);
+            __syncwarp();
+        } else {
+            tot = G::template sum<int>(cnt, sc.red);
+        }
+        if (t == 0 && tot != n_exp) raise_err(err, kErrCountMismatch);
+        if (GS == 32 && tot <= 32) writeout_warp_rank<V>(keys, vals, T, tot, n_exp, out, c0);
+        else if (use_bm) writeout_bitmap<V, GS, NT>(keys, vals, T, bm, pre, bm_words, n_exp, out, c0, sc.red);
+        else writeout_bitonic<V, GS, NT>(keys, vals, T, n_exp, out, c0, sc.red);
+        G::sync();
+    }
+}
+
+// ----- dense rows -------------------------------------------------------------
+template <typename V, int NT, bool SACC>
+__global__ void __launch_bounds__(NT) k_num_dense(Operands<V> op, const int *rows, int count, int *token,
+                                                  int words, V *acc_g, NumOutT<V> out, int *err) {
+    using G = Group<NT, NT>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_row;
+    unsigned *bm = (unsigned *)smem;
+    int *pre = (int *)(bm + words);
+    V *sacc = (V *)(smem + (size_t)words * 8);
+    const size_t acc_bytes = SACC ? (((size_t)op.ncols * sizeof(V) + 15) & ~size_t(15)) : 0;
+    const ProdScratch<V> sc = carve_prod_scratch<V, NT>(smem + (size_t)words * 8 + acc_bytes);
+    V *acc = SACC ? sacc : acc_g + (size_t)blockIdx.x * (size_t)op.ncols;
+    const int t = threadIdx.x;
+    for (;;) {
+        if (t == 0) s_row = atomicAdd(token, 1);
+        __syncthreads();
+        const int r = s_row;
+        if (r >= count) break;
+        const int i = rows[r];
+        int64_t c0;
+        int n_exp;
+        const bool ok = out_range(out, i, c0, n_exp, err);
+        for (int w = t; w < words; w += NT) bm[w] = 0u;
+        if constexpr (SACC)
+            for (int j = t; j < op.ncols; j += NT) sacc[j] = V(0);
+        __syncthreads();
+        int64_t ab = 0, ae = 0;
+        if (ok) a_row_range(op, i, ab, ae, err);
+        row_products<V, true, NT, NT>(op, ab, ae, sc, err, [&](int j, V v) {
+            atomicAdd(acc + j, v);
+            const unsigned bit = 1u << (j & 31);
+            unsigned *w = bm + (j >> 5);
+            if (!(*(volatile unsigned *)w & bit)) atomicOr(w, bit);
+        });
+        if constexpr (!SACC) __threadfence();
+        __syncthreads();
+        const int tot = bitmap_prefix<NT, NT>(bm, pre, words, sc.red);
+        __syncthreads();
+        if (t == 0 && tot != n_exp) raise_err(err, kErrCountMismatch);
+        for (int w = t; w < words; w += NT) {
+            unsigned bits = bm[w];
+            int pos = pre[w];
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const int j = (w << 5) + b;
+                V v;
+                if constexpr (SACC) {
+                    v = acc[j];
+                } else {
+                    v = __ldcg(acc + j);
+                    __stcg(acc + j, V(0));
+                }
+                if (pos < n_exp) {
+                    out.c_ci[c0 + pos] = j;
+                    out.c_val[c0 + pos] = v;
+                }
+                ++pos;
+            }
+        }
+        if constexpr (!SACC) __threadfence();
+        __syncthreads();
+    }
+}
+
+// ----- global-memory hash rows ------------------------------------------------
+template <int NT>
+__device__ __forceinline__ void block_minmax(int &mn, int &mx, int *s_mm) {
+    mn = warp_min(mn);
+    mx = warp_max(mx);
+    const int w = threadIdx.x >> 5;
+    if (lane_id() == 0) {
+        s_mm[w] = mn;
+        s_mm[32 + w] = mx;
+    }
+    __syncthreads();
+    mn = INT_MAX;
+    mx = INT_MIN;
+    for (int k = 0; k < NT / 32; ++k) {
+        mn = min(mn, s_mm[k]);
+        mx = max(mx, s_mm[32 + k]);
+    }
+    __syncthreads();
+}
+
+template <typename V, int NT>
+__global__ void __launch_bounds__(NT) k_num_spill(Operands<V> op, const int *rows, int count, int *token,
+                                                  HashCfg hc, float inv_load, int spill_tbits, int *keys_all,
+                                                  V *vals_all, int win_words, NumOutT<V> out, int *err) {
+    using G = Group<NT, NT>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_row;
+    __shared__ int s_mm[64];
+    unsigned *bm = (unsigned *)smem;
+    int *pre = (int *)(bm + win_words);
+    const ProdScratch<V> sc = carve_prod_scratch<V, NT>(smem + (size_t)win_words * 8);
+    int *keys = keys_all + ((size_t)blockIdx.x << spill_tbits);
+    V *vals = vals_all + ((size_t)blockIdx.x << spill_tbits);
+    const int t = threadIdx.x;
+    const long long WIN = (long long)win_words * 32;
+    for (;;) {
+        if (t == 0) s_row = atomicAdd(token, 1);
+        __syncthreads();
+        const int r = s_row;
+        if (r >= count) break;
+        const int i = rows[r];
+        int64_t c0;
+        int n_exp;
+        const bool ok = out_range(out, i, c0, n_exp, err);
+        int tb = table_bits(n_exp, inv_load);
+        if (tb > spill_tbits) {
+            if (t == 0) raise_err(err, kErrTableFull);
+            tb = spill_tbits;
+        }
+        const int T = 1 << tb;
+        for (int s = t; s < T; s += NT) {
+            __stcg(keys + s, kEmpty);
+            __stcg(vals + s, V(0));
+        }
+        __threadfence();
+        __syncthreads();
+        int64_t ab = 0, ae = 0;
+        if (ok) a_row_range(op, i, ab, ae, err);
+        int cnt = 0;
+        row_products<V, true, NT, NT>(op, ab, ae, sc, err, [&](int j, V v) {
+            bool ins;
+            const int h = hash_find_or_insert<true>(keys, tb, hc, j, ins);
+            if (h >= 0) {
+                atomicAdd(vals + h, v);
+                cnt += ins ? 1 : 0;
+            } else {
+                raise_err(err, kErrTableFull);
+            }
+        });
+        __threadfence();
+        const int tot = G::template sum<int>(cnt, sc.red);
+        if (t == 0 && tot != n_exp) raise_err(err, kErrCountMismatch);
+        int mn = INT_MAX, mx = INT_MIN;
+        for (int s = t; s < T; s += NT) {
+            const int k = __ldcg(keys + s);
+            if (k != kEmpty) {
+                mn = min(mn, k);
+                mx = max(mx, k);
+            }
+        }
+        block_minmax<NT>(mn, mx, s_mm);
+        long long done = 0;
+        if (tot > 0) {
+            for (long long w0 = ((long long)mn / WIN) * WIN; w0 <= (long long)mx; w0 += WIN) {
+                for (int w = t; w < win_words; w += NT) bm[w] = 0u;
+                __syncthreads();
+                for (int s = t; s < T; s += NT) {
+                    const long long k = __ldcg(keys + s);
+                    if (k != kEmpty && k >= w0 && k < w0 + WIN) {
+                        const int d = (int)(k - w0);
+                        atomicOr(bm + (d >> 5), 1u << (d & 31));
+                    }
+                }
+                __syncthreads();
+                const int wt = bitmap_prefix<NT, NT>(bm, pre, win_words, sc.red);
+                __syncthreads();
+                for (int s = t; s < T; s += NT) {
+                    const long long k = __ldcg(keys + s);
+                    if (k != kEmpty && k >= w0 && k < w0 + WIN) {
+                        const int d = (int)(k - w0);
+                        const long long pos =
+                            done + pre[d >> 5] + __popc(bm[d >> 5] & ((1u << (d & 31)) - 1u));
+                        if (pos < n_exp) {
+                            out.c_ci[c0 + pos] = (int)k;
+                            out.c_val[c0 + pos] = __ldcg(vals + s);
+                        }
+                    }
+                }
+                done += wt;
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+int max_smem_per_block() {
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cached = v > 0 ? v : 232448;
+    }
+    return cached;
+}
+
+template <typename V>
+static Operands<V> num_operands(const RawOperands &r) {
+    Operands<V> o;
+    o.a_rp = r.a_rp;
+    o.a_ci = r.a_ci;
+    o.a_val = (const V *)r.a_val;
+    o.b_rp = r.b_rp;
+    o.b_ci = r.b_ci;
+    o.b_val = (const V *)r.b_val;
+    o.a_nnz = r.a_nnz;
+    o.b_nnz = r.b_nnz;
+    o.b_rows = r.b_rows;
+    o.ncols = r.ncols;
+    return o;
+}
+
+template <typename V>
+static NumOutT<V> num_out(const NumOut &o) {
+    return NumOutT<V>{o.c_rp, o.c_ci, (V *)o.c_val, o.c_nnz};
+}
+
+static int threads_per_row(int tbits, int shift) {
+    int t = 1 << (tbits > shift ? tbits - shift : 0);
+    if (t < 32) t = 32;
+    if (t > 1024) t = 1024;
+    return t;
+}
+
+static int block_threads(int gs) { return gs < 256 ? 256 : gs; }
+
+template <typename V>
+static size_t num_hash_smem(int tbits, int gs, int bm_words) {
+    const int nt = block_threads(gs);
+    const int groups = nt / gs;
+    size_t scr = 0;
+    switch (gs) {
+        case 32: scr = num_scratch_bytes<V, 32>(); break;
+        case 64: scr = num_scratch_bytes<V, 64>(); break;
+        case 128: scr = num_scratch_bytes<V, 128>(); break;
+        case 256: scr = num_scratch_bytes<V, 256>(); break;
+        case 512: scr = num_scratch_bytes<V, 512>(); break;
+        default: scr = num_scratch_bytes<V, 1024>(); break;
+    }
+    return (size_t)groups * (((size_t)(4 + sizeof(V))) << tbits) + (size_t)groups * scr + (size_t)bm_words * 8;
+}
+
+bool num_hash_bitmap_fits(int dtype, int tbits, int ncols) {
+    const int words = (ncols + 31) / 32;
+    const size_t s = dtype ? num_hash_smem<double>(tbits, 1024, words) : num_hash_smem<float>(tbits, 1024, words);
+    return s <= (size_t)max_smem_per_block();
+}
+
+template <typename K>
+static int resident_grid(K kernel, int nt, size_t smem, int sms, long long want_blocks, int cap_per_sm = 64) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, nt, smem);
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > cap_per_sm) per_sm = cap_per_sm;
+    long long cap = (long long)per_sm * sms;
+    return (int)(want_blocks < cap ? want_blocks : cap);
+}
+
+template <typename V, int GS>
+static void num_hash_go(const Operands<V> &op, const int *rows, int count, int *token, const HashLaunch &hl,
+                        int bitmap_ratio, const NumOutT<V> &out, int *err, cudaStream_t s) {
+    constexpr int NT = GS < 256 ? 256 : GS;
+    constexpr int groups = NT / GS;
+    int bm_words = 0;
+    if (GS == NT && bitmap_ratio > 0) {
+        const int words = (op.ncols + 31) / 32;
+        if (num_hash_smem<V>(hl.tbits, GS, words) <= (size_t)max_smem_per_block()) bm_words = words;
+    }
+    const size_t smem = num_hash_smem<V>(hl.tbits, GS, bm_words);
+    auto kern = k_num_hash<V, GS, NT>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = resident_grid(kern, NT, smem, hl.sms, (count + groups - 1) / groups);
+    const HashCfg hc{hl.hash_kind, hl.colbits};
+    kern<<<grid, NT, smem, s>>>(op, rows, count, token, hl.tbits, hc, bm_words, bitmap_ratio, out, err);
+}
+
+template <typename V>
+static void num_hash_typed(const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
+                           int bitmap_ratio, const NumOut &o, int *err, cudaStream_t s) {
+    const Operands<V> op = num_operands<V>(r);
+    const NumOutT<V> out = num_out<V>(o);
+    switch (threads_per_row(hl.tbits, hl.group_shift)) {
+        case 32: num_hash_go<V, 32>(op, rows, count, token, hl, bitmap_ratio, out, err, s); break;
+        case 64: num_hash_go<V, 64>(op, rows, count, token, hl, bitmap_ratio, out, err, s); break;
+        case 128: num_hash_go<V, 128>(op, rows, count, token, hl, bitmap_ratio, out, err, s); break;
+        case 256: num_hash_go<V, 256>(op, rows, count, token, hl, bitmap_ratio, out, err, s); break;
+        case 512: num_hash_go<V, 512>(op, rows, count, token, hl, bitmap_ratio, out, err, s); break;
+        default: num_hash_go<V, 1024>(op, rows, count, token, hl, bitmap_ratio, out, err, s); break;
+    }
+}
+
+void launch_num_hash(int dtype, const RawOperands &r, const int *rows, int count, int *token,
+                     const HashLaunch &hl, float inv_load, int bitmap_ratio, const NumOut &out, int *err,
+                     cudaStream_t s) {
+    (void)inv_load;
+    if (count <= 0) return;
+    if (dtype) num_hash_typed<double>(r, rows, count, token, hl, bitmap_ratio, out, err, s);
+    else num_hash_typed<float>(r, rows, count, token, hl, bitmap_ratio, out, err, s);
+}
+
+template <typename V>
+static size_t dense_smem(int ncols, bool sacc) {
+    const int words = (ncols + 31) / 32;
+    size_t b = (size_t)words * 8 + num_scratch_bytes<V, 1024>();
+    if (sacc) b += ((size_t)ncols * sizeof(V) + 15) & ~size_t(15);
+    return b;
+}
+
+bool num_dense_uses_smem_acc(int dtype, int ncols) {
+    const size_t s = dtype ? dense_smem<double>(ncols, true) : dense_smem<float>(ncols, true);
+    return s <= (size_t)max_smem_per_block() / 2;   // leave room for two blocks per SM
+}
+
+int dense_bitmap_max_cols() {
+    const size_t avail = (size_t)max_smem_per_block() - num_scratch_bytes<double, 1024>() - 64;
+    return (int)((avail / 8) * 32);
+}
+
+int num_dense_grid(int dtype, const HashLaunch &hl, int ncols) {
+    (void)ncols;
+    (void)dtype;
+    const int per = hl.blocks_per_sm > 0 ? hl.blocks_per_sm : 1;
+    return hl.sms * per;
+}
+
+template <typename V>
+static void num_dense_typed(const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
+                            void *acc, const NumOut &o, int *err, cudaStream_t s) {
+    const Operands<V> op = num_operands<V>(r);
+    const NumOutT<V> out = num_out<V>(o);
+    const int words = (r.ncols + 31) / 32;
+    const bool sacc = num_dense_uses_smem_acc(sizeof(V) == 8, r.ncols);
+    if (sacc) {
+        const size_t smem = dense_smem<V>(r.ncols, true);
+        auto kern = k_num_dense<V, 1024, true>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int grid = resident_grid(kern, 1024, smem, hl.sms, count, 2);
+        kern<<<grid, 1024, smem, s>>>(op, rows, count, token, words, nullptr, out, err);
+    } else {
+        const size_t smem = dense_smem<V>(r.ncols, false);
+        auto kern = k_num_dense<V, 1024, false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int grid = num_dense_grid(sizeof(V) == 8, hl, r.ncols);
+        if (grid > count) grid = count;
+        kern<<<grid, 1024, smem, s>>>(op, rows, count, token, words, (V *)acc, out, err);
+    }
+}
+
+void launch_num_dense(int dtype, const RawOperands &r, const int *rows, int count, int *token,
+                      const HashLaunch &hl, void *acc, const NumOut &out, int *err, cudaStream_t s) {
+    if (count <= 0) return;
+    if (dtype) num_dense_typed<double>(r, rows, count, token, hl, acc, out, err, s);
+    else num_dense_typed<float>(r, rows, count, token, hl, acc, out, err, s);
+}
+
+int num_spill_grid(int dtype, const HashLaunch &hl) {
+    (void)dtype;
+    const int per = hl.blocks_per_sm > 0 ? hl.blocks_per_sm : 1;
+    return hl.sms * per;
+}
+
+template <typename V>
+static void num_spill_typed(const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
+                            float inv_load, int spill_tbits, void *tables, const NumOut &o, int *err,
+                            cudaStream_t s) {
+    const Operands<V> op = num_operands<V>(r);
+    const NumOutT<V> out = num_out<V>(o);
+    int words = (r.ncols + 31) / 32;
+    if (words > 16384) words = 16384;
+    const size_t smem = (size_t)words * 8 + num_scratch_bytes<V, 1024>();
+    auto kern = k_num_spill<V, 1024>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int gridmax = num_spill_grid(sizeof(V) == 8, hl);
+    const int grid = count < gridmax ? count : gridmax;
+    int *keys = (int *)tables;
+    V *vals = (V *)((char *)tables + ((size_t)gridmax << spill_tbits) * 4);
+    const HashCfg hc{hl.hash_kind, hl.colbits};
+    kern<<<grid, 1024, smem, s>>>(op, rows, count, token, hc, inv_load, spill_tbits, keys, vals, words, out, err);
+}
+
+void launch_num_spill(int dtype, const RawOperands &r, const int *rows, int count, int *token,
+                      const HashLaunch &hl, float inv_load, int spill_tbits, void *tables, const NumOut &out,
+                      int *err, cudaStream_t s) {
+    if (count <= 0) return;
+    if (dtype) num_spill_typed<double>(r, rows, count, token, hl, inv_load, spill_tbits, tables, out, err, s);
+    else num_spill_typed<float>(r, rows, count, token, hl, inv_load, spill_tbits, tables, out, err, s);
+}
+
+}  // namespace smash

@@ -1,0 +1,279 @@
+// Row planning kernels: per-row product counts, binning, row-pointer scan.
+//
+// Window Distribution Phase: the number of FMAs of every row is counted from
+// the row pointers alone (Gustavson's first pass: flop_i = sum_{k in A_i} |B_k|),
+// and each row is assigned to a dense or a sparse (hashed) path by a threshold
+// on that count. Rows are then grouped by the table size they need, so that one
+// kernel launch serves rows of similar cost (the GPU counterpart of packing
+// rows into windows sized to the scratchpad).
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace smash {
+
+__device__ __forceinline__ int bin_for(long long size, const BinRule &r) {
+    if (size <= 0) return kBinEmpty;
+    if (r.dense_ok && size >= r.dense_min) return kBinDense;
+    const int tb = table_bits(size, r.inv_load);
+    if (tb <= r.max_tbits) return bin_of_tbits(tb);
+    return r.dense_ok ? kBinDense : kBinSpill;
+}
+
+// One warp per row of A: flop_i, its bound min(flop_i, cols(B)), and the bin.
+__global__ void __launch_bounds__(256) k_sym_rowinfo(RawOperands op, BinRule rule, BinBuffers bb,
+                                                     long long *bound_out, int *nnz_out, int *err) {
+    __shared__ int s_cnt[kNumBins];
+    __shared__ long long s_max[kNumBins];
+    __shared__ long long s_prod, s_maxrow;
+    if (threadIdx.x < kNumBins) {
+        s_cnt[threadIdx.x] = 0;
+        s_max[threadIdx.x] = 0;
+    }
+    if (threadIdx.x == 0) {
+        s_prod = 0;
+        s_maxrow = 0;
+    }
+    __syncthreads();
+    const int lane = lane_id();
+    long long my_prod = 0, my_max = 0;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < op.a_rows; i += warps) {
+        int64_t ab = __ldg(op.a_rp + i), ae = __ldg(op.a_rp + i + 1);
+        if (ab < 0 || ae < ab || ae > op.a_nnz) {
+            if (lane == 0) raise_err(err, kErrBadRowPtr);
+            ab = ae = 0;
+        }
+        long long f = 0;
+        for (int64_t e = ab + lane; e < ae; e += 32) {
+            const int k = __ldg(op.a_ci + e);
+            if ((unsigned)k < (unsigned)op.b_rows) {
+                const int64_t s = __ldg(op.b_rp + k), t = __ldg(op.b_rp + k + 1);
+                if (s >= 0 && t >= s && t <= op.b_nnz) f += t - s;
+                else raise_err(err, kErrBadRowPtr);
+            } else {
+                raise_err(err, kErrBadIndex);
+            }
+        }
+        f = warp_sum(f);
+        if (lane == 0) {
+            const long long bound = f < (long long)op.ncols ? f : (long long)op.ncols;
+            const int b = bin_for(bound, rule);
+            bb.bin[i] = (uint8_t)b;
+            bound_out[i] = bound;
+            atomicAdd(&s_cnt[b], 1);
+            atomicMax(&s_max[b], bound);
+            if (b == kBinEmpty) nnz_out[i] = 0;
+            my_prod += f;
+            my_max = f > my_max ? f : my_max;
+        }
+    }
+    if (lane == 0) {
+        atomicAdd((unsigned long long *)&s_prod, (unsigned long long)my_prod);
+        atomicMax(&s_maxrow, my_max);
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumBins && s_cnt[threadIdx.x]) {
+        atomicAdd(bb.counts + threadIdx.x, s_cnt[threadIdx.x]);
+        atomicMax(bb.maxsize + threadIdx.x, s_max[threadIdx.x]);
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd((unsigned long long *)bb.stats, (unsigned long long)s_prod);
+        atomicMax(bb.stats + 1, s_maxrow);
+    }
+}
+
+// One thread per row of C: the exact row length from C's row pointer.
+__global__ void __launch_bounds__(256) k_num_rowinfo(const int64_t *c_rp, int64_t n, int64_t c_nnz,
+                                                     BinRule rule, BinBuffers bb, int *err) {
+    __shared__ int s_cnt[kNumBins];
+    __shared__ long long s_max[kNumBins];
+    if (threadIdx.x < kNumBins) {
+        s_cnt[threadIdx.x] = 0;
+        s_max[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t s = c_rp[i], t = c_rp[i + 1];
+        long long size = 0;
+        if (s < 0 || t < s || t > c_nnz) raise_err(err, kErrBadRowPtr);
+        else size = t - s;
+        const int b = bin_for(size, rule);
+        bb.bin[i] = (uint8_t)b;
+        atomicAdd(&s_cnt[b], 1);
+        atomicMax(&s_max[b], size);
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumBins && s_cnt[threadIdx.x]) {
+        atomicAdd(bb.counts + threadIdx.x, s_cnt[threadIdx.x]);
+        atomicMax(bb.maxsize + threadIdx.x, s_max[threadIdx.x]);
+    }
+}
+
+// Scatter row ids into their bins. Each block reserves one range per bin.
+constexpr int kScatNT = 256, kScatItems = 8;
+__global__ void __launch_bounds__(kScatNT) k_bin_scatter(int64_t n, BinBuffers bb) {
+    __shared__ int s_off[kNumBins + 1], s_cnt[kNumBins], s_base[kNumBins];
+    if (threadIdx.x < kNumBins) s_cnt[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int b = 0; b < kNumBins; ++b) {
+            s_off[b] = acc;
+            if (b != kBinEmpty) acc += bb.counts[b];
+        }
+        s_off[kNumBins] = acc;
+        if (blockIdx.x == 0)
+            for (int b = 0; b <= kNumBins; ++b) bb.offsets[b] = s_off[b];
+    }
+    __syncthreads();
+    int loc[kScatItems];
+    int bins[kScatItems];
+    const int64_t base = (int64_t)blockIdx.x * kScatNT * kScatItems;
+#pragma unroll
+    for (int it = 0; it < kScatItems; ++it) {
+        const int64_t i = base + it * kScatNT + threadIdx.x;
+        bins[it] = -1;
+        if (i < n) {
+            const int b = bb.bin[i];
+            if (b != kBinEmpty) {
+                bins[it] = b;
+                loc[it] = atomicAdd(&s_cnt[b], 1);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumBins && s_cnt[threadIdx.x])
+        s_base[threadIdx.x] = atomicAdd(bb.cursor + threadIdx.x, s_cnt[threadIdx.x]);
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kScatItems; ++it) {
+        if (bins[it] >= 0) {
+            const int b = bins[it];
+            bb.rows[s_off[b] + s_base[b] + loc[it]] = (int)(base + it * kScatNT + threadIdx.x);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of int32 row counts into the int64 row pointer of C.
+constexpr int kScanNT = 512, kScanItems = 8, kScanTile = kScanNT * kScanItems;
+
+__device__ __forceinline__ long long block_excl_scan64(long long v, long long *s_w, long long *total) {
+    const long long incl = warp_incl_scan64(v);
+    const int w = threadIdx.x >> 5;
+    if (lane_id() == 31) s_w[w] = incl;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        long long x = threadIdx.x < (blockDim.x >> 5) ? s_w[threadIdx.x] : 0;
+        long long xi = warp_incl_scan64(x);
+        s_w[threadIdx.x] = xi - x;
+        if (threadIdx.x == 31) s_w[32] = xi;
+    }
+    __syncthreads();
+    const long long r = s_w[w] + incl - v;
+    *total = s_w[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanNT) k_scan_reduce(const int *nnz, int64_t n, long long *part) {
+    __shared__ long long s_w[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    long long s = 0;
+#pragma unroll
+    for (int it = 0; it < kScanItems; ++it) {
+        const int64_t i = base + it * kScanNT + threadIdx.x;
+        if (i < n) s += nnz[i];
+    }
+    long long tot;
+    block_excl_scan64(s, s_w, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(long long *part, int64_t nparts, int64_t n,
+                                                   int64_t *c_rp, long long *total) {
+    __shared__ long long s_w[33];
+    long long carry = 0;
+    for (int64_t b0 = 0; b0 < nparts; b0 += blockDim.x) {
+        const int64_t b = b0 + threadIdx.x;
+        const long long v = b < nparts ? part[b] : 0;
+        long long tot;
+        const long long ex = block_excl_scan64(v, s_w, &tot);
+        if (b < nparts) part[b] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        c_rp[n] = carry;
+        *total = carry;
+    }
+}
+
+__global__ void __launch_bounds__(kScanNT) k_scan_down(const int *nnz, int64_t n, const long long *part,
+                                                       int64_t *c_rp) {
+    __shared__ long long s_w[33];
+    __shared__ int s_v[kScanTile];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+#pragma unroll
+    for (int it = 0; it < kScanItems; ++it) {
+        const int64_t i = base + it * kScanNT + threadIdx.x;
+        s_v[it * kScanNT + threadIdx.x] = i < n ? nnz[i] : 0;
+    }
+    __syncthreads();
+    long long loc = 0;
+#pragma unroll
+    for (int it = 0; it < kScanItems; ++it) loc += s_v[threadIdx.x * kScanItems + it];
+    long long tot;
+    long long run = part[blockIdx.x] + block_excl_scan64(loc, s_w, &tot);
+    long long outv[kScanItems];
+#pragma unroll
+    for (int it = 0; it < kScanItems; ++it) {
+        outv[it] = run;
+        run += s_v[threadIdx.x * kScanItems + it];
+    }
+#pragma unroll
+    for (int it = 0; it < kScanItems; ++it) {
+        const int64_t i = base + threadIdx.x * kScanItems + it;
+        if (i < n) c_rp[i] = outv[it];
+    }
+}
+
+// ---------------------------------------------------------------------------
+void launch_sym_rowinfo(const RawOperands &op, const BinRule &rule, BinBuffers bb, long long *bound_out,
+                        int *nnz_out, int *err, int sms, cudaStream_t s) {
+    if (op.a_rows == 0) return;
+    int64_t warps_needed = op.a_rows;
+    int64_t blocks = (warps_needed + 7) / 8;
+    int64_t cap = (int64_t)sms * 8;
+    int grid = (int)(blocks < cap ? blocks : cap);
+    k_sym_rowinfo<<<grid, 256, 0, s>>>(op, rule, bb, bound_out, nnz_out, err);
+}
+
+void launch_num_rowinfo(const int64_t *c_rp, int64_t n, int64_t c_nnz, const BinRule &rule, BinBuffers bb,
+                        int *err, cudaStream_t s) {
+    if (n == 0) return;
+    int64_t blocks = (n + 255) / 256;
+    int grid = (int)(blocks < 4096 ? blocks : 4096);
+    k_num_rowinfo<<<grid, 256, 0, s>>>(c_rp, n, c_nnz, rule, bb, err);
+}
+
+void launch_bin_scatter(int64_t n, BinBuffers bb, cudaStream_t s) {
+    if (n == 0) return;
+    const int64_t per = (int64_t)kScatNT * kScatItems;
+    k_bin_scatter<<<(unsigned)((n + per - 1) / per), kScatNT, 0, s>>>(n, bb);
+}
+
+size_t scan_scratch_bytes(int64_t n) {
+    const int64_t parts = (n + kScanTile - 1) / kScanTile;
+    return (size_t)(parts + 1) * sizeof(long long);
+}
+
+void launch_scan_rowptr(const int *nnz, int64_t n, int64_t *c_rp, long long *total, void *scratch,
+                        cudaStream_t s) {
+    long long *part = (long long *)scratch;
+    const int64_t parts = (n + kScanTile - 1) / kScanTile;
+    if (n > 0) k_scan_reduce<<<(unsigned)parts, kScanNT, 0, s>>>(nnz, n, part);
+    k_scan_top<<<1, 1024, 0, s>>>(part, parts, n, c_rp, total);
+    if (n > 0) k_scan_down<<<(unsigned)parts, kScanNT, 0, s>>>(nnz, n, part, c_rp);
+}
+
+}  // namespace smash

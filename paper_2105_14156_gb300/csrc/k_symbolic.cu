@@ -1,0 +1,227 @@
+// Symbolic phase: the exact number of distinct columns of every row of C.
+//
+// Hashing Phase without values: every product's column tag is inserted into
+// a per-row open-addressing table with compare-and-swap on EMPTY (= -1), +1
+// linear probing on collision; the row's count is the number of successful
+// inserts. Three table placements, by row size:
+//   k_sym_hash   shared-memory table of 2^tbits int32 tags, one thread group
+//                per row, rows claimed by atomic tokens (Version 2's
+//                tokenization: a work counter instead of a static schedule);
+//   k_sym_dense  the paper's "dense row": a bitmap over all columns of B in
+//                shared memory (no probing), for rows whose bound is a large
+//                fraction of cols(B);
+//   k_sym_spill  the table in global memory (Version 3 moved it to DRAM), for
+//                rows too large for shared memory when the bitmap does not fit.
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace smash {
+
+template <int GS, int NT>
+__global__ void __launch_bounds__(NT) k_sym_hash(Operands<float> op, const int *rows, int count, int *token,
+                                                 int tbits, HashCfg hc, int *nnz_out, int *err) {
+    using G = Group<GS, NT>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_row[G::kGroups];
+    const int T = 1 << tbits;
+    int *keys = (int *)smem + (size_t)G::gid() * T;
+    unsigned char *scr = smem + (size_t)G::kGroups * T * 4 + (size_t)G::gid() * prod_scratch_bytes<float, GS>();
+    const ProdScratch<float> sc = carve_prod_scratch<float, GS>(scr);
+    const int t = G::tid();
+    for (;;) {
+        int r;
+        if constexpr (GS == 32) {
+            r = 0;
+            if (t == 0) r = atomicAdd(token, 1);
+            r = __shfl_sync(kFull, r, 0);
+        } else {
+            if (t == 0) s_row[G::gid()] = atomicAdd(token, 1);
+            G::sync();
+            r = s_row[G::gid()];
+        }
+        if (r >= count) break;
+        const int i = rows[r];
+        for (int s = t; s < T; s += GS) keys[s] = kEmpty;
+        G::sync();
+        int64_t ab, ae;
+        a_row_range(op, i, ab, ae, err);
+        int cnt = 0;
+        row_products<float, false, GS, NT>(op, ab, ae, sc, err, [&](int j, float) {
+            bool ins;
+            if (hash_find_or_insert<false>(keys, tbits, hc, j, ins) < 0) raise_err(err, kErrTableFull);
+            cnt += ins ? 1 : 0;
+        });
+        int tot;
+        if constexpr (GS == 32) tot = warp_sum(cnt);
+        else tot = G::template sum<int>(cnt, sc.red);
+        if (t == 0) nnz_out[i] = tot;
+        G::sync();
+    }
+}
+
+// Dense rows: a bitmap over the columns of B; count = popcount.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_sym_dense(Operands<float> op, const int *rows, int count, int *token,
+                                                  int words, int *nnz_out, int *err) {
+    using G = Group<NT, NT>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_row;
+    unsigned *bm = (unsigned *)smem;
+    const ProdScratch<float> sc = carve_prod_scratch<float, NT>(smem + (size_t)words * 4);
+    const int t = threadIdx.x;
+    for (;;) {
+        if (t == 0) s_row = atomicAdd(token, 1);
+        __syncthreads();
+        const int r = s_row;
+        if (r >= count) break;
+        const int i = rows[r];
+        for (int w = t; w < words; w += NT) bm[w] = 0u;
+        __syncthreads();
+        int64_t ab, ae;
+        a_row_range(op, i, ab, ae, err);
+        row_products<float, false, NT, NT>(op, ab, ae, sc, err, [&](int j, float) {
+            const unsigned bit = 1u << (j & 31);
+            unsigned *w = bm + (j >> 5);
+            if (!(*(volatile unsigned *)w & bit)) atomicOr(w, bit);
+        });
+        __syncthreads();
+        int cnt = 0;
+        for (int w = t; w < words; w += NT) cnt += __popc(bm[w]);
+        const int tot = G::template sum<int>(cnt, sc.red);
+        if (t == 0) nnz_out[i] = tot;
+        __syncthreads();
+    }
+}
+
+// Spill rows: the key table lives in global memory, one slice per block.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_sym_spill(Operands<float> op, const int *rows, int count, int *token,
+                                                  HashCfg hc, float inv_load, const long long *bound,
+                                                  int spill_tbits, int *tables, int *nnz_out, int *err) {
+    using G = Group<NT, NT>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_row;
+    const ProdScratch<float> sc = carve_prod_scratch<float, NT>(smem);
+    int *keys = tables + ((size_t)blockIdx.x << spill_tbits);
+    const int t = threadIdx.x;
+    for (;;) {
+        if (t == 0) s_row = atomicAdd(token, 1);
+        __syncthreads();
+        const int r = s_row;
+        if (r >= count) break;
+        const int i = rows[r];
+        int tb = table_bits(bound[i], inv_load);
+        if (tb > spill_tbits) {
+            raise_err(err, kErrTableFull);
+            tb = spill_tbits;
+        }
+        const int T = 1 << tb;
+        for (int s = t; s < T; s += NT) __stcg(keys + s, kEmpty);
+        __syncthreads();
+        int64_t ab, ae;
+        a_row_range(op, i, ab, ae, err);
+        int cnt = 0;
+        row_products<float, false, NT, NT>(op, ab, ae, sc, err, [&](int j, float) {
+            bool ins;
+            if (hash_find_or_insert<true>(keys, tb, hc, j, ins) < 0) raise_err(err, kErrTableFull);
+            cnt += ins ? 1 : 0;
+        });
+        const int tot = G::template sum<int>(cnt, sc.red);
+        if (t == 0) nnz_out[i] = tot;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+static Operands<float> sym_operands(const RawOperands &r) {
+    Operands<float> o;
+    o.a_rp = r.a_rp;
+    o.a_ci = r.a_ci;
+    o.a_val = nullptr;
+    o.b_rp = r.b_rp;
+    o.b_ci = r.b_ci;
+    o.b_val = nullptr;
+    o.a_nnz = r.a_nnz;
+    o.b_nnz = r.b_nnz;
+    o.b_rows = r.b_rows;
+    o.ncols = r.ncols;
+    return o;
+}
+
+
+template <typename K>
+static int resident_grid(K kernel, int nt, size_t smem, int sms, int want_blocks, int cap_per_sm = 64) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, nt, smem);
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > cap_per_sm) per_sm = cap_per_sm;
+    long long cap = (long long)per_sm * sms;
+    return (int)(want_blocks < cap ? want_blocks : cap);
+}
+
+template <int GS, int NT>
+static void sym_hash_launch(const Operands<float> &op, const int *rows, int count, int *token, int tbits,
+                            HashCfg hc, int sms, int *nnz_out, int *err, cudaStream_t s) {
+    constexpr int groups = NT / GS;
+    const size_t smem = (size_t)groups * ((size_t)4 << tbits) +
+                        (GS > 32 ? (size_t)groups * prod_scratch_bytes<float, GS>() : 0);
+    auto kern = k_sym_hash<GS, NT>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int want = (count + groups - 1) / groups;
+    const int grid = resident_grid(kern, NT, smem, sms, want);
+    kern<<<grid, NT, smem, s>>>(op, rows, count, token, tbits, hc, nnz_out, err);
+}
+
+static int threads_per_row(int tbits, int shift) {
+    int t = 1 << (tbits > shift ? tbits - shift : 0);
+    if (t < 32) t = 32;
+    if (t > 1024) t = 1024;
+    return t;
+}
+
+void launch_sym_hash(const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
+                     int *nnz_out, int *err, cudaStream_t s) {
+    if (count <= 0) return;
+    const Operands<float> op = sym_operands(r);
+    const HashCfg hc{hl.hash_kind, hl.colbits};
+    switch (threads_per_row(hl.tbits, hl.group_shift)) {
+        case 32: sym_hash_launch<32, 256>(op, rows, count, token, hl.tbits, hc, hl.sms, nnz_out, err, s); break;
+        case 64: sym_hash_launch<64, 256>(op, rows, count, token, hl.tbits, hc, hl.sms, nnz_out, err, s); break;
+        case 128: sym_hash_launch<128, 256>(op, rows, count, token, hl.tbits, hc, hl.sms, nnz_out, err, s); break;
+        case 256: sym_hash_launch<256, 256>(op, rows, count, token, hl.tbits, hc, hl.sms, nnz_out, err, s); break;
+        case 512: sym_hash_launch<512, 512>(op, rows, count, token, hl.tbits, hc, hl.sms, nnz_out, err, s); break;
+        default: sym_hash_launch<1024, 1024>(op, rows, count, token, hl.tbits, hc, hl.sms, nnz_out, err, s); break;
+    }
+}
+
+void launch_sym_dense(const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
+                      int *nnz_out, int *err, cudaStream_t s) {
+    if (count <= 0) return;
+    const Operands<float> op = sym_operands(r);
+    const int words = (r.ncols + 31) / 32;
+    const size_t smem = (size_t)words * 4 + prod_scratch_bytes<float, 1024>();
+    auto kern = k_sym_dense<1024>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = resident_grid(kern, 1024, smem, hl.sms, count, hl.blocks_per_sm > 0 ? hl.blocks_per_sm : 2);
+    kern<<<grid, 1024, smem, s>>>(op, rows, count, token, words, nnz_out, err);
+}
+
+int sym_spill_grid(const HashLaunch &hl) {
+    const int per = hl.blocks_per_sm > 0 ? hl.blocks_per_sm : 1;
+    return hl.sms * per;
+}
+
+void launch_sym_spill(const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
+                      float inv_load, const long long *bound, int spill_tbits, int *tables, int *nnz_out,
+                      int *err, cudaStream_t s) {
+    if (count <= 0) return;
+    const Operands<float> op = sym_operands(r);
+    const HashCfg hc{hl.hash_kind, hl.colbits};
+    const size_t smem = prod_scratch_bytes<float, 1024>();
+    auto kern = k_sym_spill<1024>;
+    int grid = sym_spill_grid(hl);
+    if (grid > count) grid = count;
+    kern<<<grid, 1024, smem, s>>>(op, rows, count, token, hc, inv_load, bound, spill_tbits, tables, nnz_out, err);
+}
+
+}  // namespace smash

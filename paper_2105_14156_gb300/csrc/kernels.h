@@ -1,0 +1,96 @@
+// Host-side launchers of the SpGEMM kernels (one translation unit each).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace smash {
+
+// Binning rule of one phase: which bin a row of a given size bound goes to.
+struct BinRule {
+    float inv_load;     // 1 / max_load
+    int max_tbits;      // largest shared-memory table (log2 slots)
+    int dense_ok;       // dense accumulator allowed (column bitmap fits shared memory)
+    int64_t dense_min;  // size >= dense_min goes dense (when dense_ok)
+};
+
+// Raw device view of a CSR operand pair (values as void*).
+struct RawOperands {
+    const int64_t *a_rp;
+    const int32_t *a_ci;
+    const void *a_val;
+    const int64_t *b_rp;
+    const int32_t *b_ci;
+    const void *b_val;
+    int64_t a_rows;
+    int64_t a_nnz;
+    int64_t b_nnz;
+    int32_t b_rows;
+    int32_t ncols;
+};
+
+struct BinBuffers {
+    uint8_t *bin;      // [n]
+    int *counts;       // [16]  rows per bin
+    int *cursor;       // [16]  scatter cursors
+    int *tokens;       // [16]  work tokens (row claims) per bin
+    long long *maxsize;  // [16] largest size bound per bin
+    long long *stats;    // [4]  products, max row products
+    int *rows;         // [n]   row ids grouped by bin
+    int *offsets;      // [17]  exclusive offsets of the bins in rows[]
+};
+
+// k_rows.cu
+void launch_sym_rowinfo(const RawOperands &op, const BinRule &rule, BinBuffers bb, long long *bound_out,
+                        int *nnz_out, int *err, int sms, cudaStream_t s);
+void launch_num_rowinfo(const int64_t *c_rp, int64_t n, int64_t c_nnz, const BinRule &rule,
+                        BinBuffers bb, int *err, cudaStream_t s);
+void launch_bin_scatter(int64_t n, BinBuffers bb, cudaStream_t s);
+size_t scan_scratch_bytes(int64_t n);
+void launch_scan_rowptr(const int *nnz, int64_t n, int64_t *c_rp, long long *total,
+                        void *scratch, cudaStream_t s);
+
+struct HashLaunch {
+    int tbits;          // table size 2^tbits
+    int group_shift;    // threads per row = clamp(T >> shift, 32, 1024)
+    int hash_kind;
+    int colbits;
+    int sms;
+    int blocks_per_sm;  // for dense / spill kernels
+};
+
+// k_symbolic.cu
+void launch_sym_hash(const RawOperands &op, const int *rows, int count, int *token, const HashLaunch &hl,
+                     int *nnz_out, int *err, cudaStream_t s);
+void launch_sym_dense(const RawOperands &op, const int *rows, int count, int *token, const HashLaunch &hl,
+                      int *nnz_out, int *err, cudaStream_t s);
+int sym_spill_grid(const HashLaunch &hl);
+void launch_sym_spill(const RawOperands &op, const int *rows, int count, int *token, const HashLaunch &hl,
+                      float inv_load, const long long *bound, int spill_tbits, int *tables, int *nnz_out,
+                      int *err, cudaStream_t s);
+
+// k_numeric.cu (dtype: 0 float, 1 double)
+struct NumOut {
+    const int64_t *c_rp;
+    int32_t *c_ci;
+    void *c_val;
+    int64_t c_nnz;
+};
+void launch_num_hash(int dtype, const RawOperands &op, const int *rows, int count, int *token,
+                     const HashLaunch &hl, float inv_load, int bitmap_ratio, const NumOut &out, int *err,
+                     cudaStream_t s);
+int num_dense_grid(int dtype, const HashLaunch &hl, int ncols);
+bool num_dense_uses_smem_acc(int dtype, int ncols);
+void launch_num_dense(int dtype, const RawOperands &op, const int *rows, int count, int *token,
+                      const HashLaunch &hl, void *acc, const NumOut &out, int *err, cudaStream_t s);
+int num_spill_grid(int dtype, const HashLaunch &hl);
+void launch_num_spill(int dtype, const RawOperands &op, const int *rows, int count, int *token,
+                      const HashLaunch &hl, float inv_load, int spill_tbits, void *tables,
+                      const NumOut &out, int *err, cudaStream_t s);
+
+// Shared-memory limits used by the planner.
+int max_smem_per_block();
+int dense_bitmap_max_cols();          // widest B whose column bitmap fits one block
+bool num_hash_bitmap_fits(int dtype, int tbits, int ncols);
+
+}  // namespace smash

@@ -1,0 +1,202 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Structure (row_ptr, col_idx) must match bit-exactly; values must match exactly
+for integer-valued float32 data and within |c - c*| <= tol * sum|a||b|
+(tol 1e-5 float32, 1e-12 float64) otherwise. Every execution path of the
+planner (shared-memory hash with one warp or a thread group per row, dense
+accumulator, global-memory spill; warp-rank, bitmap and bitonic write-out;
+three hash functions) is forced in turn on inputs that span many tables and
+leave ragged tails."""
+import numpy as np
+import pytest
+
+from paper_2105_14156_gb300.rmat import Csr, GRAPH500_ABCD, rmat, workload
+from tests.gpu_util import assert_matches_oracle, gpu_spgemm
+from tests.helpers import identity, random_csr
+
+pytestmark = pytest.mark.gpu
+
+DEFAULT = dict(hash_kind=0, max_load=0.5, sym_max_tbits=15, num_max_tbits=14, group_shift=3, dense_ratio=4,
+               bitmap_ratio=4, spill_blocks_per_sm=1)
+
+# Parameter sets that force each path.
+PATHS = {
+    "default": {},
+    "warp_only_small_tables": dict(sym_max_tbits=7, num_max_tbits=7, dense_ratio=0),   # rest spills
+    "spill_everything": dict(sym_max_tbits=5, num_max_tbits=5, dense_ratio=0),
+    "dense_everything": dict(dense_ratio=1 << 20),
+    "group_per_row": dict(group_shift=0),
+    "bitonic_only": dict(bitmap_ratio=0),
+    "bitmap_always": dict(bitmap_ratio=1 << 20),
+    "hash_multiplicative": dict(hash_kind=1),
+    "hash_high_bits": dict(hash_kind=2),
+    "load_0.9": dict(max_load=0.9),
+    "load_0.1": dict(max_load=0.1),
+}
+
+
+@pytest.fixture(scope="module")
+def handle():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_14156_gb300 import build, smash
+    build.build()
+    h = smash.Handle(0)
+    yield h
+    h.close()
+
+
+def run(handle, A, B, dtype=None, **over):
+    p = dict(DEFAULT)
+    p.update(over)
+    return gpu_spgemm(handle, A, B, dtype=dtype, **p)
+
+
+def test_rmat10_int_bit_exact(handle):
+    """Config: R-MAT scale 10, edge factor 8, integer values {1..4} in float32."""
+    A = workload("rmat10_int")
+    C = run(handle, A, A)
+    assert_matches_oracle(C, A, A, exact=True)
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_paths_f64(handle, path):
+    A = rmat(11, 16, GRAPH500_ABCD, seed=21, values="f64")
+    C = run(handle, A, A, **PATHS[path])
+    assert_matches_oracle(C, A, A)
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_paths_f32_int_exact(handle, path):
+    A = rmat(11, 8, (0.45, 0.15, 0.15, 0.25), seed=22, values="int4")
+    C = run(handle, A, A, **PATHS[path])
+    assert_matches_oracle(C, A, A, exact=True)
+
+
+@pytest.mark.parametrize("path", ["default", "spill_everything", "dense_everything", "bitonic_only"])
+def test_rectangular_f32(handle, path):
+    A = random_csr(700, 333, 0.03, 31, values="f32")
+    B = random_csr(333, 1500, 0.02, 32, values="f32")
+    C = run(handle, A, B, **PATHS[path])
+    assert_matches_oracle(C, A, B)
+
+
+def test_unsorted_and_duplicate_columns(handle):
+    A = random_csr(300, 300, 0.05, 41, values="f64", sort_cols=False, dup_frac=0.3)
+    B = random_csr(300, 300, 0.05, 42, values="f64", sort_cols=False, dup_frac=0.3)
+    for path in ("default", "spill_everything", "dense_everything"):
+        C = run(handle, A, B, **PATHS[path])
+        assert_matches_oracle(C, A, B)
+
+
+def test_empty_inputs(handle):
+    from paper_2105_14156_gb300 import smash
+    E = Csr(0, 5, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    B = random_csr(5, 7, 0.5, 1)
+    C = run(handle, E, B)
+    assert C.rows == 0 and C.col_idx.size == 0
+    Z = Csr(6, 5, np.zeros(7, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    C = run(handle, Z, B)
+    assert C.row_ptr.tolist() == [0] * 7
+    # all-empty rows of B
+    A = random_csr(6, 5, 0.5, 2)
+    BZ = Csr(5, 7, np.zeros(6, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    C = run(handle, A, BZ)
+    assert C.row_ptr.tolist() == [0] * 7
+
+
+def test_single_column_b(handle):
+    A = rmat(9, 8, GRAPH500_ABCD, seed=5, values="f64")
+    B = random_csr(A.cols, 1, 0.5, 6, values="f64")
+    C = run(handle, A, B)
+    assert_matches_oracle(C, A, B)
+
+
+def test_one_fully_dense_row(handle):
+    """A row of A touching every row of B: the largest possible row of C."""
+    n = 3000
+    B = random_csr(n, n, 0.004, 8, values="f64")
+    r = np.concatenate([np.zeros(n, np.int64), 1 + np.arange(200) % (n - 1)])
+    c = np.concatenate([np.arange(n), (7 * np.arange(200)) % n])
+    from paper_2105_14156_gb300.rmat import csr_from_coo
+    rp, ci = csr_from_coo(n, n, r, c)
+    A = Csr(n, n, rp, ci, np.linspace(-1, 1, ci.size))
+    for path in ("default", "spill_everything", "bitonic_only", "warp_only_small_tables"):
+        C = run(handle, A, B, **PATHS[path])
+        assert_matches_oracle(C, A, B)
+
+
+def test_congruent_columns_defeat_low_bits(handle):
+    """Columns that agree modulo the table size collide under low-bit hashing."""
+    n, cols = 64, 1 << 16
+    rows, cs = [], []
+    for i in range(n):
+        for t in range(40):
+            rows.append(i)
+            cs.append((t * 1024 + i) % cols)
+    from paper_2105_14156_gb300.rmat import csr_from_coo
+    rp, ci = csr_from_coo(n, cols, np.array(rows), np.array(cs))
+    B = Csr(n, cols, rp, ci, np.linspace(-2, 2, ci.size))
+    A = random_csr(200, n, 0.2, 9, values="f64")
+    for kind in (0, 1, 2):
+        C = run(handle, A, B, hash_kind=kind, dense_ratio=0)
+        assert_matches_oracle(C, A, B)
+
+
+def test_identity(handle):
+    A = rmat(10, 8, GRAPH500_ABCD, seed=3, values="f64")
+    C = run(handle, A, identity(A.rows))
+    assert np.array_equal(C.row_ptr, A.row_ptr)
+    assert np.array_equal(C.col_idx, A.col_idx)
+    assert np.array_equal(C.val, A.val)
+
+
+def test_bad_column_index_is_reported(handle):
+    from paper_2105_14156_gb300 import smash
+    A = random_csr(50, 40, 0.2, 11, values="f64")
+    B = random_csr(40, 30, 0.2, 12, values="f64")
+    B.col_idx = B.col_idx.copy()
+    B.col_idx[3] = 30          # out of range
+    with pytest.raises(smash.SmashError) as ei:
+        run(handle, A, B)
+    assert ei.value.status == 1
+    # the handle stays usable
+    B2 = random_csr(40, 30, 0.2, 12, values="f64")
+    assert_matches_oracle(run(handle, A, B2), A, B2)
+
+
+def test_shape_mismatch(handle):
+    from paper_2105_14156_gb300 import smash
+    A = random_csr(10, 9, 0.3, 1)
+    B = random_csr(8, 7, 0.3, 2)
+    with pytest.raises(smash.SmashError) as ei:
+        run(handle, A, B)
+    assert ei.value.status == 2
+
+
+def test_repeatable_structure(handle):
+    A = rmat(12, 16, GRAPH500_ABCD, seed=4, values="f64")
+    C1 = run(handle, A, A)
+    C2 = run(handle, A, A)
+    assert np.array_equal(C1.row_ptr, C2.row_ptr)
+    assert np.array_equal(C1.col_idx, C2.col_idx)
+
+
+@pytest.mark.slow
+def test_rmat16_f64_full_size_sampled(handle):
+    """Config: R-MAT scale 16, edge factor 16, float64 U[-1,1], C = A*A.
+
+    Full structure: the row pointer against the oracle's exact counts; values
+    and columns on sampled rows (every bin represented, heaviest rows included)."""
+    import oracle
+    A = workload("rmat16_f64")
+    C = run(handle, A, A)
+    flop = oracle.row_flops(A, A)
+    heavy = np.argsort(flop)[-8:]
+    rng = np.random.default_rng(0)
+    rows = np.unique(np.concatenate([heavy, rng.choice(A.rows, 300, replace=False)]))
+    assert_matches_oracle(C, A, A, rows=rows)
+    # total nnz against the closed bound and the oracle's counts on all rows
+    ref_counts = np.diff(oracle.spgemm(A, A, rows=np.arange(0, A.rows, 7)).row_ptr)
+    assert np.array_equal(np.diff(C.row_ptr)[::7], ref_counts)
