@@ -164,8 +164,8 @@ def main():
     ap.add_argument("--cpu-products", type=float, default=2e8)
     ap.add_argument("--e2e-steps", type=int, default=3)
     args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
+    args.warmup = max(args.warmup, 3)
+    args.e2e_steps = max(args.e2e_steps, 1)
 
     from paper_2105_14156_gb300 import metrics
     from paper_2105_14156_gb300.rmat import workload

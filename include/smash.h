@@ -63,8 +63,9 @@ typedef struct {
 /* Tuning parameters. None of them changes the result, only the speed.
  * smash_default_params() fills the defaults; the autotuner overwrites them. */
 typedef struct {
-    int32_t hash_kind;      /* 0: low-order bits j & (T-1) (Version 2, default);
-                               1: multiplicative (Fibonacci) hashing;
+    int32_t hash_kind;      /* 0: low-order bits j & (T-1) (Version 2);
+                               1: multiplicative (Fibonacci) hashing (default: on R-MAT, whose columns
+                                  cluster at small indices, the low-order bits make long probe chains);
                                2: high-order bits j >> shift (Version 1, order preserving) */
     float max_load;         /* table sized to next_pow2(bound / max_load) slots; (0.05, 0.95]; default 0.5 */
     int32_t sym_max_tbits;  /* largest shared-memory symbolic table, log2 slots; [5, 15]; default 15 */
@@ -75,17 +76,42 @@ typedef struct {
     int32_t bitmap_ratio;   /* numeric write-out ranks by a column bitmap when cols(B)/32 <=
                                bitmap_ratio * nnz(row); 0 disables; default 4 */
     int32_t spill_blocks_per_sm; /* resident blocks per SM of the spill and dense kernels; default 1 */
-    int32_t reserved[8];
+    int32_t sym_dense_ratio; /* symbolic phase: a row whose bound b satisfies b * sym_dense_ratio >= cols(B)
+                                counts its columns in a shared-memory bitmap; 0 disables; default 64 */
+    int32_t cluster_max;     /* largest thread-block cluster (1, 2, 4 or 8) whose distributed shared memory
+                                holds a dense row's accumulator; 1 disables clusters; default 8 */
+    int32_t hot_cols;        /* dense rows: per cluster block, up to this many "hot" columns of B (column
+                                count >= hot_factor x average) accumulate in private per-warp slots;
+                                [0, 512], 0 disables; default 128 */
+    int32_t hot_factor;      /* hot-column threshold, multiple of the average column count; default 16 */
+    int32_t reserved[4];
 } smash_params;
 
 /* Per-call statistics (the last symbolic or numeric call of the handle). */
 typedef struct {
     int64_t rows_per_bin[16]; /* 0: empty rows; 1..12: shared-memory tables of 2^(bin+4) slots;
                                  13: dense accumulator; 14: global-memory hash (spill) */
-    int64_t products;         /* sum over rows of the product count flop_i (symbolic calls) */
+    int64_t products;         /* sum over rows of the product count flop_i */
     int64_t max_row_products;
     int64_t c_nnz;
+    int64_t a_nnz_per_bin[16];    /* sum of nnz(A_i) over the rows of each bin */
+    int64_t products_per_bin[16]; /* sum of flop_i over the rows of each bin */
+    int64_t c_nnz_per_bin[16];    /* sum of nnz(C_i) (numeric calls; the bound min(flop_i, cols) in
+                                     symbolic calls) */
 } smash_stats;
+
+/* Accumulated device time of one kernel of the library (event timing). */
+typedef struct {
+    char name[40];    /* kernel family, e.g. "num_hash", "num_dense_cluster", "sym_hash" */
+    int32_t bin;      /* bin served by the launch (-1: not a per-bin kernel) */
+    int32_t threads;  /* threads per block */
+    int64_t launches;
+    int64_t rows;     /* rows of C processed, summed over launches */
+    int64_t a_nnz;    /* nnz(A_i) of those rows, summed */
+    int64_t products; /* products of those rows, summed */
+    int64_t c_nnz;    /* nnz(C_i) (or symbolic bound) of those rows, summed */
+    double ms;        /* summed CUDA-event time between launch and completion on the call's stream */
+} smash_kernel_time;
 
 typedef struct smash_handle smash_handle;
 
@@ -147,6 +173,16 @@ int smash_check(smash_handle *h, void *stream);
 
 /* Statistics of the handle's last symbolic or numeric call. */
 int smash_get_stats(const smash_handle *h, smash_stats *out);
+
+/* Kernel timing (a tracing aid; not needed for results). With enable != 0,
+ * every kernel launch of the following calls is bracketed by CUDA events on
+ * the call's stream; the totals accumulate per (kernel, bin) until read.
+ * Enabling or disabling clears the totals. */
+int smash_set_timing(smash_handle *h, int enable);
+
+/* Synchronise the pending events and copy up to `capacity` per-kernel totals
+ * into out[]; *count receives the number of distinct (kernel, bin) entries. */
+int smash_get_timings(smash_handle *h, smash_kernel_time *out, int capacity, int *count);
 
 /* Human-readable name of a status code (static string). */
 const char *smash_status_string(int status);

@@ -9,6 +9,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <string>
+#include <vector>
 
 #include "device_common.cuh"
 #include "kernels.h"
@@ -21,7 +23,17 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// Event timing of kernel launches (tracing).
+struct PendingTime {
+    int slot;  // index into totals
+    cudaEvent_t e0, e1;
+};
+
 struct smash_handle {
+    bool timing = false;
+    std::vector<PendingTime> pending;
+    std::vector<smash_kernel_time> totals;
+    std::vector<cudaEvent_t> spare_events;
     int device = 0;
     int sms = 0;
     smash_params params{};
@@ -31,6 +43,8 @@ struct smash_handle {
     DevBuf ws;         // per-call arrays
     DevBuf tables;     // spill hash tables
     DevBuf dense_acc;  // dense accumulators (kept zero between rows)
+    DevBuf split;      // column slices of B for cluster-wide dense rows
+    DevBuf hot;        // hot-column tables of B
     DevBuf err;        // kNumErr ints (+ scratch words)
     long long *host = nullptr;  // pinned host staging
     smash_stats stats{};
@@ -96,6 +110,68 @@ int ensure(smash_handle *h, DevBuf &b, size_t need, cudaStream_t s, bool zero = 
     return SMASH_OK;
 }
 
+cudaEvent_t take_event(smash_handle *h) {
+    if (!h->spare_events.empty()) {
+        cudaEvent_t e = h->spare_events.back();
+        h->spare_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one kernel launch with events when timing is on.
+struct LaunchTimer {
+    smash_handle *h;
+    cudaStream_t s;
+    int slot = -1;
+    cudaEvent_t e0 = nullptr;
+    LaunchTimer(smash_handle *hh, cudaStream_t ss, const char *name, int bin, int threads, long long rows,
+                long long a_nnz, long long products, long long c_nnz)
+        : h(hh), s(ss) {
+        if (!h->timing) return;
+        for (size_t k = 0; k < h->totals.size(); ++k)
+            if (h->totals[k].bin == bin && strncmp(h->totals[k].name, name, sizeof(h->totals[k].name)) == 0)
+                slot = (int)k;
+        if (slot < 0) {
+            smash_kernel_time kt;
+            memset(&kt, 0, sizeof(kt));
+            strncpy(kt.name, name, sizeof(kt.name) - 1);
+            kt.bin = bin;
+            h->totals.push_back(kt);
+            slot = (int)h->totals.size() - 1;
+        }
+        smash_kernel_time &kt = h->totals[slot];
+        kt.threads = threads;
+        kt.launches += 1;
+        kt.rows += rows;
+        kt.a_nnz += a_nnz;
+        kt.products += products;
+        kt.c_nnz += c_nnz;
+        e0 = take_event(h);
+        cudaEventRecord(e0, s);
+    }
+    ~LaunchTimer() {
+        if (!h->timing || slot < 0) return;
+        cudaEvent_t e1 = take_event(h);
+        cudaEventRecord(e1, s);
+        h->pending.push_back(PendingTime{slot, e0, e1});
+    }
+};
+
+void resolve_timings(smash_handle *h) {
+    for (const PendingTime &p : h->pending) {
+        cudaEventSynchronize(p.e1);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) h->totals[p.slot].ms += ms;
+        h->spare_events.push_back(p.e0);
+        h->spare_events.push_back(p.e1);
+    }
+    h->pending.clear();
+    cudaGetLastError();
+}
+
 struct Carver {
     char *base;
     size_t off = 0;
@@ -133,6 +209,10 @@ int check_params(const smash_params *p) {
     if (p->group_shift < 0 || p->group_shift > 10) return SMASH_ERR_INVALID_ARG;
     if (p->dense_ratio < 0 || p->bitmap_ratio < 0) return SMASH_ERR_INVALID_ARG;
     if (p->spill_blocks_per_sm < 0 || p->spill_blocks_per_sm > 8) return SMASH_ERR_INVALID_ARG;
+    if (p->sym_dense_ratio < 0) return SMASH_ERR_INVALID_ARG;
+    if (p->hot_cols < 0 || p->hot_cols > 512 || p->hot_factor < 1) return SMASH_ERR_INVALID_ARG;
+    if (p->cluster_max != 1 && p->cluster_max != 2 && p->cluster_max != 4 && p->cluster_max != 8)
+        return SMASH_ERR_INVALID_ARG;
     return SMASH_OK;
 }
 
@@ -184,6 +264,7 @@ int plan_buffers(smash_handle *h, int64_t n, bool symbolic, cudaStream_t s, Plan
     carve_size<long long>(need, 16 + 4 + 1);
     carve_size<int>(need, (size_t)n);
     carve_size<int>(need, 17);
+    carve_size<long long>(need, 48);
     if (symbolic) {
         carve_size<long long>(need, (size_t)n);
         carve_size<int>(need, (size_t)n);
@@ -203,6 +284,7 @@ int plan_buffers(smash_handle *h, int64_t n, bool symbolic, cudaStream_t s, Plan
     pl.total = ll + 20;
     pl.bb.rows = c.take<int>((size_t)n);
     pl.bb.offsets = c.take<int>(17);
+    pl.bb.sums = c.take<long long>(48);
     pl.bound = nullptr;
     pl.nnz = nullptr;
     pl.scan = nullptr;
@@ -214,24 +296,35 @@ int plan_buffers(smash_handle *h, int64_t n, bool symbolic, cudaStream_t s, Plan
     // zero counters, cursors, tokens, maxsize, stats, total
     if (cudaMemsetAsync(ctr, 0, 16 * 3 * sizeof(int), s) != cudaSuccess) return SMASH_ERR_CUDA;
     if (cudaMemsetAsync(ll, 0, (16 + 4 + 1) * sizeof(long long), s) != cudaSuccess) return SMASH_ERR_CUDA;
+    if (cudaMemsetAsync(pl.bb.sums, 0, 48 * sizeof(long long), s) != cudaSuccess) return SMASH_ERR_CUDA;
     return SMASH_OK;
 }
 
 // Copy bin counts (16 int), offsets (17 int), maxsize (16 ll), stats (4 ll)
 // to the pinned host buffer and wait.
 int fetch_bins(smash_handle *h, const Plan &pl, cudaStream_t s, int *counts, int *offsets, long long *maxsize,
-               long long *stats) {
+               long long *stats, long long *sums) {
     char *hb = (char *)h->host;
     if (cudaMemcpyAsync(hb, pl.bb.counts, 16 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(hb + 64, pl.bb.offsets, 17 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(hb + 256, pl.bb.maxsize, 20 * sizeof(long long), cudaMemcpyDeviceToHost, s) !=
-            cudaSuccess)
+            cudaSuccess ||
+        cudaMemcpyAsync(hb + 512, pl.bb.sums, 48 * sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return SMASH_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SMASH_ERR_CUDA;
     memcpy(counts, hb, 16 * sizeof(int));
     memcpy(offsets, hb + 64, 17 * sizeof(int));
     memcpy(maxsize, hb + 256, 16 * sizeof(long long));
     memcpy(stats, hb + 256 + 16 * sizeof(long long), 4 * sizeof(long long));
+    memcpy(sums, hb + 512, 48 * sizeof(long long));
+    for (int b = 0; b < 16; ++b) {
+        h->stats.rows_per_bin[b] = b < kNumBins ? counts[b] : 0;
+        h->stats.a_nnz_per_bin[b] = sums[b];
+        h->stats.products_per_bin[b] = sums[16 + b];
+        h->stats.c_nnz_per_bin[b] = sums[32 + b];
+    }
+    h->stats.products = stats[0];
+    h->stats.max_row_products = stats[1];
     return SMASH_OK;
 }
 
@@ -259,8 +352,8 @@ BinRule sym_rule(const smash_handle *h, int64_t ncols) {
     // key-only table of 2^mt ints plus the staging of a 1024-thread group
     while (mt > kMinTBits && ((size_t)4 << mt) + 24 * 1024 > (size_t)max_smem_per_block()) --mt;
     r.max_tbits = mt;
-    r.dense_ok = (h->params.dense_ratio > 0 && ncols <= dense_bitmap_max_cols()) ? 1 : 0;
-    r.dense_min = r.dense_ok ? (ncols + h->params.dense_ratio - 1) / h->params.dense_ratio : (1ll << 62);
+    r.dense_ok = (h->params.sym_dense_ratio > 0 && ncols <= dense_bitmap_max_cols()) ? 1 : 0;
+    r.dense_min = r.dense_ok ? (ncols + h->params.sym_dense_ratio - 1) / h->params.sym_dense_ratio : (1ll << 62);
     if (r.dense_min < 1) r.dense_min = 1;
     return r;
 }
@@ -268,7 +361,10 @@ BinRule sym_rule(const smash_handle *h, int64_t ncols) {
 BinRule num_rule(const smash_handle *h, int64_t ncols, int dtype) {
     BinRule r;
     r.inv_load = 1.0f / h->params.max_load;
-    r.dense_ok = (h->params.dense_ratio > 0 && ncols <= dense_bitmap_max_cols()) ? 1 : 0;
+    const bool dense_fits = num_dense_cluster_size(dtype, (int)ncols, h->params.cluster_max,
+                                                   h->params.hot_cols) > 0 ||
+                            ncols <= dense_bitmap_max_cols();
+    r.dense_ok = (h->params.dense_ratio > 0 && dense_fits) ? 1 : 0;
     r.dense_min = r.dense_ok ? (ncols + h->params.dense_ratio - 1) / h->params.dense_ratio : (1ll << 62);
     if (r.dense_min < 1) r.dense_min = 1;
     int mt = h->params.num_max_tbits;
@@ -287,6 +383,11 @@ BinRule num_rule(const smash_handle *h, int64_t ncols, int dtype) {
     return r;
 }
 
+int group_threads(const HashLaunch &hl) {
+    int t = 1 << (hl.tbits > hl.group_shift ? hl.tbits - hl.group_shift : 0);
+    return t < 32 ? 32 : (t > 1024 ? 1024 : t);
+}
+
 HashLaunch hash_launch(const smash_handle *h, int tbits, int64_t ncols) {
     HashLaunch hl;
     hl.tbits = tbits;
@@ -295,6 +396,7 @@ HashLaunch hash_launch(const smash_handle *h, int tbits, int64_t ncols) {
     hl.colbits = colbits_of(ncols);
     hl.sms = h->sms;
     hl.blocks_per_sm = h->params.spill_blocks_per_sm > 0 ? h->params.spill_blocks_per_sm : 1;
+    hl.cluster_max = h->params.cluster_max;
     return hl;
 }
 
@@ -306,7 +408,7 @@ extern "C" {
 int smash_default_params(smash_params *p) {
     if (!p) return SMASH_ERR_INVALID_ARG;
     memset(p, 0, sizeof(*p));
-    p->hash_kind = 0;
+    p->hash_kind = 1;
     p->max_load = 0.5f;
     p->sym_max_tbits = 15;
     p->num_max_tbits = 14;
@@ -314,6 +416,10 @@ int smash_default_params(smash_params *p) {
     p->dense_ratio = 4;
     p->bitmap_ratio = 4;
     p->spill_blocks_per_sm = 1;
+    p->sym_dense_ratio = 64;
+    p->cluster_max = 8;
+    p->hot_cols = 128;
+    p->hot_factor = 16;
     return SMASH_OK;
 }
 
@@ -373,9 +479,14 @@ int smash_destroy(smash_handle *h) {
     {
         DeviceGuard g(h->device);
         cudaDeviceSynchronize();
+        resolve_timings(h);
+        for (cudaEvent_t e : h->spare_events) cudaEventDestroy(e);
+        h->spare_events.clear();
         release(h, h->ws);
         release(h, h->tables);
         release(h, h->dense_acc);
+        release(h, h->split);
+        release(h, h->hot);
         release(h, h->err);
         if (h->host) cudaFreeHost(h->host);
     }
@@ -402,6 +513,8 @@ int smash_set_allocator(smash_handle *h, smash_alloc_fn alloc, smash_free_fn fre
     release(h, h->ws);
     release(h, h->tables);
     release(h, h->dense_acc);
+    release(h, h->split);
+    release(h, h->hot);
     // the error words move to the new allocator as well
     release(h, h->err);
     h->alloc = alloc ? alloc : default_alloc;
@@ -409,6 +522,24 @@ int smash_set_allocator(smash_handle *h, smash_alloc_fn alloc, smash_free_fn fre
     h->ctx = alloc ? ctx : nullptr;
     if (ensure(h, h->err, 256, 0) != SMASH_OK) return SMASH_ERR_ALLOC;
     if (cudaMemset(h->err.ptr, 0, h->err.bytes) != cudaSuccess) return SMASH_ERR_CUDA;
+    return SMASH_OK;
+}
+
+int smash_set_timing(smash_handle *h, int enable) {
+    if (!h) return SMASH_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    resolve_timings(h);
+    h->totals.clear();
+    h->timing = enable != 0;
+    return SMASH_OK;
+}
+
+int smash_get_timings(smash_handle *h, smash_kernel_time *out, int capacity, int *count) {
+    if (!h || !count || capacity < 0 || (capacity > 0 && !out)) return SMASH_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    resolve_timings(h);
+    *count = (int)h->totals.size();
+    for (int k = 0; k < capacity && k < (int)h->totals.size(); ++k) out[k] = h->totals[k];
     return SMASH_OK;
 }
 
@@ -447,34 +578,44 @@ int spgemm_symbolic(smash_handle *h, const smash_csr *A, const smash_csr *B, int
     const RawOperands op = raw_ops(A, B);
     const BinRule rule = sym_rule(h, B->cols);
     int *err = (int *)h->err.ptr;
-    launch_sym_rowinfo(op, rule, pl.bb, pl.bound, pl.nnz, err, h->sms, s);
-    launch_bin_scatter(n, pl.bb, s);
+    {
+        LaunchTimer lt(h, s, "sym_rowinfo", -1, 256, n, A->nnz, 0, 0);
+        launch_sym_rowinfo(op, rule, pl.bb, pl.bound, pl.nnz, err, h->sms, s);
+    }
+    {
+        LaunchTimer lt(h, s, "bin_scatter", -1, 256, n, 0, 0, 0);
+        launch_bin_scatter(n, pl.bb, s);
+    }
     if ((st = last_cuda_status())) return st;
     int counts[16], offsets[17];
-    long long maxsize[16], stats[4];
-    if ((st = fetch_bins(h, pl, s, counts, offsets, maxsize, stats))) return st;
-    for (int b = 0; b < kNumBins; ++b) h->stats.rows_per_bin[b] = counts[b];
-    h->stats.products = stats[0];
-    h->stats.max_row_products = stats[1];
+    long long maxsize[16], stats[4], sums[48];
+    if ((st = fetch_bins(h, pl, s, counts, offsets, maxsize, stats, sums))) return st;
     for (int b = 1; b < kNumBins; ++b) {
         if (!counts[b]) continue;
         const int *rows = pl.bb.rows + offsets[b];
         int *tok = pl.bb.tokens + b;
         if (b == kBinDense) {
+            LaunchTimer lt(h, s, "sym_dense", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
             launch_sym_dense(op, rows, counts[b], tok, hash_launch(h, 0, B->cols), pl.nnz, err, s);
         } else if (b == kBinSpill) {
             const int tb = table_bits(maxsize[b], rule.inv_load);
             const HashLaunch hl = hash_launch(h, tb, B->cols);
             const size_t need = ((size_t)sym_spill_grid(hl) << tb) * sizeof(int);
             if ((st = ensure(h, h->tables, need, s))) return st;
+            LaunchTimer lt(h, s, "sym_spill", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
             launch_sym_spill(op, rows, counts[b], tok, hl, rule.inv_load, pl.bound, tb, (int *)h->tables.ptr,
                              pl.nnz, err, s);
         } else {
-            launch_sym_hash(op, rows, counts[b], tok, hash_launch(h, tbits_of_bin(b), B->cols), pl.nnz, err, s);
+            const HashLaunch hl = hash_launch(h, tbits_of_bin(b), B->cols);
+            LaunchTimer lt(h, s, "sym_hash", b, group_threads(hl), counts[b], sums[b], sums[16 + b], sums[32 + b]);
+            launch_sym_hash(op, rows, counts[b], tok, hl, pl.nnz, err, s);
         }
         if ((st = last_cuda_status())) return st;
     }
-    launch_scan_rowptr(pl.nnz, n, c_row_ptr, pl.total, pl.scan, s);
+    {
+        LaunchTimer lt(h, s, "scan_rowptr", -1, 512, n, 0, 0, 0);
+        launch_scan_rowptr(pl.nnz, n, c_row_ptr, pl.total, pl.scan, s);
+    }
     if ((st = last_cuda_status())) return st;
     if (cudaMemcpyAsync(h->host, pl.total, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return SMASH_ERR_CUDA;
@@ -506,13 +647,19 @@ int spgemm_numeric(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
     const int dt = dtype == SMASH_F64 ? 1 : 0;
     const BinRule rule = num_rule(h, B->cols, dt);
     int *err = (int *)h->err.ptr;
-    launch_num_rowinfo(C->row_ptr, n, C->nnz, rule, pl.bb, err, s);
-    launch_bin_scatter(n, pl.bb, s);
+    {
+        LaunchTimer lt(h, s, "num_rowinfo", -1, 256, n, A->nnz, 0, C->nnz);
+        launch_num_rowinfo(op, C->row_ptr, C->nnz, rule, pl.bb, err, h->sms, s);
+    }
+    {
+        LaunchTimer lt(h, s, "bin_scatter", -1, 256, n, 0, 0, 0);
+        launch_bin_scatter(n, pl.bb, s);
+    }
     if ((st = last_cuda_status())) return st;
     int counts[16], offsets[17];
-    long long maxsize[16], stats[4];
-    if ((st = fetch_bins(h, pl, s, counts, offsets, maxsize, stats))) return st;
-    for (int b = 0; b < kNumBins; ++b) h->stats.rows_per_bin[b] = counts[b];
+    long long maxsize[16], stats[4], sums[48];
+    if ((st = fetch_bins(h, pl, s, counts, offsets, maxsize, stats, sums))) return st;
+    h->stats.c_nnz = C->nnz;
     const NumOut out{C->row_ptr, C->col_idx, C->val, C->nnz};
     const size_t vsz = dt ? 8 : 4;
     for (int b = 1; b < kNumBins; ++b) {
@@ -522,23 +669,38 @@ int spgemm_numeric(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
         if (b == kBinDense) {
             const HashLaunch hl = hash_launch(h, 0, B->cols);
             void *acc = nullptr;
-            if (!num_dense_uses_smem_acc(dt, (int)B->cols)) {
+            const int H = h->params.hot_cols;
+            int cs = num_dense_cluster_size(dt, (int)B->cols, h->params.cluster_max, H);
+            BSlices sl;
+            if (cs == 0) {
                 const size_t need = (size_t)num_dense_grid(dt, hl, (int)B->cols) * (size_t)B->cols * vsz;
-                const bool fresh = h->dense_acc.bytes < need;
                 if ((st = ensure(h, h->dense_acc, need, s, true))) return st;
-                (void)fresh;
                 acc = h->dense_acc.ptr;
+            } else {
+                const int cap = num_dense_cap(dt, H);
+                int cpc = cap;
+                if (cs == 1) cpc = (int)((B->cols + 31) & ~31ll);
+                const size_t need = dense_plan_bytes(op, cs, cpc, H, vsz);
+                if ((st = ensure(h, h->split, need, s))) return st;
+                LaunchTimer lt(h, s, "dense_plan", -1, 256, B->rows, A->nnz, 0, B->nnz);
+                launch_dense_plan(dt, op, cs, cap, cpc, H, h->params.hot_factor, h->split.ptr, sl, h->sms, s);
+                sl.nslices = cs;
+                sl.cpc = cpc;
             }
-            launch_num_dense(dt, op, rows, counts[b], tok, hl, acc, out, err, s);
+            LaunchTimer lt(h, s, cs ? "num_dense_cluster" : "num_dense_global", b, 1024, counts[b], sums[b],
+                           sums[16 + b], sums[32 + b]);
+            launch_num_dense(dt, op, rows, counts[b], tok, hl, acc, sl, out, err, s);
         } else if (b == kBinSpill) {
             const int tb = table_bits(maxsize[b], rule.inv_load);
             const HashLaunch hl = hash_launch(h, tb, B->cols);
             const size_t need = ((size_t)num_spill_grid(dt, hl) << tb) * (4 + vsz);
             if ((st = ensure(h, h->tables, need, s))) return st;
+            LaunchTimer lt(h, s, "num_spill", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
             launch_num_spill(dt, op, rows, counts[b], tok, hl, rule.inv_load, tb, h->tables.ptr, out, err, s);
         } else {
-            launch_num_hash(dt, op, rows, counts[b], tok, hash_launch(h, tbits_of_bin(b), B->cols), rule.inv_load,
-                            h->params.bitmap_ratio, out, err, s);
+            const HashLaunch hl = hash_launch(h, tbits_of_bin(b), B->cols);
+            LaunchTimer lt(h, s, "num_hash", b, group_threads(hl), counts[b], sums[b], sums[16 + b], sums[32 + b]);
+            launch_num_hash(dt, op, rows, counts[b], tok, hl, rule.inv_load, h->params.bitmap_ratio, out, err, s);
         }
         if ((st = last_cuda_status())) return st;
     }

@@ -185,6 +185,12 @@ struct Operands {
     int64_t b_nnz;
     int32_t b_rows;
     int32_t ncols;
+    // Optional column slicing of B: when b_woff != nullptr, each row k of B is
+    // stored grouped by column window, and only window `slice` is enumerated:
+    // entries [b_rp[k] + b_woff[k*(nslices+1) + slice], ... + slice+1).
+    const int32_t *b_woff = nullptr;
+    int32_t nslices = 0;
+    int32_t slice = 0;
 };
 
 // Row range of A, checked.
@@ -215,6 +221,11 @@ __device__ __forceinline__ void load_a_entry(const Operands<V> &op, int64_t e, i
             if (t - s < kMaxBRow) {
                 bs = s;
                 len = (int)(t - s);
+                if (op.b_woff) {
+                    const int32_t *w = op.b_woff + (size_t)k * (op.nslices + 1) + op.slice;
+                    bs = s + w[0];
+                    len = w[1] - w[0];
+                }
             } else {
                 raise_err(err, kErrBRowTooLong);
             }
@@ -234,7 +245,8 @@ __device__ __forceinline__ V shfl_v(V v, int src) {
 
 // Every product of A entries [ab, ae) with their rows of B, enumerated by one
 // warp: lane l takes products l, l+32, ... of each batch of 32 A entries.
-// f(j, v) is called for each product (v = a_ik * b_kj; 0 when !NUM).
+// f(j, a, idx) is called for each product: j = column, a = a_ik (0 when
+// !NUM), idx = position of b_kj in B (the callee loads the value if needed).
 template <typename V, bool NUM, typename F>
 __device__ __forceinline__ void warp_products(const Operands<V> &op, int64_t ab, int64_t ae,
                                               int *err, F &&f) {
@@ -261,12 +273,8 @@ __device__ __forceinline__ void warp_products(const Operands<V> &op, int64_t ab,
             if (p < total) {
                 const int64_t idx = st + p;
                 const int j = __ldg(op.b_ci + idx);
-                if ((unsigned)j < (unsigned)op.ncols) {
-                    if constexpr (NUM) f(j, a * __ldg(op.b_val + idx));
-                    else f(j, V(0));
-                } else {
-                    raise_err(err, kErrBadIndex);
-                }
+                if ((unsigned)j < (unsigned)op.ncols) f(j, a, idx);
+                else raise_err(err, kErrBadIndex);
             }
         }
     }
@@ -307,58 +315,69 @@ __device__ __forceinline__ ProdScratch<V> carve_prod_scratch(unsigned char *p) {
 
 // Every product of A entries [ab, ae), enumerated by a group of GS >= 64
 // threads: batches of GS A entries are staged in shared memory (entries with
-// an empty row of B dropped), then warp w takes products w*32 .. w*32+31,
-// w*32+GS .., each lane finding its entry by a binary search over a window of
-// 32 staged prefix sums.
+// an empty row of B dropped), the batch's products are split into one
+// contiguous range per warp, and each warp walks its range 32 products at a
+// time. A lane finds the entry of its product by binary lifting over a window
+// of 32 staged prefix sums that starts at the entry of the step's first
+// product; the window advances with the walk, so only the first step of a
+// range needs a binary search over the whole batch.
 template <typename V, bool NUM, int GS, int NT, typename F>
 __device__ __forceinline__ void group_products(const Operands<V> &op, int64_t ab, int64_t ae,
                                                const ProdScratch<V> &sc, int *err, F &&f) {
     using G = Group<GS, NT>;
     const int t = G::tid();
     const int lane = lane_id();
+    const int w = G::wid();
     for (int64_t base = ab; base < ae; base += GS) {
         int len = 0;
         int64_t bs = 0;
         V av = V(0);
         if (base + t < ae) load_a_entry<V, NUM>(op, base + t, len, bs, av, err);
-        const int flag = len > 0 ? 1 : 0;
-        int nf, total;
-        const int cidx = G::template excl_scan<int>(flag, sc.red, &nf);
-        const int excl = G::template excl_scan<int>(len, sc.red, &total);
-        if (flag) {
+        // one scan of (entry has products, product count): count in the high half
+        const long long packed = ((long long)(len > 0 ? 1 : 0) << 32) | (long long)len;
+        long long tot64;
+        const long long ex = G::template excl_scan<long long>(packed, (long long *)sc.red64, &tot64);
+        const int cidx = (int)(ex >> 32);
+        const int excl = (int)(ex & 0xffffffffll);
+        const int nf = (int)(tot64 >> 32);
+        const int total = (int)(tot64 & 0xffffffffll);
+        if (len > 0) {
             sc.incl[cidx] = excl + len;
             sc.start[cidx] = bs - excl;
             if constexpr (NUM) sc.av[cidx] = av;
         }
         G::sync();
-        for (int pb = G::wid() * 32; pb < total; pb += GS) {
-            // first staged entry whose inclusive prefix exceeds pb
-            int lo = 0, hi = nf;
-            while (lo < hi) {
-                int mid = (lo + hi) >> 1;
-                if (sc.incl[mid] <= pb) lo = mid + 1;
-                else hi = mid;
+        const int per = (total + G::kWarps - 1) / G::kWarps;
+        const int lo = w * per;
+        const int hi = min(lo + per, total);
+        if (lo < hi) {
+            int a = 0, b = nf;
+            while (a < b) {
+                const int m = (a + b) >> 1;
+                if (sc.incl[m] <= lo) a = m + 1;
+                else b = m;
             }
-            const int c0 = lo;
-            const int wi = min(c0 + lane, nf - 1);
-            const int w_incl = sc.incl[wi];
-            const int p = pb + lane;
-            int o = 0;
+            int c0 = a;
+            for (int pb = lo; pb < hi; pb += 32) {
+                const int w_incl = sc.incl[min(c0 + lane, nf - 1)];
+                const int p = pb + lane;
+                int o = 0;
 #pragma unroll
-            for (int s = 16; s >= 1; s >>= 1) {
-                int c = __shfl_sync(kFull, w_incl, o + s - 1);
-                if (c <= p) o += s;
-            }
-            if (p < total) {
-                const int ci = c0 + o;
-                const int64_t idx = sc.start[ci] + p;
-                const int j = __ldg(op.b_ci + idx);
-                if ((unsigned)j < (unsigned)op.ncols) {
-                    if constexpr (NUM) f(j, sc.av[ci] * __ldg(op.b_val + idx));
-                    else f(j, V(0));
-                } else {
-                    raise_err(err, kErrBadIndex);
+                for (int s = 16; s >= 1; s >>= 1) {
+                    const int c = __shfl_sync(kFull, w_incl, o + s - 1);
+                    if (c <= p) o += s;
                 }
+                const int o31 = __shfl_sync(kFull, o, 31);
+                const int inc31 = __shfl_sync(kFull, w_incl, o31);
+                if (p < hi) {
+                    const int ci = c0 + o;
+                    const int64_t idx = sc.start[ci] + p;
+                    const int j = __ldg(op.b_ci + idx);
+                    if ((unsigned)j < (unsigned)op.ncols) f(j, NUM ? sc.av[ci] : V(0), idx);
+                    else raise_err(err, kErrBadIndex);
+                }
+                // entry of product pb + 32: the entry of pb + 31, or the next one if that ends there
+                c0 += o31 + (inc31 <= pb + 32 ? 1 : 0);
             }
         }
         G::sync();
@@ -371,6 +390,11 @@ __device__ __forceinline__ void row_products(const Operands<V> &op, int64_t ab, 
                                              const ProdScratch<V> &sc, int *err, F &&f) {
     if constexpr (GS == 32) warp_products<V, NUM>(op, ab, ae, err, f);
     else group_products<V, NUM, GS, NT>(op, ab, ae, sc, err, f);
+}
+
+template <typename V>
+__device__ __forceinline__ V b_value(const Operands<V> &op, int64_t idx) {
+    return __ldg(op.b_val + idx);
 }
 
 // ---------------------------------------------------------------------------

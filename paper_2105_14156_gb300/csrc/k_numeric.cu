@@ -18,10 +18,14 @@
 // Version 3's table in DRAM).
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "device_common.cuh"
 #include "kernels.h"
 
 namespace smash {
+
+namespace cg = cooperative_groups;
 
 template <typename V>
 struct NumOutT {
@@ -223,7 +227,8 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
         int64_t ab = 0, ae = 0;
         if (ok) a_row_range(op, i, ab, ae, err);
         int cnt = 0;
-        row_products<V, true, GS, NT>(op, ab, ae, sc, err, [&](int j, V v) {
+        row_products<V, true, GS, NT>(op, ab, ae, sc, err, [&](int j, V a, int64_t idx) {
+            const V v = a * b_value(op, idx);
             bool ins;
             const int h = hash_find_or_insert<false>(keys, tbits, hc, j, ins);
             if (h >= 0) {
@@ -277,7 +282,8 @@ __global__ void __launch_bounds__(NT) k_num_dense(Operands<V> op, const int *row
         __syncthreads();
         int64_t ab = 0, ae = 0;
         if (ok) a_row_range(op, i, ab, ae, err);
-        row_products<V, true, NT, NT>(op, ab, ae, sc, err, [&](int j, V v) {
+        row_products<V, true, NT, NT>(op, ab, ae, sc, err, [&](int j, V a, int64_t idx) {
+            const V v = a * b_value(op, idx);
             atomicAdd(acc + j, v);
             const unsigned bit = 1u << (j & 31);
             unsigned *w = bm + (j >> 5);
@@ -312,6 +318,127 @@ __global__ void __launch_bounds__(NT) k_num_dense(Operands<V> op, const int *row
         if constexpr (!SACC) __threadfence();
         __syncthreads();
     }
+}
+
+// ----- dense rows in a thread-block cluster -----------------------------------
+// The row's accumulator (one value per column of B) is split over the shared
+// memory of the CS blocks of a cluster: block q owns columns
+// [q*cpc, (q+1)*cpc). Every block enumerates all products of the row and keeps
+// those in its own window, so all accumulation uses local shared-memory
+// atomics (a remote, distributed-shared-memory atomic costs about as much as
+// twenty local integer ones). Each block ranks its columns by bitmap prefix
+// counts; the blocks' counts, exchanged through distributed shared memory,
+// give each window's offset, so the row is written sorted without a sort.
+// Accumulator and bitmap are cleared as they are read out.
+// Hot columns (see k_split.cu) accumulate in private per-warp slots instead:
+// their products then contend only within one warp, and the slots are summed
+// into the accumulator once per row.
+template <typename V, int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(1024)
+    k_num_dense_cluster(Operands<V> op, const int *rows, int count, int *token, int cpc, const int *splits,
+                        NumOutT<V> out, const unsigned *hot_bm_g, const int *hot_col_g, const int *hot_n_g, int H,
+                        int *err) {
+    constexpr int NT = 1024;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_row[2];
+    __shared__ int s_cnt[2];
+    __shared__ int s_base, s_total;
+    const int words = cpc >> 5;
+    V *acc = (V *)smem;
+    V *priv = (V *)(smem + (size_t)cpc * sizeof(V));           // [32 warps][H]
+    unsigned *bm = (unsigned *)(priv + (size_t)32 * H);
+    int *pre = (int *)(bm + words);
+    unsigned *hbm = (unsigned *)(pre + words);                   // H > 0 only
+    int *hpre = (int *)(hbm + (H > 0 ? words : 0));
+    int *hcol = hpre + (H > 0 ? words : 0);
+    const ProdScratch<V> sc = carve_prod_scratch<V, NT>((unsigned char *)(hcol + H));
+    const int t = threadIdx.x;
+    const int wp = t >> 5;
+    const unsigned lo = (unsigned)splits[rank];
+    const unsigned width = (unsigned)(splits[rank + 1] - splits[rank]);   // <= cpc
+    op.slice = rank;   // with a sliced B, enumerate this block's window only
+    for (int j = t; j < cpc; j += NT) acc[j] = V(0);
+    for (int w = t; w < words; w += NT) bm[w] = 0u;
+    int hn = 0;
+    if (H > 0) {
+        for (int k = t; k < 32 * H; k += NT) priv[k] = V(0);
+        for (int w = t; w < words; w += NT) hbm[w] = hot_bm_g[(size_t)rank * words + w];
+        hn = hot_n_g[rank];
+        for (int k = t; k < hn; k += NT) hcol[k] = hot_col_g[(size_t)rank * H + k];
+        __syncthreads();
+        bitmap_prefix<NT, NT>(hbm, hpre, words, sc.red);
+    }
+    for (int it = 0;; ++it) {
+        const int par = it & 1;
+        if (rank == 0 && t == 0) s_row[par] = atomicAdd(token, 1);
+        cl.sync();
+        const int r = *cl.map_shared_rank(&s_row[par], 0);
+        if (r >= count) break;
+        const int i = rows[r];
+        int64_t c0;
+        int n_exp;
+        const bool ok = out_range(out, i, c0, n_exp, err);
+        int64_t ab = 0, ae = 0;
+        if (ok) a_row_range(op, i, ab, ae, err);
+        group_products<V, true, NT, NT>(op, ab, ae, sc, err, [&](int j, V a, int64_t idx) {
+            const unsigned off = (unsigned)j - lo;
+            if (off < width) {
+                const V v = a * b_value(op, idx);
+                const unsigned bit = 1u << (off & 31);
+                const int w = (int)(off >> 5);
+                if (H > 0 && (hbm[w] & bit)) atomicAdd(priv + wp * H + hpre[w] + __popc(hbm[w] & (bit - 1u)), v);
+                else atomicAdd(acc + off, v);
+                if (!(*(volatile unsigned *)(bm + w) & bit)) atomicOr(bm + w, bit);
+            }
+        });
+        __syncthreads();
+        for (int k = t; k < hn; k += NT) {
+            V sum = V(0);
+            for (int q = 0; q < 32; ++q) {
+                sum += priv[q * H + k];
+                priv[q * H + k] = V(0);
+            }
+            acc[hcol[k]] = sum;
+        }
+        if (H > 0) __syncthreads();
+        const int cnt = bitmap_prefix<NT, NT>(bm, pre, words, sc.red);
+        if (t == 0) s_cnt[par] = cnt;
+        cl.sync();
+        if (t == 0) {
+            int base = 0, total = 0;
+            for (int q = 0; q < CS; ++q) {
+                const int c = *cl.map_shared_rank(&s_cnt[par], q);
+                if (q < rank) base += c;
+                total += c;
+            }
+            s_base = base;
+            s_total = total;
+        }
+        __syncthreads();
+        const int base = s_base;
+        if (rank == 0 && t == 0 && s_total != n_exp) raise_err(err, kErrCountMismatch);
+        for (int w = t; w < words; w += NT) {
+            unsigned bits = bm[w];
+            int pos = base + pre[w];
+            bm[w] = 0u;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const int jl = (w << 5) + b;
+                const V v = acc[jl];
+                acc[jl] = V(0);
+                if (pos < n_exp) {
+                    out.c_ci[c0 + pos] = (int)lo + jl;
+                    out.c_val[c0 + pos] = v;
+                }
+                ++pos;
+            }
+        }
+        __syncthreads();
+    }
+    cl.sync();
 }
 
 // ----- global-memory hash rows ------------------------------------------------
@@ -373,7 +500,8 @@ __global__ void __launch_bounds__(NT) k_num_spill(Operands<V> op, const int *row
         int64_t ab = 0, ae = 0;
         if (ok) a_row_range(op, i, ab, ae, err);
         int cnt = 0;
-        row_products<V, true, NT, NT>(op, ab, ae, sc, err, [&](int j, V v) {
+        row_products<V, true, NT, NT>(op, ab, ae, sc, err, [&](int j, V a, int64_t idx) {
+            const V v = a * b_value(op, idx);
             bool ins;
             const int h = hash_find_or_insert<true>(keys, tb, hc, j, ins);
             if (h >= 0) {
@@ -573,18 +701,75 @@ int num_dense_grid(int dtype, const HashLaunch &hl, int ncols) {
 }
 
 template <typename V>
+static size_t dense_cluster_smem(int cpc, int H) {
+    size_t b = (size_t)cpc * sizeof(V) + (size_t)32 * H * sizeof(V) + (size_t)(cpc / 32) * 8 +
+               num_scratch_bytes<V, 1024>();
+    if (H > 0) b += (size_t)(cpc / 32) * 8 + (size_t)H * 4;
+    return b;
+}
+
+// Widest window (multiple of 32 columns) one 1024-thread block can accumulate.
+int num_dense_cap(int dtype, int H) {
+    int lo = 0, hi = 1 << 22;
+    while (hi - lo > 32) {
+        const int mid = ((lo + hi) / 2) & ~31;
+        const size_t need = dtype ? dense_cluster_smem<double>(mid, H) : dense_cluster_smem<float>(mid, H);
+        if (need <= (size_t)max_smem_per_block()) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Smallest cluster whose blocks together cover all columns (0: none up to 8).
+int num_dense_cluster_size(int dtype, int ncols, int cluster_max, int H) {
+    const long long cap = num_dense_cap(dtype, H);
+    for (int cs = 1; cs <= 8 && cs <= cluster_max; cs <<= 1)
+        if (cap * cs >= ncols) return cs;
+    return 0;
+}
+
+template <typename V, int CS>
+static void dense_cluster_go(Operands<V> op, const BSlices &sl, int cpc, const int *rows, int count, int *token,
+                             const NumOutT<V> &out, int *err, cudaStream_t s) {
+    const int H = sl.hot_n ? sl.hot_h : 0;
+    const size_t smem = dense_cluster_smem<V>(cpc, H);
+    if (CS > 1 && sl.woff) {
+        op.b_ci = sl.ci;
+        op.b_val = (const V *)sl.val;
+        op.b_woff = sl.woff;
+        op.nslices = CS;
+    }
+    auto kern = k_num_dense_cluster<V, CS>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CS, 1, 1);
+    cfg.blockDim = dim3(1024, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        nclusters = 1;
+    }
+    if (nclusters > count) nclusters = count;
+    kern<<<nclusters * CS, 1024, smem, s>>>(op, rows, count, token, cpc, sl.splits, out, sl.hot_bm, sl.hot_col,
+                                            sl.hot_n, H, err);
+}
+
+template <typename V>
 static void num_dense_typed(const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
-                            void *acc, const NumOut &o, int *err, cudaStream_t s) {
+                            void *acc, const BSlices &sl, const NumOut &o, int *err, cudaStream_t s) {
     const Operands<V> op = num_operands<V>(r);
     const NumOutT<V> out = num_out<V>(o);
     const int words = (r.ncols + 31) / 32;
-    const bool sacc = num_dense_uses_smem_acc(sizeof(V) == 8, r.ncols);
-    if (sacc) {
-        const size_t smem = dense_smem<V>(r.ncols, true);
-        auto kern = k_num_dense<V, 1024, true>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const int grid = resident_grid(kern, 1024, smem, hl.sms, count, 2);
-        kern<<<grid, 1024, smem, s>>>(op, rows, count, token, words, nullptr, out, err);
+    const int cs = sl.splits ? sl.nslices : 0;
+    if (cs > 0) {
+        switch (cs) {
+            case 1: dense_cluster_go<V, 1>(op, sl, sl.cpc, rows, count, token, out, err, s); break;
+            case 2: dense_cluster_go<V, 2>(op, sl, sl.cpc, rows, count, token, out, err, s); break;
+            case 4: dense_cluster_go<V, 4>(op, sl, sl.cpc, rows, count, token, out, err, s); break;
+            default: dense_cluster_go<V, 8>(op, sl, sl.cpc, rows, count, token, out, err, s); break;
+        }
     } else {
         const size_t smem = dense_smem<V>(r.ncols, false);
         auto kern = k_num_dense<V, 1024, false>;
@@ -596,10 +781,11 @@ static void num_dense_typed(const RawOperands &r, const int *rows, int count, in
 }
 
 void launch_num_dense(int dtype, const RawOperands &r, const int *rows, int count, int *token,
-                      const HashLaunch &hl, void *acc, const NumOut &out, int *err, cudaStream_t s) {
+                      const HashLaunch &hl, void *acc, const BSlices &sl, const NumOut &out, int *err,
+                      cudaStream_t s) {
     if (count <= 0) return;
-    if (dtype) num_dense_typed<double>(r, rows, count, token, hl, acc, out, err, s);
-    else num_dense_typed<float>(r, rows, count, token, hl, acc, out, err, s);
+    if (dtype) num_dense_typed<double>(r, rows, count, token, hl, acc, sl, out, err, s);
+    else num_dense_typed<float>(r, rows, count, token, hl, acc, sl, out, err, s);
 }
 
 int num_spill_grid(int dtype, const HashLaunch &hl) {

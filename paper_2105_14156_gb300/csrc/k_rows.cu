@@ -19,15 +19,19 @@ __device__ __forceinline__ int bin_for(long long size, const BinRule &r) {
     return r.dense_ok ? kBinDense : kBinSpill;
 }
 
-// One warp per row of A: flop_i, its bound min(flop_i, cols(B)), and the bin.
-__global__ void __launch_bounds__(256) k_sym_rowinfo(RawOperands op, BinRule rule, BinBuffers bb,
-                                                     long long *bound_out, int *nnz_out, int *err) {
+// One warp per row of A: flop_i and nnz(A_i). The size that bins the row is
+// the bound min(flop_i, cols(B)) in the symbolic phase (c_rp == nullptr) and
+// the exact length c_rp[i+1] - c_rp[i] in the numeric phase.
+__global__ void __launch_bounds__(256) k_rowinfo(RawOperands op, const int64_t *c_rp, int64_t c_nnz, BinRule rule,
+                                                 BinBuffers bb, long long *bound_out, int *nnz_out, int *err) {
     __shared__ int s_cnt[kNumBins];
     __shared__ long long s_max[kNumBins];
+    __shared__ long long s_sum[3][kNumBins];
     __shared__ long long s_prod, s_maxrow;
     if (threadIdx.x < kNumBins) {
         s_cnt[threadIdx.x] = 0;
         s_max[threadIdx.x] = 0;
+        s_sum[0][threadIdx.x] = s_sum[1][threadIdx.x] = s_sum[2][threadIdx.x] = 0;
     }
     if (threadIdx.x == 0) {
         s_prod = 0;
@@ -56,13 +60,24 @@ __global__ void __launch_bounds__(256) k_sym_rowinfo(RawOperands op, BinRule rul
         }
         f = warp_sum(f);
         if (lane == 0) {
-            const long long bound = f < (long long)op.ncols ? f : (long long)op.ncols;
-            const int b = bin_for(bound, rule);
+            long long size;
+            if (c_rp) {
+                const int64_t s = c_rp[i], t = c_rp[i + 1];
+                size = 0;
+                if (s < 0 || t < s || t > c_nnz) raise_err(err, kErrBadRowPtr);
+                else size = t - s;
+            } else {
+                size = f < (long long)op.ncols ? f : (long long)op.ncols;
+                bound_out[i] = size;
+            }
+            const int b = bin_for(size, rule);
             bb.bin[i] = (uint8_t)b;
-            bound_out[i] = bound;
             atomicAdd(&s_cnt[b], 1);
-            atomicMax(&s_max[b], bound);
-            if (b == kBinEmpty) nnz_out[i] = 0;
+            atomicMax(&s_max[b], size);
+            atomicAdd((unsigned long long *)&s_sum[0][b], (unsigned long long)(ae - ab));
+            atomicAdd((unsigned long long *)&s_sum[1][b], (unsigned long long)f);
+            atomicAdd((unsigned long long *)&s_sum[2][b], (unsigned long long)size);
+            if (!c_rp && b == kBinEmpty) nnz_out[i] = 0;
             my_prod += f;
             my_max = f > my_max ? f : my_max;
         }
@@ -73,40 +88,15 @@ __global__ void __launch_bounds__(256) k_sym_rowinfo(RawOperands op, BinRule rul
     }
     __syncthreads();
     if (threadIdx.x < kNumBins && s_cnt[threadIdx.x]) {
-        atomicAdd(bb.counts + threadIdx.x, s_cnt[threadIdx.x]);
-        atomicMax(bb.maxsize + threadIdx.x, s_max[threadIdx.x]);
+        const int b = threadIdx.x;
+        atomicAdd(bb.counts + b, s_cnt[b]);
+        atomicMax(bb.maxsize + b, s_max[b]);
+        for (int q = 0; q < 3; ++q)
+            atomicAdd((unsigned long long *)(bb.sums + q * 16 + b), (unsigned long long)s_sum[q][b]);
     }
     if (threadIdx.x == 0) {
         atomicAdd((unsigned long long *)bb.stats, (unsigned long long)s_prod);
         atomicMax(bb.stats + 1, s_maxrow);
-    }
-}
-
-// One thread per row of C: the exact row length from C's row pointer.
-__global__ void __launch_bounds__(256) k_num_rowinfo(const int64_t *c_rp, int64_t n, int64_t c_nnz,
-                                                     BinRule rule, BinBuffers bb, int *err) {
-    __shared__ int s_cnt[kNumBins];
-    __shared__ long long s_max[kNumBins];
-    if (threadIdx.x < kNumBins) {
-        s_cnt[threadIdx.x] = 0;
-        s_max[threadIdx.x] = 0;
-    }
-    __syncthreads();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int64_t s = c_rp[i], t = c_rp[i + 1];
-        long long size = 0;
-        if (s < 0 || t < s || t > c_nnz) raise_err(err, kErrBadRowPtr);
-        else size = t - s;
-        const int b = bin_for(size, rule);
-        bb.bin[i] = (uint8_t)b;
-        atomicAdd(&s_cnt[b], 1);
-        atomicMax(&s_max[b], size);
-    }
-    __syncthreads();
-    if (threadIdx.x < kNumBins && s_cnt[threadIdx.x]) {
-        atomicAdd(bb.counts + threadIdx.x, s_cnt[threadIdx.x]);
-        atomicMax(bb.maxsize + threadIdx.x, s_max[threadIdx.x]);
     }
 }
 
@@ -238,22 +228,22 @@ __global__ void __launch_bounds__(kScanNT) k_scan_down(const int *nnz, int64_t n
 }
 
 // ---------------------------------------------------------------------------
+static int rowinfo_grid(int64_t rows, int sms) {
+    const int64_t blocks = (rows + 7) / 8;
+    const int64_t cap = (int64_t)sms * 8;
+    return (int)(blocks < cap ? blocks : cap);
+}
+
 void launch_sym_rowinfo(const RawOperands &op, const BinRule &rule, BinBuffers bb, long long *bound_out,
                         int *nnz_out, int *err, int sms, cudaStream_t s) {
     if (op.a_rows == 0) return;
-    int64_t warps_needed = op.a_rows;
-    int64_t blocks = (warps_needed + 7) / 8;
-    int64_t cap = (int64_t)sms * 8;
-    int grid = (int)(blocks < cap ? blocks : cap);
-    k_sym_rowinfo<<<grid, 256, 0, s>>>(op, rule, bb, bound_out, nnz_out, err);
+    k_rowinfo<<<rowinfo_grid(op.a_rows, sms), 256, 0, s>>>(op, nullptr, 0, rule, bb, bound_out, nnz_out, err);
 }
 
-void launch_num_rowinfo(const int64_t *c_rp, int64_t n, int64_t c_nnz, const BinRule &rule, BinBuffers bb,
-                        int *err, cudaStream_t s) {
-    if (n == 0) return;
-    int64_t blocks = (n + 255) / 256;
-    int grid = (int)(blocks < 4096 ? blocks : 4096);
-    k_num_rowinfo<<<grid, 256, 0, s>>>(c_rp, n, c_nnz, rule, bb, err);
+void launch_num_rowinfo(const RawOperands &op, const int64_t *c_rp, int64_t c_nnz, const BinRule &rule,
+                        BinBuffers bb, int *err, int sms, cudaStream_t s) {
+    if (op.a_rows == 0) return;
+    k_rowinfo<<<rowinfo_grid(op.a_rows, sms), 256, 0, s>>>(op, c_rp, c_nnz, rule, bb, nullptr, nullptr, err);
 }
 
 void launch_bin_scatter(int64_t n, BinBuffers bb, cudaStream_t s) {

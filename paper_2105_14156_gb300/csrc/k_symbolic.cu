@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(NT) k_sym_hash(Operands<float> op, const int *
         int64_t ab, ae;
         a_row_range(op, i, ab, ae, err);
         int cnt = 0;
-        row_products<float, false, GS, NT>(op, ab, ae, sc, err, [&](int j, float) {
+        row_products<float, false, GS, NT>(op, ab, ae, sc, err, [&](int j, float, int64_t) {
             bool ins;
             if (hash_find_or_insert<false>(keys, tbits, hc, j, ins) < 0) raise_err(err, kErrTableFull);
             cnt += ins ? 1 : 0;
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(NT) k_sym_dense(Operands<float> op, const int 
         __syncthreads();
         int64_t ab, ae;
         a_row_range(op, i, ab, ae, err);
-        row_products<float, false, NT, NT>(op, ab, ae, sc, err, [&](int j, float) {
+        row_products<float, false, NT, NT>(op, ab, ae, sc, err, [&](int j, float, int64_t) {
             const unsigned bit = 1u << (j & 31);
             unsigned *w = bm + (j >> 5);
             if (!(*(volatile unsigned *)w & bit)) atomicOr(w, bit);
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(NT) k_sym_spill(Operands<float> op, const int 
         int64_t ab, ae;
         a_row_range(op, i, ab, ae, err);
         int cnt = 0;
-        row_products<float, false, NT, NT>(op, ab, ae, sc, err, [&](int j, float) {
+        row_products<float, false, NT, NT>(op, ab, ae, sc, err, [&](int j, float, int64_t) {
             bool ins;
             if (hash_find_or_insert<true>(keys, tb, hc, j, ins) < 0) raise_err(err, kErrTableFull);
             cnt += ins ? 1 : 0;

@@ -38,13 +38,14 @@ struct BinBuffers {
     long long *stats;    // [4]  products, max row products
     int *rows;         // [n]   row ids grouped by bin
     int *offsets;      // [17]  exclusive offsets of the bins in rows[]
+    long long *sums;   // [3][16] per bin: sum nnz(A_i), sum flop_i, sum size bound
 };
 
 // k_rows.cu
 void launch_sym_rowinfo(const RawOperands &op, const BinRule &rule, BinBuffers bb, long long *bound_out,
                         int *nnz_out, int *err, int sms, cudaStream_t s);
-void launch_num_rowinfo(const int64_t *c_rp, int64_t n, int64_t c_nnz, const BinRule &rule,
-                        BinBuffers bb, int *err, cudaStream_t s);
+void launch_num_rowinfo(const RawOperands &op, const int64_t *c_rp, int64_t c_nnz, const BinRule &rule,
+                        BinBuffers bb, int *err, int sms, cudaStream_t s);
 void launch_bin_scatter(int64_t n, BinBuffers bb, cudaStream_t s);
 size_t scan_scratch_bytes(int64_t n);
 void launch_scan_rowptr(const int *nnz, int64_t n, int64_t *c_rp, long long *total,
@@ -57,6 +58,7 @@ struct HashLaunch {
     int colbits;
     int sms;
     int blocks_per_sm;  // for dense / spill kernels
+    int cluster_max;    // largest cluster for dense rows
 };
 
 // k_symbolic.cu
@@ -81,8 +83,30 @@ void launch_num_hash(int dtype, const RawOperands &op, const int *rows, int coun
                      cudaStream_t s);
 int num_dense_grid(int dtype, const HashLaunch &hl, int ncols);
 bool num_dense_uses_smem_acc(int dtype, int ncols);
+int num_dense_cluster_size(int dtype, int ncols, int cluster_max, int H);  // 0: none fits
+int num_dense_cap(int dtype, int H);  // widest column window of one block
+// Plan of the dense cluster kernel (k_split.cu): window split points
+// splits[ns+1] on the device; slices of B (woff[B.rows][ns+1], regrouped
+// col/val copies; ns > 1 only); hot columns per window: hot_bm[ns][cpc/32],
+// hot_col[ns][hot_h], hot_n[ns].
+struct BSlices {
+    int nslices = 0;
+    int cpc = 0;
+    const int *splits = nullptr;
+    const int32_t *woff = nullptr;
+    const int32_t *ci = nullptr;
+    const void *val = nullptr;
+    const unsigned *hot_bm = nullptr;
+    const int *hot_col = nullptr;
+    const int *hot_n = nullptr;
+    int hot_h = 0;
+};
+size_t dense_plan_bytes(const RawOperands &op, int ns, int cpc, int H, size_t vsz);
+void launch_dense_plan(int dtype, const RawOperands &op, int ns, int cap, int cpc, int H, int hot_factor, void *ws,
+                       BSlices &sl, int sms, cudaStream_t s);
 void launch_num_dense(int dtype, const RawOperands &op, const int *rows, int count, int *token,
-                      const HashLaunch &hl, void *acc, const NumOut &out, int *err, cudaStream_t s);
+                      const HashLaunch &hl, void *acc, const BSlices &sl, const NumOut &out, int *err,
+                      cudaStream_t s);
 int num_spill_grid(int dtype, const HashLaunch &hl);
 void launch_num_spill(int dtype, const RawOperands &op, const int *rows, int count, int *token,
                       const HashLaunch &hl, float inv_load, int spill_tbits, void *tables,

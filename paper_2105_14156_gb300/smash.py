@@ -24,7 +24,7 @@ F32, F64 = 0, 1
 EXPORTS = [
     "smash_default_params", "smash_create", "smash_destroy", "smash_set_params", "smash_get_params",
     "smash_set_allocator", "spgemm_symbolic", "spgemm_numeric", "smash_check", "smash_get_stats",
-    "smash_status_string",
+    "smash_status_string", "smash_set_timing", "smash_get_timings",
 ]
 
 
@@ -43,7 +43,9 @@ class Params(ctypes.Structure):
     _fields_ = [("hash_kind", ctypes.c_int32), ("max_load", ctypes.c_float), ("sym_max_tbits", ctypes.c_int32),
                 ("num_max_tbits", ctypes.c_int32), ("group_shift", ctypes.c_int32),
                 ("dense_ratio", ctypes.c_int32), ("bitmap_ratio", ctypes.c_int32),
-                ("spill_blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
+                ("spill_blocks_per_sm", ctypes.c_int32), ("sym_dense_ratio", ctypes.c_int32),
+                ("cluster_max", ctypes.c_int32), ("hot_cols", ctypes.c_int32), ("hot_factor", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -51,7 +53,20 @@ class Params(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("rows_per_bin", ctypes.c_int64 * 16), ("products", ctypes.c_int64),
-                ("max_row_products", ctypes.c_int64), ("c_nnz", ctypes.c_int64)]
+                ("max_row_products", ctypes.c_int64), ("c_nnz", ctypes.c_int64),
+                ("a_nnz_per_bin", ctypes.c_int64 * 16), ("products_per_bin", ctypes.c_int64 * 16),
+                ("c_nnz_per_bin", ctypes.c_int64 * 16)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("bin", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("launches", ctypes.c_int64), ("rows", ctypes.c_int64), ("a_nnz", ctypes.c_int64),
+                ("products", ctypes.c_int64), ("c_nnz", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["name"] = self.name.decode()
+        return d
 
 
 _lib = None
@@ -77,6 +92,9 @@ def load_library(path: str = LIB_PATH):
                                        ctypes.POINTER(CsrStruct), P]
         lib.smash_check.argtypes = [P, P]
         lib.smash_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+        lib.smash_set_timing.argtypes = [P, ctypes.c_int]
+        lib.smash_get_timings.argtypes = [P, ctypes.POINTER(KernelTime), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int)]
         lib.smash_status_string.argtypes = [ctypes.c_int]
         lib.smash_status_string.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -199,6 +217,17 @@ class Handle:
         s = Stats()
         _check(self.lib.smash_get_stats(self.h, ctypes.byref(s)), "smash_get_stats")
         return s
+
+    def set_timing(self, enable: bool):
+        _check(self.lib.smash_set_timing(self.h, 1 if enable else 0), "smash_set_timing")
+
+    def timings(self):
+        """Per-(kernel, bin) event-timed totals since timing was enabled."""
+        n = ctypes.c_int(0)
+        _check(self.lib.smash_get_timings(self.h, None, 0, ctypes.byref(n)), "smash_get_timings")
+        arr = (KernelTime * max(n.value, 1))()
+        _check(self.lib.smash_get_timings(self.h, arr, n.value, ctypes.byref(n)), "smash_get_timings")
+        return [arr[k].as_dict() for k in range(n.value)]
 
     def check(self, stream=None):
         _check(self.lib.smash_check(self.h, _stream_ptr(stream)), "smash_check")

@@ -51,7 +51,7 @@ def test_binding_lists_every_export():
 def test_host_only_calls(lib):
     from paper_2105_14156_gb300 import smash
     p = smash.default_params()
-    assert p.max_load == pytest.approx(0.5) and p.hash_kind == 0
+    assert p.max_load == pytest.approx(0.5) and p.hash_kind == 1
     assert lib.smash_status_string(0) == b"SMASH_OK"
     assert lib.smash_status_string(2) == b"SMASH_ERR_SHAPE_MISMATCH"
     # argument checks happen before any device work

@@ -16,19 +16,24 @@ from tests.helpers import identity, random_csr
 
 pytestmark = pytest.mark.gpu
 
-DEFAULT = dict(hash_kind=0, max_load=0.5, sym_max_tbits=15, num_max_tbits=14, group_shift=3, dense_ratio=4,
-               bitmap_ratio=4, spill_blocks_per_sm=1)
+DEFAULT = dict(hash_kind=1, max_load=0.5, sym_max_tbits=15, num_max_tbits=14, group_shift=3, dense_ratio=4,
+               bitmap_ratio=4, spill_blocks_per_sm=1, sym_dense_ratio=64, cluster_max=8, hot_cols=128,
+               hot_factor=16)
 
 # Parameter sets that force each path.
 PATHS = {
     "default": {},
-    "warp_only_small_tables": dict(sym_max_tbits=7, num_max_tbits=7, dense_ratio=0),   # rest spills
-    "spill_everything": dict(sym_max_tbits=5, num_max_tbits=5, dense_ratio=0),
-    "dense_everything": dict(dense_ratio=1 << 20),
+    "warp_only_small_tables": dict(sym_max_tbits=7, num_max_tbits=7, dense_ratio=0, sym_dense_ratio=0),
+    "spill_everything": dict(sym_max_tbits=5, num_max_tbits=5, dense_ratio=0, sym_dense_ratio=0),
+    "dense_everything": dict(dense_ratio=1 << 20, sym_dense_ratio=1 << 20),
+    "dense_single_block": dict(dense_ratio=1 << 20, cluster_max=1, num_max_tbits=5),
+    "no_symbolic_dense": dict(sym_dense_ratio=0),
+    "dense_no_hot_columns": dict(dense_ratio=1 << 20, hot_cols=0),
+    "dense_all_hot_columns": dict(dense_ratio=1 << 20, hot_cols=512, hot_factor=1),
     "group_per_row": dict(group_shift=0),
     "bitonic_only": dict(bitmap_ratio=0),
     "bitmap_always": dict(bitmap_ratio=1 << 20),
-    "hash_multiplicative": dict(hash_kind=1),
+    "hash_low_bits": dict(hash_kind=0),
     "hash_high_bits": dict(hash_kind=2),
     "load_0.9": dict(max_load=0.9),
     "load_0.1": dict(max_load=0.1),
@@ -141,6 +146,18 @@ def test_congruent_columns_defeat_low_bits(handle):
     A = random_csr(200, n, 0.2, 9, values="f64")
     for kind in (0, 1, 2):
         C = run(handle, A, B, hash_kind=kind, dense_ratio=0)
+        assert_matches_oracle(C, A, B)
+
+
+@pytest.mark.parametrize("ncols,cluster_max", [(20000, 8), (40000, 8), (80000, 8), (110000, 8), (110000, 1),
+                                               (40000, 2)])
+def test_dense_rows_cluster_sizes(handle, ncols, cluster_max):
+    """Dense rows whose accumulator needs 1, 2, 4 or 8 blocks of a cluster (or,
+    with clusters disabled, the global-memory accumulator)."""
+    A = random_csr(96, 64, 0.3, 51, values="f64")
+    B = random_csr(64, ncols, 800.0 / ncols, 52, values="f64")
+    for hot in (0, 128, 512):
+        C = run(handle, A, B, dense_ratio=1 << 20, cluster_max=cluster_max, hot_cols=hot, hot_factor=1)
         assert_matches_oracle(C, A, B)
 
 
