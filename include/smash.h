@@ -174,6 +174,98 @@ int smash_check(smash_handle *h, void *stream);
 /* Statistics of the handle's last symbolic or numeric call. */
 int smash_get_stats(const smash_handle *h, smash_stats *out);
 
+/* ---------------------------------------------------------------------------
+ * Learned sizing. The paper has no counterpart: it sizes output with the exact
+ * per-row count of its setup phase. Here a small multilayer perceptron
+ * predicts y_i = log(1 + nnz(C_i)) of each row from six features of the row
+ * (log1p of nnz(A_i), of flop_i, of the longest and the mean selected row of
+ * B, of min(flop_i, cols(B)); and min(flop_i, cols(B)) / cols(B)). Network:
+ * x = (f - mean) * inv_std, h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2) with
+ * 64 units each, y = w3 . h2 + b3. The prediction sizes hash tables, bins and
+ * a staging buffer, so the exact symbolic pass is skipped; any row whose
+ * prediction proves too small is recomputed by the exact path, so C is always
+ * exact. Parameters: SMASH_MLP_PARAMS floats in the order W1 (64x6,
+ * row-major), b1, W2 (64x64, row-major), b2, w3, b3. Inference reads bfloat16
+ * copies of the weights and accumulates in fp32; training keeps fp32 master
+ * weights and Adam moments, all on the device.
+ */
+#define SMASH_MLP_PARAMS 4673
+#define SMASH_MLP_FEATURES 6
+
+typedef struct smash_model smash_model;
+
+typedef struct {
+    int32_t epochs;   /* passes over the data; default 8 */
+    int32_t batch;    /* minibatch size; default 4096 */
+    float lr;         /* Adam step size; default 2e-3 */
+    float beta1, beta2, eps;  /* defaults 0.9, 0.999, 1e-8 */
+    float weight_decay;       /* L2 term added to the gradient; default 0 */
+    uint64_t seed;    /* sample order */
+    int32_t reserved[4];
+} smash_train_cfg;
+
+typedef struct {
+    int64_t rows;           /* rows of C */
+    int64_t overflow_rows;  /* rows recomputed by the exact path */
+    int64_t staged_nnz;     /* capacity of the staging buffer (sum of predicted capacities) */
+    int64_t c_nnz;          /* nnz(C) */
+} smash_learned_stats;
+
+int smash_train_cfg_default(smash_train_cfg *cfg);
+
+/* Create a model with He-initialised weights (seeded) and identity
+ * normalisation, on the handle's device. */
+int smash_model_create(smash_handle *h, smash_model **out, uint64_t seed);
+int smash_model_destroy(smash_model *m);
+
+/* Host copies of the fp32 parameters (SMASH_MLP_PARAMS floats) and of the
+ * normalisation (mean[6] then inv_std[6]); either pointer may be NULL. */
+int smash_model_get(const smash_model *m, float *params, float *norm);
+int smash_model_set(smash_model *m, const float *params, const float *norm);
+
+/* Binary file: 8-byte magic "SMASHMLP", int32 version (1), int32 parameter
+ * count, then the parameters and the normalisation as little-endian floats. */
+int smash_model_save(const smash_model *m, const char *path);
+int smash_model_load(smash_model *m, const char *path);
+
+/* Features of every row of C = A*B (device float[A.rows * 6], row-major). */
+int smash_row_features(smash_handle *h, const smash_csr *A, const smash_csr *B, float *feats, void *stream);
+
+/* Train on n samples: feats device float[n*6] (raw features as produced by
+ * smash_row_features), targets device float[n] (log1p of the exact row
+ * counts). The normalisation is set from the data's mean and standard
+ * deviation. *final_loss (host, may be NULL) receives the last epoch's mean
+ * squared error. Synchronises the stream. */
+int smash_mlp_train(smash_handle *h, smash_model *m, const float *feats, const float *targets, int64_t n,
+                    const smash_train_cfg *cfg, float *final_loss, void *stream);
+
+/* Mean squared error and its gradient over n samples with the current fp32
+ * weights: grad device float[SMASH_MLP_PARAMS], *loss host. Synchronises. */
+int smash_mlp_gradient(smash_handle *h, smash_model *m, const float *feats, const float *targets, int64_t n,
+                       float *grad, float *loss, void *stream);
+
+/* Predictions y (device float[n]) with the bfloat16 inference weights. */
+int smash_mlp_predict(smash_handle *h, const smash_model *m, const float *feats, int64_t n, float *y,
+                      void *stream);
+
+/*
+ * C = A*B with learned sizing. Each row gets a capacity
+ * min(ceil((1 + margin) * expm1(y_i)), min(flop_i, cols(B))) from the model;
+ * rows are binned and hashed with tables sized by it and written to a staging
+ * buffer; rows whose result did not fit are recomputed exactly (symbolic then
+ * numeric); finally C is assembled. C->row_ptr, C->col_idx and C->val are
+ * allocated through the handle's allocator and owned by the caller (release
+ * them with the same allocator); C->rows, cols and nnz are set.
+ * margin > -1 (a negative margin forces under-prediction: a test hook).
+ * stats may be NULL. Synchronises the stream.
+ */
+int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smash_dtype dtype,
+                   const smash_model *m, float margin, smash_csr *C, smash_learned_stats *stats, void *stream);
+
+/* Release C's three arrays through the handle's allocator (for C filled by
+ * spgemm_learned or spgemm_batched). */
+int smash_free_csr(smash_handle *h, smash_csr *C);
+
 /* Kernel timing (a tracing aid; not needed for results). With enable != 0,
  * every kernel launch of the following calls is bracketed by CUDA events on
  * the call's stream; the totals accumulate per (kernel, bin) until read.

@@ -1,0 +1,428 @@
+// Host-side internals shared by the C ABI translation units: the handle,
+// scratch-memory management, launch timing and the row planner.
+//
+// The planner follows the paper's Window Distribution Phase: count each row's
+// products from the row pointers, decide dense or sparse per row by a
+// threshold, and group rows so that each group's tables fit on-chip memory
+// (here: one block's shared memory instead of a PIUMA block's scratchpad).
+#pragma once
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "device_common.cuh"
+#include "kernels.h"
+#include "smash.h"
+
+
+namespace smash {
+
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+// Event timing of kernel launches (tracing).
+struct PendingTime {
+    int slot;  // index into totals
+    cudaEvent_t e0, e1;
+};
+
+}  // namespace smash
+
+struct smash_handle {
+    bool timing = false;
+    std::vector<smash::PendingTime> pending;
+    std::vector<smash_kernel_time> totals;
+    std::vector<cudaEvent_t> spare_events;
+    int device = 0;
+    int sms = 0;
+    smash_params params{};
+    smash_alloc_fn alloc = nullptr;
+    smash_free_fn free_fn = nullptr;
+    void *ctx = nullptr;
+    smash::DevBuf ws;         // per-call arrays
+    smash::DevBuf tables;     // spill hash tables
+    smash::DevBuf dense_acc;  // dense accumulators (kept zero between rows)
+    smash::DevBuf split;      // dense-row plan: column windows, slices of B, hot columns
+    smash::DevBuf stage;      // learned path: capacity-padded staging of C
+    smash::DevBuf learn;      // learned path: per-row arrays
+    smash::DevBuf err;        // kNumErr ints (+ scratch words)
+    long long *host = nullptr;  // pinned host staging
+    smash_stats stats{};
+};
+
+namespace smash {
+namespace host {
+
+constexpr int kHostWords = 256;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+inline void *default_alloc(size_t bytes, void *) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+inline void default_free(void *p, void *) { cudaFree(p); }
+
+inline int release(smash_handle *h, DevBuf &b) {
+    if (b.ptr) {
+        cudaDeviceSynchronize();
+        h->free_fn(b.ptr, h->ctx);
+    }
+    b.ptr = nullptr;
+    b.bytes = 0;
+    return SMASH_OK;
+}
+
+// Grow-only buffer. Growing synchronises the stream first (the old buffer may
+// still be read by queued kernels).
+inline int ensure(smash_handle *h, DevBuf &b, size_t need, cudaStream_t s, bool zero = false) {
+    if (need == 0) need = 256;
+    if (b.bytes >= need) return SMASH_OK;
+    cudaStreamSynchronize(s);
+    if (b.ptr) h->free_fn(b.ptr, h->ctx);
+    b.ptr = nullptr;
+    b.bytes = 0;
+    size_t want = need + need / 4;
+    want = (want + 4095) & ~size_t(4095);
+    void *p = h->alloc(want, h->ctx);
+    if (!p) {
+        want = (need + 4095) & ~size_t(4095);
+        p = h->alloc(want, h->ctx);
+    }
+    if (!p) return SMASH_ERR_ALLOC;
+    b.ptr = p;
+    b.bytes = want;
+    if (zero && cudaMemsetAsync(p, 0, want, s) != cudaSuccess) return SMASH_ERR_CUDA;
+    return SMASH_OK;
+}
+
+inline cudaEvent_t take_event(smash_handle *h) {
+    if (!h->spare_events.empty()) {
+        cudaEvent_t e = h->spare_events.back();
+        h->spare_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one kernel launch with events when timing is on.
+struct LaunchTimer {
+    smash_handle *h;
+    cudaStream_t s;
+    int slot = -1;
+    cudaEvent_t e0 = nullptr;
+    LaunchTimer(smash_handle *hh, cudaStream_t ss, const char *name, int bin, int threads, long long rows,
+                long long a_nnz, long long products, long long c_nnz)
+        : h(hh), s(ss) {
+        if (!h->timing) return;
+        for (size_t k = 0; k < h->totals.size(); ++k)
+            if (h->totals[k].bin == bin && strncmp(h->totals[k].name, name, sizeof(h->totals[k].name)) == 0)
+                slot = (int)k;
+        if (slot < 0) {
+            smash_kernel_time kt;
+            memset(&kt, 0, sizeof(kt));
+            strncpy(kt.name, name, sizeof(kt.name) - 1);
+            kt.bin = bin;
+            h->totals.push_back(kt);
+            slot = (int)h->totals.size() - 1;
+        }
+        smash_kernel_time &kt = h->totals[slot];
+        kt.threads = threads;
+        kt.launches += 1;
+        kt.rows += rows;
+        kt.a_nnz += a_nnz;
+        kt.products += products;
+        kt.c_nnz += c_nnz;
+        e0 = take_event(h);
+        cudaEventRecord(e0, s);
+    }
+    ~LaunchTimer() {
+        if (!h->timing || slot < 0) return;
+        cudaEvent_t e1 = take_event(h);
+        cudaEventRecord(e1, s);
+        h->pending.push_back(PendingTime{slot, e0, e1});
+    }
+};
+
+inline void resolve_timings(smash_handle *h) {
+    for (const PendingTime &p : h->pending) {
+        cudaEventSynchronize(p.e1);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) h->totals[p.slot].ms += ms;
+        h->spare_events.push_back(p.e0);
+        h->spare_events.push_back(p.e1);
+    }
+    h->pending.clear();
+    cudaGetLastError();
+}
+
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *p) : base((char *)p) {}
+    template <typename T>
+    T *take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T *r = (T *)(base + off);
+        off += count * sizeof(T);
+        return r;
+    }
+};
+template <typename T>
+inline size_t carve_size(size_t &acc, size_t count) {
+    acc = (acc + 255) & ~size_t(255);
+    acc += count * sizeof(T);
+    return acc;
+}
+
+inline int status_from_flags(const long long *flags_as_ll) {
+    const int *f = (const int *)flags_as_ll;
+    if (f[kErrBadIndex] || f[kErrBadRowPtr] || f[kErrCountMismatch]) return SMASH_ERR_INVALID_ARG;
+    if (f[kErrBRowTooLong]) return SMASH_ERR_UNSUPPORTED;
+    if (f[kErrTimeout]) return SMASH_ERR_TIMEOUT;
+    if (f[kErrTableFull]) return SMASH_ERR_INTERNAL;
+    return SMASH_OK;
+}
+
+inline int check_params(const smash_params *p) {
+    if (!p) return SMASH_ERR_INVALID_ARG;
+    if (p->hash_kind < 0 || p->hash_kind > 2) return SMASH_ERR_INVALID_ARG;
+    if (!(p->max_load > 0.05f && p->max_load <= 0.95f)) return SMASH_ERR_INVALID_ARG;
+    if (p->sym_max_tbits < kMinTBits || p->sym_max_tbits > 15) return SMASH_ERR_INVALID_ARG;
+    if (p->num_max_tbits < kMinTBits || p->num_max_tbits > 14) return SMASH_ERR_INVALID_ARG;
+    if (p->group_shift < 0 || p->group_shift > 10) return SMASH_ERR_INVALID_ARG;
+    if (p->dense_ratio < 0 || p->bitmap_ratio < 0) return SMASH_ERR_INVALID_ARG;
+    if (p->spill_blocks_per_sm < 0 || p->spill_blocks_per_sm > 8) return SMASH_ERR_INVALID_ARG;
+    if (p->sym_dense_ratio < 0) return SMASH_ERR_INVALID_ARG;
+    if (p->hot_cols < 0 || p->hot_cols > 512 || p->hot_factor < 1) return SMASH_ERR_INVALID_ARG;
+    if (p->cluster_max != 1 && p->cluster_max != 2 && p->cluster_max != 4 && p->cluster_max != 8)
+        return SMASH_ERR_INVALID_ARG;
+    return SMASH_OK;
+}
+
+inline int check_csr(const smash_csr *M, bool need_val) {
+    if (!M) return SMASH_ERR_INVALID_ARG;
+    if (M->rows < 0 || M->cols < 0 || M->nnz < 0) return SMASH_ERR_INVALID_ARG;
+    if (M->rows >= (1ll << 31) || M->cols >= (1ll << 31)) return SMASH_ERR_UNSUPPORTED;
+    if (!M->row_ptr) return SMASH_ERR_INVALID_ARG;
+    if (M->nnz > 0 && !M->col_idx) return SMASH_ERR_INVALID_ARG;
+    if (need_val && M->nnz > 0 && !M->val) return SMASH_ERR_INVALID_ARG;
+    return SMASH_OK;
+}
+
+inline int colbits_of(int64_t ncols) {
+    int b = 0;
+    while ((1ll << b) < ncols) ++b;
+    return b;
+}
+
+inline RawOperands raw_ops(const smash_csr *A, const smash_csr *B) {
+    RawOperands r;
+    r.a_rp = A->row_ptr;
+    r.a_ci = A->col_idx;
+    r.a_val = A->val;
+    r.b_rp = B->row_ptr;
+    r.b_ci = B->col_idx;
+    r.b_val = B->val;
+    r.a_rows = A->rows;
+    r.a_nnz = A->nnz;
+    r.b_nnz = B->nnz;
+    r.b_rows = (int32_t)B->rows;
+    r.ncols = (int32_t)B->cols;
+    return r;
+}
+
+// Per-call planning buffers carved from h->ws.
+struct Plan {
+    BinBuffers bb;
+    long long *bound;
+    int *nnz;
+    void *scan;
+    long long *total;
+};
+
+inline int plan_buffers(smash_handle *h, int64_t n, bool symbolic, cudaStream_t s, Plan &pl) {
+    size_t need = 0;
+    carve_size<uint8_t>(need, (size_t)n);
+    carve_size<int>(need, 16 * 3);
+    carve_size<long long>(need, 16 + 4 + 1);
+    carve_size<int>(need, (size_t)n);
+    carve_size<int>(need, 17);
+    carve_size<long long>(need, 48);
+    if (symbolic) {
+        carve_size<long long>(need, (size_t)n);
+        carve_size<int>(need, (size_t)n);
+        carve_size<char>(need, scan_scratch_bytes(n));
+    }
+    int st = ensure(h, h->ws, need, s);
+    if (st) return st;
+    Carver c(h->ws.ptr);
+    pl.bb.bin = c.take<uint8_t>((size_t)n);
+    int *ctr = c.take<int>(16 * 3);
+    long long *ll = c.take<long long>(16 + 4 + 1);
+    pl.bb.counts = ctr;
+    pl.bb.cursor = ctr + 16;
+    pl.bb.tokens = ctr + 32;
+    pl.bb.maxsize = ll;
+    pl.bb.stats = ll + 16;
+    pl.total = ll + 20;
+    pl.bb.rows = c.take<int>((size_t)n);
+    pl.bb.offsets = c.take<int>(17);
+    pl.bb.sums = c.take<long long>(48);
+    pl.bound = nullptr;
+    pl.nnz = nullptr;
+    pl.scan = nullptr;
+    if (symbolic) {
+        pl.bound = c.take<long long>((size_t)n);
+        pl.nnz = c.take<int>((size_t)n);
+        pl.scan = c.take<char>(scan_scratch_bytes(n));
+    }
+    // zero counters, cursors, tokens, maxsize, stats, total
+    if (cudaMemsetAsync(ctr, 0, 16 * 3 * sizeof(int), s) != cudaSuccess) return SMASH_ERR_CUDA;
+    if (cudaMemsetAsync(ll, 0, (16 + 4 + 1) * sizeof(long long), s) != cudaSuccess) return SMASH_ERR_CUDA;
+    if (cudaMemsetAsync(pl.bb.sums, 0, 48 * sizeof(long long), s) != cudaSuccess) return SMASH_ERR_CUDA;
+    return SMASH_OK;
+}
+
+// Copy bin counts (16 int), offsets (17 int), maxsize (16 ll), stats (4 ll)
+// to the pinned host buffer and wait.
+inline int fetch_bins(smash_handle *h, const Plan &pl, cudaStream_t s, int *counts, int *offsets, long long *maxsize,
+               long long *stats, long long *sums) {
+    char *hb = (char *)h->host;
+    if (cudaMemcpyAsync(hb, pl.bb.counts, 16 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(hb + 64, pl.bb.offsets, 17 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(hb + 256, pl.bb.maxsize, 20 * sizeof(long long), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(hb + 512, pl.bb.sums, 48 * sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return SMASH_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SMASH_ERR_CUDA;
+    memcpy(counts, hb, 16 * sizeof(int));
+    memcpy(offsets, hb + 64, 17 * sizeof(int));
+    memcpy(maxsize, hb + 256, 16 * sizeof(long long));
+    memcpy(stats, hb + 256 + 16 * sizeof(long long), 4 * sizeof(long long));
+    memcpy(sums, hb + 512, 48 * sizeof(long long));
+    for (int b = 0; b < 16; ++b) {
+        h->stats.rows_per_bin[b] = b < kNumBins ? counts[b] : 0;
+        h->stats.a_nnz_per_bin[b] = sums[b];
+        h->stats.products_per_bin[b] = sums[16 + b];
+        h->stats.c_nnz_per_bin[b] = sums[32 + b];
+    }
+    h->stats.products = stats[0];
+    h->stats.max_row_products = stats[1];
+    return SMASH_OK;
+}
+
+inline int read_flags(smash_handle *h, cudaStream_t s, bool clear) {
+    char *hb = (char *)h->host + 1024;
+    if (cudaMemcpyAsync(hb, h->err.ptr, kNumErr * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return SMASH_ERR_CUDA;
+    if (clear && cudaMemsetAsync(h->err.ptr, 0, kNumErr * sizeof(int), s) != cudaSuccess) return SMASH_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SMASH_ERR_CUDA;
+    const int st = status_from_flags((const long long *)hb);
+    // a row that failed may have left a dense accumulator dirty: drop them
+    if (st != SMASH_OK) release(h, h->dense_acc);
+    return st;
+}
+
+inline int last_cuda_status() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SMASH_OK : SMASH_ERR_CUDA;
+}
+
+inline BinRule sym_rule(const smash_handle *h, int64_t ncols) {
+    BinRule r;
+    r.inv_load = 1.0f / h->params.max_load;
+    int mt = h->params.sym_max_tbits;
+    // key-only table of 2^mt ints plus the staging of a 1024-thread group
+    while (mt > kMinTBits && ((size_t)4 << mt) + 24 * 1024 > (size_t)max_smem_per_block()) --mt;
+    r.max_tbits = mt;
+    r.dense_ok = (h->params.sym_dense_ratio > 0 && ncols <= dense_bitmap_max_cols()) ? 1 : 0;
+    r.dense_min = r.dense_ok ? (ncols + h->params.sym_dense_ratio - 1) / h->params.sym_dense_ratio : (1ll << 62);
+    if (r.dense_min < 1) r.dense_min = 1;
+    return r;
+}
+
+inline BinRule num_rule(const smash_handle *h, int64_t ncols, int dtype) {
+    BinRule r;
+    r.inv_load = 1.0f / h->params.max_load;
+    const bool dense_fits = num_dense_cluster_size(dtype, (int)ncols, h->params.cluster_max,
+                                                   h->params.hot_cols) > 0 ||
+                            ncols <= dense_bitmap_max_cols();
+    r.dense_ok = (h->params.dense_ratio > 0 && dense_fits) ? 1 : 0;
+    r.dense_min = r.dense_ok ? (ncols + h->params.dense_ratio - 1) / h->params.dense_ratio : (1ll << 62);
+    if (r.dense_min < 1) r.dense_min = 1;
+    int mt = h->params.num_max_tbits;
+    // The largest tables are one 1024-thread group; if their rows would want
+    // the bitmap write-out but it does not fit, let them take the dense path.
+    while (mt > kMinTBits) {
+        const int words = (int)((ncols + 31) / 32);
+        const long long n_small = (long long)((1ll << (mt - 1)) * h->params.max_load);
+        const bool want_bm = h->params.bitmap_ratio > 0 && words <= (long long)h->params.bitmap_ratio * n_small;
+        const bool fits_plain = num_hash_bitmap_fits(dtype, mt, 0);
+        const bool fits_bm = num_hash_bitmap_fits(dtype, mt, (int)ncols);
+        if (fits_plain && (!want_bm || fits_bm || !r.dense_ok)) break;
+        --mt;
+    }
+    r.max_tbits = mt;
+    return r;
+}
+
+inline int group_threads(const HashLaunch &hl) {
+    int t = 1 << (hl.tbits > hl.group_shift ? hl.tbits - hl.group_shift : 0);
+    return t < 32 ? 32 : (t > 1024 ? 1024 : t);
+}
+
+inline HashLaunch hash_launch(const smash_handle *h, int tbits, int64_t ncols) {
+    HashLaunch hl;
+    hl.tbits = tbits;
+    hl.group_shift = h->params.group_shift;
+    hl.hash_kind = h->params.hash_kind;
+    hl.colbits = colbits_of(ncols);
+    hl.sms = h->sms;
+    hl.blocks_per_sm = h->params.spill_blocks_per_sm > 0 ? h->params.spill_blocks_per_sm : 1;
+    hl.cluster_max = h->params.cluster_max;
+    return hl;
+}
+
+}  // namespace host
+}  // namespace smash
+
+namespace smash {
+namespace host {
+
+// Bin drivers (api.cu). They plan the rows of A (all rows, or the rows of
+// row_list), scatter them into bins and launch one kernel per non-empty bin.
+//   run_symbolic: writes the exact count of every planned row to nnz_out.
+//   run_numeric:  fills the planned rows of `out` (exact or capacity mode);
+//                 c_rp gives each planned row its size.
+int run_symbolic(smash_handle *h, const RawOperands &op, int64_t n, Plan &pl, int *nnz_out, cudaStream_t s,
+                 const int *row_list, int64_t list_n);
+int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const NumOut &out, Plan &pl,
+                cudaStream_t s, const int *row_list, int64_t list_n);
+
+}  // namespace host
+}  // namespace smash

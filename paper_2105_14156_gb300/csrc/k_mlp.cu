@@ -1,0 +1,366 @@
+// Row-size predictor: features, inference and training kernels.
+//
+// Not part of the paper: a multilayer perceptron predicts y_i = log(1 +
+// nnz(C_i)) of every output row from six features of the row, so that hash
+// tables, bins and C's staging allocation can be sized without the exact
+// symbolic pass (rows whose prediction proves too small fall back to the exact
+// path). Network: x = (f - mean) * inv_std (6 inputs), h1 = relu(W1 x + b1),
+// h2 = relu(W2 h1 + b2) (64 units each), y = w3 . h2 + b3. Parameters are one
+// flat float vector W1 (64x6, row-major), b1, W2 (64x64, row-major), b2, w3,
+// b3. Inference reads a bfloat16 copy of the weights and accumulates in fp32;
+// training keeps fp32 master weights and Adam moments.
+//
+// The features of row i are computed from the row pointers alone (the same
+// information as the flop count of the Window Distribution Phase):
+//   f0 = log1p(nnz(A_i))            f1 = log1p(flop_i)
+//   f2 = log1p(max_k |B_k|)         f3 = log1p(flop_i / nnz(A_i))
+//   f4 = log1p(min(flop_i, cols))   f5 = min(flop_i, cols) / cols
+#include <cuda_bf16.h>
+
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace smash {
+
+constexpr int kHid = 64;
+constexpr int kFeat = 6;
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kHid * kFeat;
+constexpr int kOffW2 = kOffB1 + kHid;
+constexpr int kOffB2 = kOffW2 + kHid * kHid;
+constexpr int kOffW3 = kOffB2 + kHid;
+constexpr int kOffB3 = kOffW3 + kHid;
+static_assert(kOffB3 + 1 == kMlpParams, "parameter layout");
+
+// One warp per row (all rows, or the rows of a list).
+__global__ void __launch_bounds__(256) k_features(RawOperands op, const int *row_list, int64_t nrows, float *feats,
+                                                  long long *bound, int *err) {
+    const int lane = lane_id();
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += warps) {
+        const int64_t i = row_list ? row_list[r] : r;
+        int64_t ab = __ldg(op.a_rp + i), ae = __ldg(op.a_rp + i + 1);
+        if (ab < 0 || ae < ab || ae > op.a_nnz) {
+            if (lane == 0) raise_err(err, kErrBadRowPtr);
+            ab = ae = 0;
+        }
+        long long f = 0, mx = 0;
+        for (int64_t e = ab + lane; e < ae; e += 32) {
+            const int k = __ldg(op.a_ci + e);
+            if ((unsigned)k < (unsigned)op.b_rows) {
+                const int64_t s = __ldg(op.b_rp + k), t = __ldg(op.b_rp + k + 1);
+                if (s >= 0 && t >= s && t <= op.b_nnz) {
+                    f += t - s;
+                    mx = (t - s) > mx ? (t - s) : mx;
+                }
+            }
+        }
+        f = warp_sum(f);
+        mx = warp_max(mx);
+        if (lane == 0) {
+            const double na = (double)(ae - ab);
+            const long long ub = f < (long long)op.ncols ? f : (long long)op.ncols;
+            float *x = feats + (size_t)i * kFeat;
+            x[0] = (float)log1p(na);
+            x[1] = (float)log1p((double)f);
+            x[2] = (float)log1p((double)mx);
+            x[3] = (float)log1p(na > 0 ? (double)f / na : 0.0);
+            x[4] = (float)log1p((double)ub);
+            x[5] = op.ncols > 0 ? (float)((double)ub / (double)op.ncols) : 0.f;
+            if (bound) bound[i] = ub;
+        }
+    }
+}
+
+// Inference: one thread per row. cap_i = clamp(ceil((1+margin) expm1(y_i)), 1, bound_i);
+// rows with bound 0 get cap 0. Weights: bf16 in global memory, fp32 in shared.
+__global__ void __launch_bounds__(256) k_mlp_infer(const float *feats, const long long *bound, const int *row_list,
+                                                   int64_t nrows, const __nv_bfloat16 *wb, const float *norm,
+                                                   float margin, float *y_out, int *cap_out) {
+    __shared__ float w[kMlpParams];
+    __shared__ float nm[2 * kFeat];
+    for (int k = threadIdx.x; k < kMlpParams; k += blockDim.x) w[k] = __bfloat162float(wb[k]);
+    if (threadIdx.x < 2 * kFeat) nm[threadIdx.x] = norm[threadIdx.x];
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += stride) {
+        const int64_t i = row_list ? row_list[r] : r;
+        float x[kFeat];
+#pragma unroll
+        for (int c = 0; c < kFeat; ++c) x[c] = (feats[(size_t)i * kFeat + c] - nm[c]) * nm[kFeat + c];
+        float h1[kHid];
+#pragma unroll
+        for (int u = 0; u < kHid; ++u) {
+            float a = w[kOffB1 + u];
+#pragma unroll
+            for (int c = 0; c < kFeat; ++c) a = fmaf(w[kOffW1 + u * kFeat + c], x[c], a);
+            h1[u] = fmaxf(a, 0.f);
+        }
+        float y = w[kOffB3];
+        for (int u = 0; u < kHid; ++u) {
+            float a = w[kOffB2 + u];
+#pragma unroll
+            for (int v = 0; v < kHid; ++v) a = fmaf(w[kOffW2 + u * kHid + v], h1[v], a);
+            y = fmaf(w[kOffW3 + u], fmaxf(a, 0.f), y);
+        }
+        if (y_out) y_out[r] = y;
+        if (cap_out) {
+            const long long ub = bound[i];
+            long long cap = 0;
+            if (ub > 0) {
+                const double pred = expm1((double)fminf(y, 40.f));
+                double c = ceil((1.0 + (double)margin) * pred);
+                if (!(c >= 1.0)) c = 1.0;
+                cap = c > (double)ub ? ub : (long long)c;
+            }
+            cap_out[i] = (int)cap;
+        }
+    }
+}
+
+// Training: loss and gradient of a minibatch, TILE samples per block.
+// Sample s of minibatch step uses data index perm(base + s) with
+// perm(q) = (a*q + c) mod n, a coprime with n (a fresh c per epoch).
+constexpr int kTile = 64;
+
+struct Batch {
+    int64_t n;          // data size
+    int64_t first;      // first position of this minibatch in the epoch's order
+    int64_t count;      // samples in the minibatch
+    unsigned long long mul;  // a
+    const unsigned long long *shift;  // c (device, per epoch); nullptr: 0
+    float scale;        // 1 / count (the mean of the squared errors)
+};
+
+__global__ void __launch_bounds__(kTile) k_mlp_grad(const float *feats, const float *targets, Batch bt,
+                                                    const float *params, const float *norm, float *grad,
+                                                    float *loss_acc) {
+    extern __shared__ __align__(16) float sm[];
+    float *w = sm;                                  // kMlpParams
+    float *sh1 = w + ((kMlpParams + 3) & ~3);       // [kHid][kTile]
+    float *sh2 = sh1 + kHid * kTile;                // [kHid][kTile]
+    float *sdh2 = sh2 + kHid * kTile;               // [kHid][kTile]
+    float *sdh1 = sdh2 + kHid * kTile;              // [kHid][kTile]
+    float *sx = sdh1 + kHid * kTile;                // [kFeat][kTile]
+    float *sdy = sx + kFeat * kTile;                // [kTile]
+    __shared__ float nm[2 * kFeat];
+    const int t = threadIdx.x;
+    for (int k = t; k < kMlpParams; k += kTile) w[k] = params[k];
+    if (t < 2 * kFeat) nm[t] = norm[t];
+    __syncthreads();
+    const unsigned long long c = bt.shift ? *bt.shift : 0ull;
+    for (int64_t base = (int64_t)blockIdx.x * kTile; base < bt.count; base += (int64_t)gridDim.x * kTile) {
+        const int64_t q = base + t;
+        const bool valid = q < bt.count;
+        float x[kFeat];
+        float tgt = 0.f;
+        if (valid) {
+            const unsigned long long pos = (unsigned long long)(bt.first + q);
+            const int64_t idx = (int64_t)((bt.mul * (pos % (unsigned long long)bt.n) + c) %
+                                          (unsigned long long)bt.n);
+#pragma unroll
+            for (int k = 0; k < kFeat; ++k) x[k] = (feats[(size_t)idx * kFeat + k] - nm[k]) * nm[kFeat + k];
+            tgt = targets[idx];
+        } else {
+#pragma unroll
+            for (int k = 0; k < kFeat; ++k) x[k] = 0.f;
+        }
+        // forward
+        float h1[kHid];
+#pragma unroll
+        for (int u = 0; u < kHid; ++u) {
+            float a = w[kOffB1 + u];
+#pragma unroll
+            for (int k = 0; k < kFeat; ++k) a = fmaf(w[kOffW1 + u * kFeat + k], x[k], a);
+            h1[u] = fmaxf(a, 0.f);
+            sh1[u * kTile + t] = h1[u];
+        }
+        float y = w[kOffB3];
+        for (int u = 0; u < kHid; ++u) {
+            float a = w[kOffB2 + u];
+#pragma unroll
+            for (int v = 0; v < kHid; ++v) a = fmaf(w[kOffW2 + u * kHid + v], h1[v], a);
+            const float h = fmaxf(a, 0.f);
+            sh2[u * kTile + t] = h;
+            y = fmaf(w[kOffW3 + u], h, y);
+        }
+        const float r = valid ? (y - tgt) : 0.f;
+        const float dy = 2.f * r * bt.scale;
+        sdy[t] = dy;
+        float lsum = warp_sum(r * r * bt.scale);
+        if (lane_id() == 0 && loss_acc) atomicAdd(loss_acc, lsum);
+        // backward through layer 2 and 1 (per sample)
+        for (int u = 0; u < kHid; ++u) sdh2[u * kTile + t] = sh2[u * kTile + t] > 0.f ? dy * w[kOffW3 + u] : 0.f;
+        for (int v = 0; v < kHid; ++v) {
+            float a = 0.f;
+            for (int u = 0; u < kHid; ++u) a = fmaf(w[kOffW2 + u * kHid + v], sdh2[u * kTile + t], a);
+            sdh1[v * kTile + t] = h1[v] > 0.f ? a : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < kFeat; ++k) sx[k * kTile + t] = x[k];
+        __syncthreads();
+        // parameter gradients: sums over the tile's samples
+        for (int p = t; p < kHid * kHid; p += kTile) {
+            const int u = p / kHid, v = p % kHid;
+            float a = 0.f;
+            for (int s = 0; s < kTile; ++s) a = fmaf(sdh2[u * kTile + s], sh1[v * kTile + s], a);
+            atomicAdd(grad + kOffW2 + p, a);
+        }
+        for (int p = t; p < kHid * kFeat; p += kTile) {
+            const int u = p / kFeat, k = p % kFeat;
+            float a = 0.f;
+            for (int s = 0; s < kTile; ++s) a = fmaf(sdh1[u * kTile + s], sx[k * kTile + s], a);
+            atomicAdd(grad + kOffW1 + p, a);
+        }
+        {
+            const int u = t;   // kTile == kHid
+            float gb1 = 0.f, gb2 = 0.f, gw3 = 0.f;
+            for (int s = 0; s < kTile; ++s) {
+                gb1 += sdh1[u * kTile + s];
+                gb2 += sdh2[u * kTile + s];
+                gw3 = fmaf(sdy[s], sh2[u * kTile + s], gw3);
+            }
+            atomicAdd(grad + kOffB1 + u, gb1);
+            atomicAdd(grad + kOffB2 + u, gb2);
+            atomicAdd(grad + kOffW3 + u, gw3);
+        }
+        if (t < 32) {
+            float g = sdy[t] + sdy[t + 32];
+            g = warp_sum(g);
+            if (t == 0) atomicAdd(grad + kOffB3, g);
+        }
+        __syncthreads();
+    }
+}
+
+// Adam step on all parameters (then the gradient is cleared and the bf16 copy refreshed).
+__global__ void __launch_bounds__(256) k_adam(float *params, float *grad, float *m, float *v, __nv_bfloat16 *wb,
+                                              float lr, float b1, float b2, float eps, float wd,
+                                              const unsigned long long *stepc) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const float step = (float)(*stepc + 1);
+    if (p < kMlpParams) {
+        const float g = grad[p] + wd * params[p];
+        const float mm = b1 * m[p] + (1.f - b1) * g;
+        const float vv = b2 * v[p] + (1.f - b2) * g * g;
+        m[p] = mm;
+        v[p] = vv;
+        const float mh = mm / (1.f - powf(b1, step));
+        const float vh = vv / (1.f - powf(b2, step));
+        const float w = params[p] - lr * mh / (sqrtf(vh) + eps);
+        params[p] = w;
+        wb[p] = __float2bfloat16(w);
+        grad[p] = 0.f;
+    }
+}
+
+__global__ void k_counter_add(unsigned long long *c, unsigned long long d) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *c += d;
+}
+
+// Per-epoch permutation shift: c_e = splitmix(seed, epoch) mod n.
+__global__ void k_epoch_shift(unsigned long long *epoch, unsigned long long *shift, unsigned long long seed,
+                              unsigned long long n) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        unsigned long long z = seed + (*epoch + 1ull) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        *shift = n ? z % n : 0ull;
+        *epoch += 1ull;
+    }
+}
+
+// Feature statistics: sums and sums of squares per feature (double).
+__global__ void __launch_bounds__(256) k_feat_stats(const float *feats, int64_t n, double *acc) {
+    double s[kFeat], q[kFeat];
+#pragma unroll
+    for (int k = 0; k < kFeat; ++k) s[k] = q[k] = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+#pragma unroll
+        for (int k = 0; k < kFeat; ++k) {
+            const double x = feats[(size_t)i * kFeat + k];
+            s[k] += x;
+            q[k] += x * x;
+        }
+#pragma unroll
+    for (int k = 0; k < kFeat; ++k) {
+        s[k] = warp_sum(s[k]);
+        q[k] = warp_sum(q[k]);
+        if (lane_id() == 0) {
+            atomicAdd(acc + k, s[k]);
+            atomicAdd(acc + kFeat + k, q[k]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+void launch_features(const RawOperands &op, const int *row_list, int64_t nrows, float *feats, long long *bound,
+                     int *err, int sms, cudaStream_t s) {
+    if (nrows <= 0) return;
+    const int64_t blocks = (nrows + 7) / 8;
+    const int64_t cap = (int64_t)sms * 8;
+    k_features<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(op, row_list, nrows, feats, bound, err);
+}
+
+void launch_mlp_infer(const float *feats, const long long *bound, const int *row_list, int64_t nrows,
+                      const void *wb, const float *norm, float margin, float *y_out, int *cap_out, int sms,
+                      cudaStream_t s) {
+    if (nrows <= 0) return;
+    const int64_t blocks = (nrows + 255) / 256;
+    const int64_t cap = (int64_t)sms * 4;
+    k_mlp_infer<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(feats, bound, row_list, nrows,
+                                                                     (const __nv_bfloat16 *)wb, norm, margin, y_out,
+                                                                     cap_out);
+}
+
+static size_t grad_smem() {
+    return (size_t)(((kMlpParams + 3) & ~3) + 4 * kHid * kTile + kFeat * kTile + kTile) * sizeof(float);
+}
+
+void launch_mlp_grad(const float *feats, const float *targets, int64_t n, int64_t first, int64_t count,
+                     unsigned long long mul, const unsigned long long *shift, const float *params, const float *norm,
+                     float *grad, float *loss_acc, int sms, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem());
+        attr = true;
+    }
+    if (count <= 0) return;
+    Batch bt{n, first, count, mul, shift, 1.0f / (float)count};
+    const int64_t tiles = (count + kTile - 1) / kTile;
+    const int64_t cap = (int64_t)sms * 2;
+    k_mlp_grad<<<(int)(tiles < cap ? tiles : cap), kTile, grad_smem(), s>>>(feats, targets, bt, params, norm, grad,
+                                                                           loss_acc);
+}
+
+void launch_adam(float *params, float *grad, float *m, float *v, void *wb, float lr, float b1, float b2, float eps,
+                 float wd, unsigned long long *stepc, cudaStream_t s) {
+    k_adam<<<(kMlpParams + 255) / 256, 256, 0, s>>>(params, grad, m, v, (__nv_bfloat16 *)wb, lr, b1, b2, eps, wd,
+                                                    stepc);
+    k_counter_add<<<1, 32, 0, s>>>(stepc, 1ull);
+}
+
+void launch_epoch_shift(unsigned long long *epoch, unsigned long long *shift, unsigned long long seed,
+                        unsigned long long n, cudaStream_t s) {
+    k_epoch_shift<<<1, 32, 0, s>>>(epoch, shift, seed, n);
+}
+
+__global__ void k_to_bf16(const float *src, __nv_bfloat16 *dst, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = __float2bfloat16(src[i]);
+}
+
+void launch_to_bf16(const float *src, void *dst, int n, cudaStream_t s) {
+    if (n > 0) k_to_bf16<<<(n + 255) / 256, 256, 0, s>>>(src, (__nv_bfloat16 *)dst, n);
+}
+
+void launch_feat_stats(const float *feats, int64_t n, double *acc, int sms, cudaStream_t s) {
+    if (n <= 0) return;
+    const int64_t blocks = (n + 255) / 256;
+    const int64_t cap = (int64_t)sms * 4;
+    k_feat_stats<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(feats, n, acc);
+}
+
+}  // namespace smash

@@ -27,12 +27,18 @@ namespace smash {
 
 namespace cg = cooperative_groups;
 
+// Output of a numeric launch. Exact mode (row_nnz == nullptr): c_rp is C's
+// row pointer and every row must have exactly c_rp[i+1]-c_rp[i] entries.
+// Capacity mode (learned sizing): c_rp gives each row a capacity; a row that
+// fits is written at the start of its range and row_nnz[i] receives its
+// length, a row that does not fit (or whose table filled up) gets -1.
 template <typename V>
 struct NumOutT {
     const int64_t *c_rp;
     int32_t *c_ci;
     V *c_val;
     int64_t c_nnz;
+    int *row_nnz;
 };
 
 template <typename V>
@@ -226,7 +232,7 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
         G::sync();
         int64_t ab = 0, ae = 0;
         if (ok) a_row_range(op, i, ab, ae, err);
-        int cnt = 0;
+        int cnt = 0, ovf = 0;
         row_products<V, true, GS, NT>(op, ab, ae, sc, err, [&](int j, V a, int64_t idx) {
             const V v = a * b_value(op, idx);
             bool ins;
@@ -234,6 +240,8 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
             if (h >= 0) {
                 atomicAdd(vals + h, v);
                 cnt += ins ? 1 : 0;
+            } else if (out.row_nnz) {
+                ovf = 1;
             } else {
                 raise_err(err, kErrTableFull);
             }
@@ -245,10 +253,22 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
         } else {
             tot = G::template sum<int>(cnt, sc.red);
         }
-        if (t == 0 && tot != n_exp) raise_err(err, kErrCountMismatch);
-        if (GS == 32 && tot <= 32) writeout_warp_rank<V>(keys, vals, T, tot, n_exp, out, c0);
-        else if (use_bm) writeout_bitmap<V, GS, NT>(keys, vals, T, bm, pre, bm_words, n_exp, out, c0, sc.red);
-        else writeout_bitonic<V, GS, NT>(keys, vals, T, n_exp, out, c0, sc.red);
+        bool over = false;
+        if (out.row_nnz) {
+            int o;
+            if constexpr (GS == 32) o = __any_sync(kFull, ovf);
+            else o = G::template sum<int>(ovf, sc.red);
+            over = o != 0 || tot > n_exp;
+            if (t == 0) out.row_nnz[i] = over ? -1 : tot;
+            n_exp = tot;
+        } else if (t == 0 && tot != n_exp) {
+            raise_err(err, kErrCountMismatch);
+        }
+        if (!over) {
+            if (GS == 32 && tot <= 32) writeout_warp_rank<V>(keys, vals, T, tot, n_exp, out, c0);
+            else if (use_bm) writeout_bitmap<V, GS, NT>(keys, vals, T, bm, pre, bm_words, n_exp, out, c0, sc.red);
+            else writeout_bitonic<V, GS, NT>(keys, vals, T, n_exp, out, c0, sc.red);
+        }
         G::sync();
     }
 }
@@ -293,7 +313,13 @@ __global__ void __launch_bounds__(NT) k_num_dense(Operands<V> op, const int *row
         __syncthreads();
         const int tot = bitmap_prefix<NT, NT>(bm, pre, words, sc.red);
         __syncthreads();
-        if (t == 0 && tot != n_exp) raise_err(err, kErrCountMismatch);
+        if (out.row_nnz) {
+            const bool over = tot > n_exp;
+            if (t == 0) out.row_nnz[i] = over ? -1 : tot;
+            if (over) n_exp = 0;   // still drain the accumulator below, write nothing
+        } else if (t == 0 && tot != n_exp) {
+            raise_err(err, kErrCountMismatch);
+        }
         for (int w = t; w < words; w += NT) {
             unsigned bits = bm[w];
             int pos = pre[w];
@@ -418,7 +444,13 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(1024)
         }
         __syncthreads();
         const int base = s_base;
-        if (rank == 0 && t == 0 && s_total != n_exp) raise_err(err, kErrCountMismatch);
+        if (out.row_nnz) {
+            const bool over = s_total > n_exp;
+            if (rank == 0 && t == 0) out.row_nnz[i] = over ? -1 : s_total;
+            if (over) n_exp = 0;   // still drain the accumulator below, write nothing
+        } else if (rank == 0 && t == 0 && s_total != n_exp) {
+            raise_err(err, kErrCountMismatch);
+        }
         for (int w = t; w < words; w += NT) {
             unsigned bits = bm[w];
             int pos = base + pre[w];
@@ -499,7 +531,7 @@ __global__ void __launch_bounds__(NT) k_num_spill(Operands<V> op, const int *row
         __syncthreads();
         int64_t ab = 0, ae = 0;
         if (ok) a_row_range(op, i, ab, ae, err);
-        int cnt = 0;
+        int cnt = 0, ovf = 0;
         row_products<V, true, NT, NT>(op, ab, ae, sc, err, [&](int j, V a, int64_t idx) {
             const V v = a * b_value(op, idx);
             bool ins;
@@ -507,13 +539,23 @@ __global__ void __launch_bounds__(NT) k_num_spill(Operands<V> op, const int *row
             if (h >= 0) {
                 atomicAdd(vals + h, v);
                 cnt += ins ? 1 : 0;
+            } else if (out.row_nnz) {
+                ovf = 1;
             } else {
                 raise_err(err, kErrTableFull);
             }
         });
         __threadfence();
-        const int tot = G::template sum<int>(cnt, sc.red);
-        if (t == 0 && tot != n_exp) raise_err(err, kErrCountMismatch);
+        int tot = G::template sum<int>(cnt, sc.red);
+        if (out.row_nnz) {
+            const int o = G::template sum<int>(ovf, sc.red);
+            const bool over = o != 0 || tot > n_exp;
+            if (t == 0) out.row_nnz[i] = over ? -1 : tot;
+            n_exp = tot;
+            if (over) tot = 0;   // nothing to write
+        } else if (t == 0 && tot != n_exp) {
+            raise_err(err, kErrCountMismatch);
+        }
         int mn = INT_MAX, mx = INT_MIN;
         for (int s = t; s < T; s += NT) {
             const int k = __ldcg(keys + s);
@@ -589,7 +631,7 @@ static Operands<V> num_operands(const RawOperands &r) {
 
 template <typename V>
 static NumOutT<V> num_out(const NumOut &o) {
-    return NumOutT<V>{o.c_rp, o.c_ci, (V *)o.c_val, o.c_nnz};
+    return NumOutT<V>{o.c_rp, o.c_ci, (V *)o.c_val, o.c_nnz, o.row_nnz};
 }
 
 static int threads_per_row(int tbits, int shift) {

@@ -23,7 +23,8 @@ __device__ __forceinline__ int bin_for(long long size, const BinRule &r) {
 // the bound min(flop_i, cols(B)) in the symbolic phase (c_rp == nullptr) and
 // the exact length c_rp[i+1] - c_rp[i] in the numeric phase.
 __global__ void __launch_bounds__(256) k_rowinfo(RawOperands op, const int64_t *c_rp, int64_t c_nnz, BinRule rule,
-                                                 BinBuffers bb, long long *bound_out, int *nnz_out, int *err) {
+                                                 BinBuffers bb, long long *bound_out, int *nnz_out, int *err,
+                                                 const int *row_list, int64_t nrows) {
     __shared__ int s_cnt[kNumBins];
     __shared__ long long s_max[kNumBins];
     __shared__ long long s_sum[3][kNumBins];
@@ -41,7 +42,8 @@ __global__ void __launch_bounds__(256) k_rowinfo(RawOperands op, const int64_t *
     const int lane = lane_id();
     long long my_prod = 0, my_max = 0;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < op.a_rows; i += warps) {
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += warps) {
+        const int64_t i = row_list ? row_list[r] : r;
         int64_t ab = __ldg(op.a_rp + i), ae = __ldg(op.a_rp + i + 1);
         if (ab < 0 || ae < ab || ae > op.a_nnz) {
             if (lane == 0) raise_err(err, kErrBadRowPtr);
@@ -235,15 +237,74 @@ static int rowinfo_grid(int64_t rows, int sms) {
 }
 
 void launch_sym_rowinfo(const RawOperands &op, const BinRule &rule, BinBuffers bb, long long *bound_out,
-                        int *nnz_out, int *err, int sms, cudaStream_t s) {
-    if (op.a_rows == 0) return;
-    k_rowinfo<<<rowinfo_grid(op.a_rows, sms), 256, 0, s>>>(op, nullptr, 0, rule, bb, bound_out, nnz_out, err);
+                        int *nnz_out, int *err, int sms, cudaStream_t s, const int *row_list, int64_t list_n) {
+    const int64_t n = row_list ? list_n : op.a_rows;
+    if (n == 0) return;
+    k_rowinfo<<<rowinfo_grid(n, sms), 256, 0, s>>>(op, nullptr, 0, rule, bb, bound_out, nnz_out, err, row_list, n);
 }
 
 void launch_num_rowinfo(const RawOperands &op, const int64_t *c_rp, int64_t c_nnz, const BinRule &rule,
-                        BinBuffers bb, int *err, int sms, cudaStream_t s) {
-    if (op.a_rows == 0) return;
-    k_rowinfo<<<rowinfo_grid(op.a_rows, sms), 256, 0, s>>>(op, c_rp, c_nnz, rule, bb, nullptr, nullptr, err);
+                        BinBuffers bb, int *err, int sms, cudaStream_t s, const int *row_list, int64_t list_n) {
+    const int64_t n = row_list ? list_n : op.a_rows;
+    if (n == 0) return;
+    k_rowinfo<<<rowinfo_grid(n, sms), 256, 0, s>>>(op, c_rp, c_nnz, rule, bb, nullptr, nullptr, err, row_list, n);
+}
+
+// Rows whose staged result did not fit (row_nnz < 0): appended to list.
+__global__ void __launch_bounds__(256) k_overflow_list(const int *row_nnz, int64_t n, int *list, int *count,
+                                                       uint8_t *ovf) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const bool o = row_nnz[i] < 0;
+        ovf[i] = o ? 1 : 0;
+        const unsigned m = __ballot_sync(__activemask(), o);
+        if (o) {
+            const int leader = __ffs(m) - 1;
+            int base = 0;
+            if (lane_id() == leader) base = atomicAdd(count, __popc(m));
+            base = __shfl_sync(m, base, leader);
+            list[base + __popc(m & lanemask_lt())] = (int)i;
+        }
+    }
+}
+
+void launch_overflow_list(const int *row_nnz, int64_t n, int *list, int *count, uint8_t *ovf, cudaStream_t s) {
+    if (n == 0) return;
+    const int64_t blocks = (n + 255) / 256;
+    k_overflow_list<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(row_nnz, n, list, count, ovf);
+}
+
+// Copy each staged row that fitted to its place in C (one warp per row).
+template <typename V>
+__global__ void __launch_bounds__(256) k_compact_rows(int64_t n, const int64_t *stage_rp, const int *len,
+                                                      const uint8_t *ovf, const int32_t *sci, const V *sval,
+                                                      const int64_t *c_rp, int32_t *cci, V *cval) {
+    const int lane = lane_id();
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        if (ovf[i]) continue;
+        const int64_t src = stage_rp[i], dst = c_rp[i];
+        const int m = len[i];
+        for (int k = lane; k < m; k += 32) {
+            cci[dst + k] = sci[src + k];
+            cval[dst + k] = sval[src + k];
+        }
+    }
+}
+
+void launch_compact_rows(int dtype, int64_t n, const int64_t *stage_rp, const int *row_nnz_final,
+                         const uint8_t *ovf, const int32_t *stage_ci, const void *stage_val, const int64_t *c_rp,
+                         int32_t *c_ci, void *c_val, int sms, cudaStream_t s) {
+    if (n == 0) return;
+    const int64_t blocks = (n + 7) / 8;
+    const int64_t cap = (int64_t)sms * 16;
+    const int grid = (int)(blocks < cap ? blocks : cap);
+    if (dtype)
+        k_compact_rows<double><<<grid, 256, 0, s>>>(n, stage_rp, row_nnz_final, ovf, stage_ci,
+                                                    (const double *)stage_val, c_rp, c_ci, (double *)c_val);
+    else
+        k_compact_rows<float><<<grid, 256, 0, s>>>(n, stage_rp, row_nnz_final, ovf, stage_ci,
+                                                   (const float *)stage_val, c_rp, c_ci, (float *)c_val);
 }
 
 void launch_bin_scatter(int64_t n, BinBuffers bb, cudaStream_t s) {

@@ -41,11 +41,37 @@ struct BinBuffers {
     long long *sums;   // [3][16] per bin: sum nnz(A_i), sum flop_i, sum size bound
 };
 
-// k_rows.cu
+// k_rows.cu. With row_list != nullptr only the listed rows are planned (the
+// caller clears bb.bin first so that the other rows stay in the empty bin).
 void launch_sym_rowinfo(const RawOperands &op, const BinRule &rule, BinBuffers bb, long long *bound_out,
-                        int *nnz_out, int *err, int sms, cudaStream_t s);
+                        int *nnz_out, int *err, int sms, cudaStream_t s, const int *row_list = nullptr,
+                        int64_t list_n = 0);
 void launch_num_rowinfo(const RawOperands &op, const int64_t *c_rp, int64_t c_nnz, const BinRule &rule,
-                        BinBuffers bb, int *err, int sms, cudaStream_t s);
+                        BinBuffers bb, int *err, int sms, cudaStream_t s, const int *row_list = nullptr,
+                        int64_t list_n = 0);
+// Learned path helpers (k_rows.cu): rows with row_nnz < 0 -> list; copy the
+// staged rows that fitted into C.
+void launch_overflow_list(const int *row_nnz, int64_t n, int *list, int *count, uint8_t *ovf, cudaStream_t s);
+void launch_compact_rows(int dtype, int64_t n, const int64_t *stage_rp, const int *row_nnz_final,
+                         const uint8_t *ovf, const int32_t *stage_ci, const void *stage_val, const int64_t *c_rp,
+                         int32_t *c_ci, void *c_val, int sms, cudaStream_t s);
+
+// k_mlp.cu: row-size predictor (see the file for the network).
+constexpr int kMlpParams = 4673;
+void launch_features(const RawOperands &op, const int *row_list, int64_t nrows, float *feats, long long *bound,
+                     int *err, int sms, cudaStream_t s);
+void launch_mlp_infer(const float *feats, const long long *bound, const int *row_list, int64_t nrows,
+                      const void *wb, const float *norm, float margin, float *y_out, int *cap_out, int sms,
+                      cudaStream_t s);
+void launch_mlp_grad(const float *feats, const float *targets, int64_t n, int64_t first, int64_t count,
+                     unsigned long long mul, const unsigned long long *shift, const float *params, const float *norm,
+                     float *grad, float *loss_acc, int sms, cudaStream_t s);
+void launch_adam(float *params, float *grad, float *m, float *v, void *wb, float lr, float b1, float b2, float eps,
+                 float wd, unsigned long long *stepc, cudaStream_t s);
+void launch_epoch_shift(unsigned long long *epoch, unsigned long long *shift, unsigned long long seed,
+                        unsigned long long n, cudaStream_t s);
+void launch_feat_stats(const float *feats, int64_t n, double *acc, int sms, cudaStream_t s);
+void launch_to_bf16(const float *src, void *dst, int n, cudaStream_t s);
 void launch_bin_scatter(int64_t n, BinBuffers bb, cudaStream_t s);
 size_t scan_scratch_bytes(int64_t n);
 void launch_scan_rowptr(const int *nnz, int64_t n, int64_t *c_rp, long long *total,
@@ -77,6 +103,7 @@ struct NumOut {
     int32_t *c_ci;
     void *c_val;
     int64_t c_nnz;
+    int *row_nnz = nullptr;  // capacity mode (learned sizing) when set, see k_numeric.cu
 };
 void launch_num_hash(int dtype, const RawOperands &op, const int *rows, int count, int *token,
                      const HashLaunch &hl, float inv_load, int bitmap_ratio, const NumOut &out, int *err,

@@ -25,7 +25,40 @@ EXPORTS = [
     "smash_default_params", "smash_create", "smash_destroy", "smash_set_params", "smash_get_params",
     "smash_set_allocator", "spgemm_symbolic", "spgemm_numeric", "smash_check", "smash_get_stats",
     "smash_status_string", "smash_set_timing", "smash_get_timings",
+    "smash_train_cfg_default", "smash_model_create", "smash_model_destroy", "smash_model_get", "smash_model_set",
+    "smash_model_save", "smash_model_load", "smash_row_features", "smash_mlp_train", "smash_mlp_gradient",
+    "smash_mlp_predict", "spgemm_learned", "smash_free_csr",
 ]
+MLP_PARAMS = 4673
+
+
+class TrainCfg(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("weight_decay", ctypes.c_float), ("seed", ctypes.c_uint64), ("reserved", ctypes.c_int32 * 4)]
+
+
+class LearnedStats(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("overflow_rows", ctypes.c_int64), ("staged_nnz", ctypes.c_int64),
+                ("c_nnz", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class _DeviceArray:
+    """Zero-copy view of library-allocated device memory (CUDA array interface)."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3}
+
+
+def _view(ptr, n, dtype):
+    import torch
+    if n == 0 or not ptr:
+        return torch.empty(0, dtype=dtype, device="cuda")
+    typestr = {torch.int64: "<i8", torch.int32: "<i4", torch.float32: "<f4", torch.float64: "<f8"}[dtype]
+    return torch.as_tensor(_DeviceArray(ptr, n, typestr), device="cuda")
 
 
 class SmashError(RuntimeError):
@@ -97,6 +130,21 @@ def load_library(path: str = LIB_PATH):
                                           ctypes.POINTER(ctypes.c_int)]
         lib.smash_status_string.argtypes = [ctypes.c_int]
         lib.smash_status_string.restype = ctypes.c_char_p
+        lib.smash_train_cfg_default.argtypes = [ctypes.POINTER(TrainCfg)]
+        lib.smash_model_create.argtypes = [P, ctypes.POINTER(P), ctypes.c_uint64]
+        lib.smash_model_destroy.argtypes = [P]
+        lib.smash_model_get.argtypes = [P, P, P]
+        lib.smash_model_set.argtypes = [P, P, P]
+        lib.smash_model_save.argtypes = [P, ctypes.c_char_p]
+        lib.smash_model_load.argtypes = [P, ctypes.c_char_p]
+        lib.smash_row_features.argtypes = [P, ctypes.POINTER(CsrStruct), ctypes.POINTER(CsrStruct), P, P]
+        lib.smash_mlp_train.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.POINTER(TrainCfg),
+                                        ctypes.POINTER(ctypes.c_float), P]
+        lib.smash_mlp_gradient.argtypes = [P, P, P, P, ctypes.c_int64, P, ctypes.POINTER(ctypes.c_float), P]
+        lib.smash_mlp_predict.argtypes = [P, P, P, ctypes.c_int64, P, P]
+        lib.spgemm_learned.argtypes = [P, ctypes.POINTER(CsrStruct), ctypes.POINTER(CsrStruct), ctypes.c_int, P,
+                                       ctypes.c_float, ctypes.POINTER(CsrStruct), ctypes.POINTER(LearnedStats), P]
+        lib.smash_free_csr.argtypes = [P, ctypes.POINTER(CsrStruct)]
         for name in EXPORTS:
             f = getattr(lib, name)
             if f.restype is None or f.restype is ctypes.c_int:
@@ -265,3 +313,115 @@ class Handle:
         if check:
             self.check(stream)
         return C
+
+    # learned sizing
+    def features(self, A: DeviceCsr, B: DeviceCsr, stream=None):
+        import torch
+        f = torch.empty((A.rows, 6), dtype=torch.float32, device=A.row_ptr.device)
+        sa, sb = A.struct(), B.struct()
+        _check(self.lib.smash_row_features(self.h, ctypes.byref(sa), ctypes.byref(sb), f.data_ptr(),
+                                           _stream_ptr(stream)), "smash_row_features")
+        return f
+
+    def mlp_train(self, model: "Model", feats, targets, stream=None, **cfg) -> float:
+        c = TrainCfg()
+        _check(self.lib.smash_train_cfg_default(ctypes.byref(c)), "smash_train_cfg_default")
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        loss = ctypes.c_float(0)
+        feats = feats.contiguous()
+        targets = targets.contiguous()
+        _check(self.lib.smash_mlp_train(self.h, model.m, feats.data_ptr(), targets.data_ptr(), feats.shape[0],
+                                        ctypes.byref(c), ctypes.byref(loss), _stream_ptr(stream)), "smash_mlp_train")
+        return float(loss.value)
+
+    def mlp_gradient(self, model: "Model", feats, targets, stream=None):
+        import torch
+        g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=feats.device)
+        loss = ctypes.c_float(0)
+        _check(self.lib.smash_mlp_gradient(self.h, model.m, feats.contiguous().data_ptr(),
+                                           targets.contiguous().data_ptr(), feats.shape[0], g.data_ptr(),
+                                           ctypes.byref(loss), _stream_ptr(stream)), "smash_mlp_gradient")
+        return g, float(loss.value)
+
+    def mlp_predict(self, model: "Model", feats, stream=None):
+        import torch
+        y = torch.empty(feats.shape[0], dtype=torch.float32, device=feats.device)
+        _check(self.lib.smash_mlp_predict(self.h, model.m, feats.contiguous().data_ptr(), feats.shape[0],
+                                          y.data_ptr(), _stream_ptr(stream)), "smash_mlp_predict")
+        return y
+
+    def spgemm_learned(self, A: DeviceCsr, B: DeviceCsr, model: "Model", margin: float = 0.15, stream=None):
+        """C = A*B sized by the model. Returns (C as zero-copy views, stats, owner);
+        call owner.free() (or let it be collected) to release C's arrays."""
+        import torch
+        dt = _dtype_code(A.val)
+        sa, sb = A.struct(), B.struct()
+        sc = CsrStruct()
+        st = LearnedStats()
+        _check(self.lib.spgemm_learned(self.h, ctypes.byref(sa), ctypes.byref(sb), dt, model.m, margin,
+                                       ctypes.byref(sc), ctypes.byref(st), _stream_ptr(stream)), "spgemm_learned")
+        owner = LibraryCsr(self, sc)
+        vdt = A.val.dtype
+        C = DeviceCsr(int(sc.rows), int(sc.cols), _view(sc.row_ptr, int(sc.rows) + 1, torch.int64),
+                      _view(sc.col_idx, int(sc.nnz), torch.int32), _view(sc.val, int(sc.nnz), vdt))
+        return C, st.as_dict(), owner
+
+
+class LibraryCsr:
+    """Owner of a CSR whose arrays the library allocated (learned / batched calls)."""
+
+    def __init__(self, handle: Handle, s: CsrStruct):
+        self.handle = handle
+        self.s = s
+
+    def free(self):
+        if self.s is not None and self.handle.h:
+            self.handle.lib.smash_free_csr(self.handle.h, ctypes.byref(self.s))
+        self.s = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Model:
+    """Row-size predictor (weights on the device)."""
+
+    def __init__(self, handle: Handle, seed: int = 1):
+        self.handle = handle
+        self.lib = handle.lib
+        m = ctypes.c_void_p()
+        _check(self.lib.smash_model_create(handle.h, ctypes.byref(m), seed), "smash_model_create")
+        self.m = m
+
+    def close(self):
+        if getattr(self, "m", None):
+            self.lib.smash_model_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get(self):
+        p = np.zeros(MLP_PARAMS, dtype=np.float32)
+        n = np.zeros(12, dtype=np.float32)
+        _check(self.lib.smash_model_get(self.m, p.ctypes.data, n.ctypes.data), "smash_model_get")
+        return p, n
+
+    def set(self, params=None, norm=None):
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        n = None if norm is None else np.ascontiguousarray(norm, dtype=np.float32)
+        _check(self.lib.smash_model_set(self.m, p.ctypes.data if p is not None else None,
+                                        n.ctypes.data if n is not None else None), "smash_model_set")
+
+    def save(self, path: str):
+        _check(self.lib.smash_model_save(self.m, path.encode()), "smash_model_save")
+
+    def load(self, path: str):
+        _check(self.lib.smash_model_load(self.m, path.encode()), "smash_model_load")

@@ -1,0 +1,135 @@
+"""Learned sizing on the GPU: the MLP kernels against the float64 oracle, and
+C = A*B through spgemm_learned against the SpGEMM oracle (structure exact,
+values within tolerance), including forced under-prediction where every
+overflowing row goes through the exact fallback."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as mlp_oracle
+from paper_2105_14156_gb300.rmat import GRAPH500_ABCD, rmat
+from tests.gpu_util import assert_matches_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def handle():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_14156_gb300 import build, smash
+    build.build()
+    h = smash.Handle(0)
+    yield h
+    h.close()
+
+
+@pytest.fixture(scope="module")
+def trained(handle):
+    from paper_2105_14156_gb300 import learned
+    from paper_2105_14156_gb300.rmat import training_matrix
+    mats = [training_matrix(s) for s in (0, 5, 10, 1, 6)]   # scales 12 and 13
+    model, loss, secs, n = learned.train(handle, mats, epochs=40, batch=512)
+    return model, loss, n
+
+
+def bf16_round(x):
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+def test_gradient_matches_oracle(handle):
+    import torch
+    from paper_2105_14156_gb300 import smash
+    rng = np.random.default_rng(3)
+    model = smash.Model(handle, seed=7)
+    p = rng.normal(0, 0.2, smash.MLP_PARAMS).astype(np.float32)
+    norm = np.concatenate([rng.normal(0, 1, 6), rng.uniform(0.5, 2, 6)]).astype(np.float32)
+    model.set(p, norm)
+    feats = rng.normal(0, 2, (1000, 6)).astype(np.float32)
+    targets = rng.normal(0, 1, 1000).astype(np.float32)
+    g, loss = handle.mlp_gradient(model, torch.from_numpy(feats).cuda(), torch.from_numpy(targets).cuda())
+    x = mlp_oracle.normalise(feats, norm[:6].astype(np.float64), norm[6:].astype(np.float64))
+    ref_loss, ref_g = mlp_oracle.loss_and_grad(p.astype(np.float64), x, targets.astype(np.float64))
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(loss - ref_loss) <= 1e-4 * max(1.0, ref_loss)
+    scale = np.max(np.abs(ref_g))
+    assert np.max(np.abs(g - ref_g)) <= 2e-4 * scale, np.max(np.abs(g - ref_g)) / scale
+    model.close()
+
+
+def test_predict_matches_oracle_with_bf16_weights(handle):
+    import torch
+    from paper_2105_14156_gb300 import smash
+    rng = np.random.default_rng(4)
+    model = smash.Model(handle, seed=9)
+    p = rng.normal(0, 0.2, smash.MLP_PARAMS).astype(np.float32)
+    norm = np.concatenate([rng.normal(0, 1, 6), rng.uniform(0.5, 2, 6)]).astype(np.float32)
+    model.set(p, norm)
+    feats = rng.normal(0, 2, (500, 6)).astype(np.float32)
+    y = handle.mlp_predict(model, torch.from_numpy(feats).cuda()).cpu().numpy()
+    x = mlp_oracle.normalise(feats, norm[:6].astype(np.float64), norm[6:].astype(np.float64))
+    ref, _ = mlp_oracle.forward(bf16_round(p).astype(np.float64), x)
+    assert np.max(np.abs(y - ref)) <= 1e-4 * max(1.0, np.max(np.abs(ref)))
+    model.close()
+
+
+def test_save_load_roundtrip(handle, tmp_path):
+    from paper_2105_14156_gb300 import smash
+    m1 = smash.Model(handle, seed=11)
+    p, n = m1.get()
+    path = str(tmp_path / "m.bin")
+    m1.save(path)
+    m2 = smash.Model(handle, seed=12)
+    m2.load(path)
+    p2, n2 = m2.get()
+    assert np.array_equal(p, p2) and np.array_equal(n, n2)
+    m1.close()
+    m2.close()
+
+
+def test_training_reduces_loss(handle, trained):
+    model, loss, n = trained
+    assert n > 10000
+    assert loss < 0.2, loss     # mean squared error of log1p(nnz)
+
+
+@pytest.mark.parametrize("values", ["f64", "f32"])
+def test_learned_matches_oracle(handle, trained, values):
+    from paper_2105_14156_gb300 import smash
+    model, _, _ = trained
+    A = rmat(12, 16, GRAPH500_ABCD, seed=33, values=values)
+    dA = smash.to_device(A)
+    C, stats, owner = handle.spgemm_learned(dA, dA, model, margin=0.15)
+    Ch = C.to_host()
+    owner.free()
+    assert_matches_oracle(Ch, A, A)
+    assert stats["c_nnz"] == Ch.col_idx.size
+    assert stats["overflow_rows"] < 0.2 * A.rows
+
+
+def test_forced_underprediction_falls_back(handle, trained):
+    from paper_2105_14156_gb300 import smash
+    model, _, _ = trained
+    A = rmat(11, 16, GRAPH500_ABCD, seed=34, values="int4")
+    dA = smash.to_device(A)
+    C, stats, owner = handle.spgemm_learned(dA, dA, model, margin=-0.9)
+    Ch = C.to_host()
+    owner.free()
+    assert stats["overflow_rows"] > 0.5 * np.count_nonzero(np.diff(Ch.row_ptr))
+    assert_matches_oracle(Ch, A, A, exact=True)
+
+
+def test_learned_rectangular_and_empty_rows(handle, trained):
+    from paper_2105_14156_gb300 import smash
+    from tests.helpers import random_csr
+    model, _, _ = trained
+    A = random_csr(500, 300, 0.02, 61, values="f64")
+    B = random_csr(300, 900, 0.03, 62, values="f64")
+    for margin in (0.15, -0.5, 3.0):
+        C, stats, owner = handle.spgemm_learned(smash.to_device(A), smash.to_device(B), model, margin=margin)
+        Ch = C.to_host()
+        owner.free()
+        assert_matches_oracle(Ch, A, B)
