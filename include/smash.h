@@ -167,6 +167,27 @@ int spgemm_symbolic(smash_handle *h, const smash_csr *A, const smash_csr *B, int
 int spgemm_numeric(smash_handle *h, const smash_csr *A, const smash_csr *B, smash_dtype dtype,
                    smash_csr *C, void *stream);
 
+/*
+ * Symbolic phase that allocates nothing. The paper has no counterpart; this
+ * is for callers that cannot allocate device memory at all (a frozen or
+ * foreign-owned memory pool, an exhausted device-memory budget, a host that
+ * may only pass in its own buffers) and so cannot even create a handle.
+ * Same result as spgemm_symbolic: c_row_ptr (device int64[A.rows+1],
+ * caller-allocated) receives C's row pointer and *c_nnz (host) nnz(C).
+ * All scratch memory comes from one fixed array inside the library
+ * (32 MiB + 256 B of device memory, held on every device that loads the
+ * library until the process exits); the call performs no cudaMalloc, no
+ * cudaFree and no allocation by any library. Limit: cols(B) <= 65536 (every
+ * row's hash table must fit one 131072-slot slice); larger inputs return
+ * SMASH_ERR_UNSUPPORTED. Uses the current CUDA device; the first call on a
+ * device looks up the array's device address (make that first call before any
+ * stream capture). Every call shares the array and leaves its contents
+ * behind; calls that overlap on the GPU (other streams, other host threads)
+ * race and must not be issued. Synchronises `stream`.
+ */
+int spgemm_symbolic_noalloc(const smash_csr *A, const smash_csr *B, int64_t *c_row_ptr, int64_t *c_nnz,
+                            void *stream);
+
 /* Synchronise `stream` and return the status recorded by the kernels of the
  * handle's previous calls (then clear it). */
 int smash_check(smash_handle *h, void *stream);

@@ -27,7 +27,7 @@ EXPORTS = [
     "smash_status_string", "smash_set_timing", "smash_get_timings",
     "smash_train_cfg_default", "smash_model_create", "smash_model_destroy", "smash_model_get", "smash_model_set",
     "smash_model_save", "smash_model_load", "smash_row_features", "smash_mlp_train", "smash_mlp_gradient",
-    "smash_mlp_predict", "spgemm_learned", "smash_free_csr",
+    "smash_mlp_predict", "spgemm_learned", "smash_free_csr", "spgemm_symbolic_noalloc",
 ]
 MLP_PARAMS = 4673
 
@@ -145,6 +145,8 @@ def load_library(path: str = LIB_PATH):
         lib.spgemm_learned.argtypes = [P, ctypes.POINTER(CsrStruct), ctypes.POINTER(CsrStruct), ctypes.c_int, P,
                                        ctypes.c_float, ctypes.POINTER(CsrStruct), ctypes.POINTER(LearnedStats), P]
         lib.smash_free_csr.argtypes = [P, ctypes.POINTER(CsrStruct)]
+        lib.spgemm_symbolic_noalloc.argtypes = [ctypes.POINTER(CsrStruct), ctypes.POINTER(CsrStruct), P,
+                                                ctypes.POINTER(ctypes.c_int64), P]
         for name in EXPORTS:
             f = getattr(lib, name)
             if f.restype is None or f.restype is ctypes.c_int:
