@@ -284,8 +284,46 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
                    const smash_model *m, float margin, smash_csr *C, smash_learned_stats *stats, void *stream);
 
 /* Release C's three arrays through the handle's allocator (for C filled by
- * spgemm_learned or spgemm_batched). */
+ * spgemm_learned, or C[0] of spgemm_batched). */
 int smash_free_csr(smash_handle *h, smash_csr *C);
+
+/* ---------------------------------------------------------------------------
+ * Batched products (not in the paper as such: Version 2's token scheduling
+ * applied across many independent products). count pairs (A[m], B[m]) give
+ * C[m] = A[m] * B[m]. One cooperative, persistent kernel claims work items
+ * (single large rows, then tiles of 8 rows of one product) from a global
+ * counter and runs the symbolic counts, the row-pointer scans, the products'
+ * offsets and the numeric values, separated by grid barriers whose waits are
+ * bounded (a timeout returns SMASH_ERR_TIMEOUT). Rows too large for one
+ * block's table (flagged "huge") are computed around the launch by the
+ * regular per-product path. The launch is recorded in a CUDA graph and
+ * replayed.
+ * Output: C[m].rows/cols/nnz are set; the arrays of all C[m] are views into
+ * three pools allocated through the handle's allocator and owned by the
+ * caller: release them with smash_free_csr(h, &C[0]) only (C[0]'s arrays are
+ * the pools' starts). Synchronises the stream.
+ */
+typedef struct {
+    int64_t products;
+    int64_t rows;       /* rows of all products */
+    int64_t big_rows;   /* rows done by a whole block */
+    int64_t huge_rows;  /* rows done by the regular path */
+    int64_t flop;       /* products a_ik * b_kj */
+    int64_t c_nnz;      /* sum of nnz(C[m]) */
+} smash_batched_stats;
+
+int spgemm_batched(smash_handle *h, int count, const smash_csr *A, const smash_csr *B, smash_dtype dtype,
+                   smash_csr *C, smash_batched_stats *stats, void *stream);
+
+/* Per-warp hash-table size of the batched kernel, 2^bits slots, bits in [6, 12] (default 10). */
+int smash_batched_set_table_bits(smash_handle *h, int bits);
+int smash_batched_get_table_bits(smash_handle *h, int *bits);
+
+/* Autotuner: times spgemm_batched on the given batch for each table size that
+ * fits (2^8 .. 2^11 slots), keeps the fastest in the handle and reports it
+ * (*best_ms: mean of two timed runs after one warm-up). */
+int smash_batched_autotune(smash_handle *h, int count, const smash_csr *A, const smash_csr *B, smash_dtype dtype,
+                           int *best_bits, float *best_ms, void *stream);
 
 /* Kernel timing (a tracing aid; not needed for results). With enable != 0,
  * every kernel launch of the following calls is bracketed by CUDA events on

@@ -90,6 +90,7 @@ int smash_destroy(smash_handle *h) {
         release(h, h->split);
         release(h, h->stage);
         release(h, h->learn);
+        batched_release(h);
         release(h, h->err);
         if (h->host) cudaFreeHost(h->host);
     }
@@ -119,6 +120,7 @@ int smash_set_allocator(smash_handle *h, smash_alloc_fn alloc, smash_free_fn fre
     release(h, h->split);
     release(h, h->stage);
     release(h, h->learn);
+    batched_release(h);
     // the error words move to the new allocator as well
     release(h, h->err);
     h->alloc = alloc ? alloc : default_alloc;

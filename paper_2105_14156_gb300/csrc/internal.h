@@ -426,3 +426,10 @@ int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const
 
 }  // namespace host
 }  // namespace smash
+
+namespace smash {
+namespace host {
+// Releases the batched path's per-handle state (batched.cu).
+void batched_release(smash_handle *h);
+}  // namespace host
+}  // namespace smash

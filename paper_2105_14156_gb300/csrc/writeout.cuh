@@ -1,0 +1,173 @@
+// Row write-out of the numeric phase (Write-back Phase): gather a row's
+// occupied table slots, order them by column and stream them to C.
+// Shared by the per-product kernels (k_numeric.cu) and the batched kernel.
+#pragma once
+
+#include <climits>
+
+#include "device_common.cuh"
+
+namespace smash {
+
+// Output of a numeric launch. Exact mode (row_nnz == nullptr): c_rp is C's
+// row pointer and every row must have exactly c_rp[i+1]-c_rp[i] entries.
+// Capacity mode (learned sizing): c_rp gives each row a capacity; a row that
+// fits is written at the start of its range and row_nnz[i] receives its
+// length, a row that does not fit (or whose table filled up) gets -1.
+template <typename V>
+struct NumOutT {
+    const int64_t *c_rp;
+    int32_t *c_ci;
+    V *c_val;
+    int64_t c_nnz;
+    int *row_nnz;
+};
+
+template <typename V>
+__device__ __forceinline__ bool out_range(const NumOutT<V> &o, int64_t i, int64_t &c0, int &n, int *err) {
+    const int64_t s = o.c_rp[i], t = o.c_rp[i + 1];
+    if (s < 0 || t < s || t > o.c_nnz || t - s > INT_MAX) {
+        raise_err(err, kErrBadRowPtr);
+        c0 = 0;
+        n = 0;
+        return false;
+    }
+    c0 = s;
+    n = (int)(t - s);
+    return true;
+}
+
+// ----- write-out: warp rank (GS = 32, at most 32 entries) --------------------
+template <typename V>
+__device__ __forceinline__ void writeout_warp_rank(int *keys, V *vals, int T, int tot, int n_exp,
+                                                   const NumOutT<V> &out, int64_t c0) {
+    const int lane = lane_id();
+    int filled = 0;
+    for (int s0 = 0; s0 < T; s0 += 32) {
+        const int k = keys[s0 + lane];
+        const V v = vals[s0 + lane];
+        const bool occ = k != kEmpty;
+        const unsigned b = __ballot_sync(kFull, occ);
+        __syncwarp();
+        if (occ) {
+            const int pos = filled + __popc(b & lanemask_lt());
+            keys[pos] = k;
+            vals[pos] = v;
+        }
+        filled += __popc(b);
+        __syncwarp();
+    }
+    const int k = lane < tot ? keys[lane] : INT_MAX;
+    const V v = lane < tot ? vals[lane] : V(0);
+    int rank = 0;
+    for (int m = 0; m < tot; ++m) rank += (__shfl_sync(kFull, k, m) < k) ? 1 : 0;
+    if (lane < tot && rank < n_exp) {
+        out.c_ci[c0 + rank] = k;
+        out.c_val[c0 + rank] = v;
+    }
+    __syncwarp();
+}
+
+// ----- write-out: compaction + bitonic sort in shared memory ------------------
+template <typename V, int GS, int NT>
+__device__ __forceinline__ void writeout_bitonic(int *keys, V *vals, int T, int n_exp, const NumOutT<V> &out,
+                                                 int64_t c0, int *red) {
+    using G = Group<GS, NT>;
+    const int t = G::tid();
+    int n = 0;
+    for (int s0 = 0; s0 < T; s0 += GS) {
+        const int s = s0 + t;
+        const int k = keys[s];
+        const V v = vals[s];
+        const int occ = k != kEmpty ? 1 : 0;
+        int ct;
+        const int pos = n + G::template excl_scan<int>(occ, red, &ct);
+        if (occ) {
+            keys[pos] = k;
+            vals[pos] = v;
+        }
+        n += ct;
+    }
+    int P = 1;
+    while (P < n) P <<= 1;
+    G::sync();
+    for (int s = n + t; s < P; s += GS) keys[s] = INT_MAX;
+    G::sync();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int idx = t; idx < (P >> 1); idx += GS) {
+                const int lo = 2 * idx - (idx & (j - 1));
+                const int hi = lo + j;
+                const int a = keys[lo], b = keys[hi];
+                const bool asc = (lo & k) == 0;
+                if ((a > b) == asc) {
+                    keys[lo] = b;
+                    keys[hi] = a;
+                    const V x = vals[lo];
+                    vals[lo] = vals[hi];
+                    vals[hi] = x;
+                }
+            }
+            G::sync();
+        }
+    }
+    const int nw = n < n_exp ? n : n_exp;
+    for (int s = t; s < nw; s += GS) {
+        out.c_ci[c0 + s] = keys[s];
+        out.c_val[c0 + s] = vals[s];
+    }
+}
+
+// Exclusive prefix of popcounts over words [0, nwords) of bm (contiguous
+// chunk per thread); returns the total.
+template <int GS, int NT>
+__device__ __forceinline__ int bitmap_prefix(const unsigned *bm, int *pre, int nwords, int *red) {
+    using G = Group<GS, NT>;
+    const int t = G::tid();
+    const int wpt = (nwords + GS - 1) / GS;
+    const int w0 = t * wpt;
+    const int w1 = min(w0 + wpt, nwords);
+    int loc = 0;
+    for (int w = w0; w < w1; ++w) loc += __popc(bm[w]);
+    int tot;
+    int run = G::template excl_scan<int>(loc, red, &tot);
+    for (int w = w0; w < w1; ++w) {
+        pre[w] = run;
+        run += __popc(bm[w]);
+    }
+    return tot;
+}
+
+// ----- write-out: bitmap rank over the columns of B ---------------------------
+template <typename V, int GS, int NT>
+__device__ __forceinline__ void writeout_bitmap(const int *keys, const V *vals, int T, unsigned *bm, int *pre,
+                                                int words, int n_exp, const NumOutT<V> &out, int64_t c0,
+                                                int *red) {
+    using G = Group<GS, NT>;
+    const int t = G::tid();
+    for (int s = t; s < T; s += GS) {
+        const int k = keys[s];
+        if (k != kEmpty) atomicOr(bm + (k >> 5), 1u << (k & 31));
+    }
+    G::sync();
+    bitmap_prefix<GS, NT>(bm, pre, words, red);
+    G::sync();
+    for (int s = t; s < T; s += GS) {
+        const int k = keys[s];
+        if (k != kEmpty) {
+            const int w = k >> 5;
+            const int pos = pre[w] + __popc(bm[w] & ((1u << (k & 31)) - 1u));
+            if (pos < n_exp) {
+                out.c_ci[c0 + pos] = k;
+                out.c_val[c0 + pos] = vals[s];
+            }
+        }
+    }
+}
+
+template <typename V, int GS>
+__host__ __device__ constexpr size_t num_scratch_bytes() {
+    return (prod_scratch_bytes<V, GS>() + 15) & ~size_t(15);
+}
+
+}  // namespace smash

@@ -28,7 +28,16 @@ EXPORTS = [
     "smash_train_cfg_default", "smash_model_create", "smash_model_destroy", "smash_model_get", "smash_model_set",
     "smash_model_save", "smash_model_load", "smash_row_features", "smash_mlp_train", "smash_mlp_gradient",
     "smash_mlp_predict", "spgemm_learned", "smash_free_csr", "spgemm_symbolic_noalloc",
+    "spgemm_batched", "smash_batched_set_table_bits", "smash_batched_get_table_bits", "smash_batched_autotune",
 ]
+
+
+class BatchedStats(ctypes.Structure):
+    _fields_ = [("products", ctypes.c_int64), ("rows", ctypes.c_int64), ("big_rows", ctypes.c_int64),
+                ("huge_rows", ctypes.c_int64), ("flop", ctypes.c_int64), ("c_nnz", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 MLP_PARAMS = 4673
 
 
@@ -147,6 +156,13 @@ def load_library(path: str = LIB_PATH):
         lib.smash_free_csr.argtypes = [P, ctypes.POINTER(CsrStruct)]
         lib.spgemm_symbolic_noalloc.argtypes = [ctypes.POINTER(CsrStruct), ctypes.POINTER(CsrStruct), P,
                                                 ctypes.POINTER(ctypes.c_int64), P]
+        lib.spgemm_batched.argtypes = [P, ctypes.c_int, ctypes.POINTER(CsrStruct), ctypes.POINTER(CsrStruct),
+                                       ctypes.c_int, ctypes.POINTER(CsrStruct), ctypes.POINTER(BatchedStats), P]
+        lib.smash_batched_set_table_bits.argtypes = [P, ctypes.c_int]
+        lib.smash_batched_get_table_bits.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
+        lib.smash_batched_autotune.argtypes = [P, ctypes.c_int, ctypes.POINTER(CsrStruct),
+                                               ctypes.POINTER(CsrStruct), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_float), P]
         for name in EXPORTS:
             f = getattr(lib, name)
             if f.restype is None or f.restype is ctypes.c_int:
@@ -368,6 +384,59 @@ class Handle:
         C = DeviceCsr(int(sc.rows), int(sc.cols), _view(sc.row_ptr, int(sc.rows) + 1, torch.int64),
                       _view(sc.col_idx, int(sc.nnz), torch.int32), _view(sc.val, int(sc.nnz), vdt))
         return C, st.as_dict(), owner
+
+
+def _pair_structs(pairs):
+    n = len(pairs)
+    SA = (CsrStruct * max(n, 1))()
+    SB = (CsrStruct * max(n, 1))()
+    for m, (A, B) in enumerate(pairs):
+        SA[m] = A.struct()
+        SB[m] = B.struct()
+    return SA, SB
+
+
+def _batched(self, pairs, stream=None):
+    """C_m = A_m * B_m for all pairs in one persistent launch. Returns
+    (list of C as zero-copy views, stats, owner); owner.free() releases them."""
+    import torch
+    n = len(pairs)
+    if n == 0:
+        return [], BatchedStats().as_dict(), None
+    dt = _dtype_code(pairs[0][0].val)
+    SA, SB = _pair_structs(pairs)
+    SC = (CsrStruct * n)()
+    st = BatchedStats()
+    _check(self.lib.spgemm_batched(self.h, n, SA, SB, dt, SC, ctypes.byref(st), _stream_ptr(stream)),
+           "spgemm_batched")
+    vdt = pairs[0][0].val.dtype
+    Cs = [DeviceCsr(int(c.rows), int(c.cols), _view(c.row_ptr, int(c.rows) + 1, torch.int64),
+                    _view(c.col_idx, int(c.nnz), torch.int32), _view(c.val, int(c.nnz), vdt)) for c in SC]
+    return Cs, st.as_dict(), LibraryCsr(self, SC[0])
+
+
+def _batched_autotune(self, pairs, stream=None):
+    n = len(pairs)
+    dt = _dtype_code(pairs[0][0].val)
+    SA, SB = _pair_structs(pairs)
+    bits = ctypes.c_int(0)
+    ms = ctypes.c_float(0)
+    _check(self.lib.smash_batched_autotune(self.h, n, SA, SB, dt, ctypes.byref(bits), ctypes.byref(ms),
+                                           _stream_ptr(stream)), "smash_batched_autotune")
+    return int(bits.value), float(ms.value)
+
+
+def _batched_table_bits(self, bits=None):
+    if bits is not None:
+        _check(self.lib.smash_batched_set_table_bits(self.h, int(bits)), "smash_batched_set_table_bits")
+    b = ctypes.c_int(0)
+    _check(self.lib.smash_batched_get_table_bits(self.h, ctypes.byref(b)), "smash_batched_get_table_bits")
+    return int(b.value)
+
+
+Handle.spgemm_batched = _batched
+Handle.batched_autotune = _batched_autotune
+Handle.batched_table_bits = _batched_table_bits
 
 
 class LibraryCsr:
