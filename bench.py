@@ -1,21 +1,29 @@
-"""Benchmark: C = A*A on R-MAT through the SMASH C ABI on GB300.
+"""Benchmark of the SMASH row-wise hash SpGEMM on GB300, through the C ABI.
 
-One step = the whole plain two-pass path on one input: per-row product
-counts and binning, the symbolic hash pass, the row-pointer scan, allocation
-of C, the numeric hash pass with write-back (shared-memory tables, dense
-rows, global-memory spill, per-row sort). Inputs are resident in HBM when the
-timed region starts; L2 (129 MB) is flushed between timed steps by writing a
-256 MiB buffer outside the timed region.
+Main line (value): one step = the whole plain two-pass path on R-MAT scale 16
+(edge factor 16, Graph500 a,b,c,d, float64 U[-1,1]), C = A*A with A and B
+separate copies resident in HBM: per-row product counts and binning, the
+symbolic hash pass, the row-pointer scan, allocation of C, the numeric pass
+(shared-memory tables, dense rows in thread-block clusters, global-memory
+spill, per-row sorted write-out). L2 (129 MB) is flushed between timed steps
+by writing a 256 MiB buffer outside the timed region. value = useful GFLOP/s
+= 2 * products / step time (CUDA events on the launching stream).
 
-Prints one JSON line (rank 0). Usage:
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl smash|reference]
-Multi-GPU (torchrun): every rank runs an independent replica of the workload
-(the rows of C are independent; there is no exchange step), value = products
-of all ranks / max time over ranks, "scaling": "weak".
+Variants (same JSON line, "variants"): learned sizing on R-MAT scale 18
+(float32) against the plain path; 512 batched products in one persistent
+launch against 512 separate plain calls; R-MAT scale 20 (float32) with learned
+sizing and autotuned planner parameters, with its HBM roofline fraction.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl smash|reference]
+                       [--variants all|none]
+With torchrun (N > 1) every rank runs an independent replica (the rows of C
+are independent; no exchange step): value = all ranks' products / max time.
 """
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import os
 import statistics
@@ -37,6 +45,7 @@ WORKLOADS = {
     "rmat18_f32": "R-MAT scale 18, edge factor 16, (0.57,0.19,0.19,0.05), float32 U[-1,1], C = A*A",
     "rmat20_f32": "R-MAT scale 20, edge factor 8, (0.45,0.15,0.15,0.25), float32 U[-1,1], C = A*A",
 }
+TRAIN_SEEDS = list(range(200))
 
 
 def row_products(A, B) -> np.ndarray:
@@ -45,15 +54,37 @@ def row_products(A, B) -> np.ndarray:
     per = blen[A.col_idx].astype(np.int64)
     out = np.zeros(A.rows, dtype=np.int64)
     nz = np.diff(A.row_ptr) > 0
-    out[nz] = np.add.reduceat(per, A.row_ptr[:-1][nz]) if per.size else 0
+    if per.size:
+        out[nz] = np.add.reduceat(per, A.row_ptr[:-1][nz])
     return out
 
 
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
-    except Exception:
+    except (OSError, ValueError):
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2105_14156_gb300", "csrc", "*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    cur = source_hash()
+    for line in open(path):
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if f.get("kernel") == kernel and f.get("workload") == workload and f.get("src") == cur:
+            return float(f["dram_bytes_per_launch"])
+    return None
 
 
 class ClockSampler:
@@ -71,7 +102,7 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
-        except Exception:
+        except OSError:
             self.proc = None
 
     def _read(self):
@@ -83,7 +114,7 @@ class ClockSampler:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
-            except Exception:
+            except subprocess.TimeoutExpired:
                 self.proc.kill()
 
     def summary(self, t0, t1):
@@ -100,21 +131,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(win)}
 
 
-def dist_setup(n_gpus):
+def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    pg = None
+    dist = None
     if world > 1:
         import torch.distributed as dist
-        backend = "nccl" if os.environ.get("SMASH_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
-        dist.init_process_group(backend)
-        pg = dist
-    return rank, world, local, pg
+        dist.init_process_group(os.environ.get("SMASH_BENCH_BACKEND", "nccl"))
+    return rank, world, local, dist
 
 
 def cpu_baseline(A, B, flop, budget_products: float, seed: int = 0):
-    """The oracle on a seeded random sample of rows (about budget_products products)."""
+    """The oracle, as it stands, on a seeded random sample of rows."""
     import oracle
     oracle.build()
     rng = np.random.default_rng(seed)
@@ -131,7 +160,7 @@ def cpu_baseline(A, B, flop, budget_products: float, seed: int = 0):
                       % (rows.size, A.rows, seed, prods, int(flop.sum()), dt)}
 
 
-def run_reference(args, A, B, flop, rank, world):
+def run_reference(args, A, B, flop, rank):
     """Reference arm: the CPU oracle as it stands, on bounded samples of the workload."""
     if rank != 0:
         return 0
@@ -142,16 +171,44 @@ def run_reference(args, A, B, flop, rank, world):
         if k >= args.warmup:
             vals.append(cb["value"])
     value = statistics.median(vals)
-    t_step = 2.0 * per_step / (value * 1e9)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 2.0 * per_step / (value * 1e9) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if A.val.dtype == np.float64 else "f32", "data": "synthetic",
             "config": {"workload": args.workload, "description": WORKLOADS[args.workload]},
             "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                              "sample": "each step: rows drawn at random until about %.0e products" % per_step},
             "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def timed(fn, steps, flush, stream):
+    """Per-step CUDA-event times (ms), L2 flushed before every step."""
+    import torch
+    out = []
+    for _ in range(steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+        del r
+    return out
+
+
+def kernel_bytes(t, vb, nnz_b, total_products):
+    """Algorithmic bytes of one timed launch group (measurement)."""
+    rows, a_nnz, prods, c_nnz = t["rows"], t["a_nnz"], t["products"], t["c_nnz"]
+    share = prods / total_products if total_products else 0.0
+    if t["name"].startswith("num_"):
+        return 16 * rows + (4 + vb) * (a_nnz + c_nnz) + (4 + vb) * nnz_b * share
+    if t["name"].startswith("sym_"):
+        return 12 * rows + 4 * a_nnz + 4 * nnz_b * share
+    return None
 
 
 def main():
@@ -163,24 +220,35 @@ def main():
     ap.add_argument("--workload", default="rmat16_f64", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-products", type=float, default=2e8)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--variants", default="all", choices=["all", "none"])
+    ap.add_argument("--variant-steps", type=int, default=3)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     args.e2e_steps = max(args.e2e_steps, 1)
 
     from paper_2105_14156_gb300 import metrics
-    from paper_2105_14156_gb300.rmat import workload
+    from paper_2105_14156_gb300.rmat import batched_workload, workload
 
-    rank, world, local, dist = dist_setup(args.gpus)
+    rank, world, local, dist = dist_setup()
     A = workload(args.workload)
     B = A
     flop = row_products(A, B)
     products = int(flop.sum())
 
     if args.impl == "reference":
-        rc = run_reference(args, A, B, flop, rank, world)
+        rc = run_reference(args, A, B, flop, rank)
         if dist:
             dist.barrier()
         return rc
+
+    do_var = args.variants == "all" and world == 1
+    train_mats = None
+    if do_var:
+        # CPU work first: the spawn pool starts before the first CUDA call
+        from paper_2105_14156_gb300 import learned
+        t0 = time.perf_counter()
+        train_mats = learned.training_matrices(TRAIN_SEEDS, workers=min(16, os.cpu_count() or 1))
+        gen_train_s = time.perf_counter() - t0
 
     import torch
     from paper_2105_14156_gb300 import build, smash
@@ -189,6 +257,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     h = smash.Handle(local)
+    h.use_torch_allocator()
     dA = smash.to_device(A, dev)
     dB = smash.to_device(B, dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -200,8 +269,8 @@ def main():
     for _ in range(args.warmup):
         C = step()
     h.check(stream)
-    torch.cuda.synchronize()
     c_nnz = C.nnz
+    del C
     vb = A.val.dtype.itemsize
 
     sampler = ClockSampler(local)
@@ -209,21 +278,15 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    h.set_timing(True)
     t_wall0 = time.time()
-    times = []
-    for _ in range(args.steps):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        C = step()
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
+    times = timed(step, args.steps, flush, stream)
     torch.cuda.synchronize()
+    t_wall1 = time.time()
+    kt = h.timings()
+    h.set_timing(False)
     if dist:
         dist.barrier()
-    t_wall1 = time.time()
     time.sleep(0.25)
     sampler.stop()
     clocks = sampler.summary(t_wall0, t_wall1)
@@ -231,19 +294,31 @@ def main():
 
     ms = sum(times) / len(times)
     if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev if dist.get_backend() == "nccl" else "cpu")
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+
+    # dominant kernel: roofline from the live per-launch event timing
+    peaks, peak_src = load_peaks()
+    launches = int(sum(t["kernels"] for t in kt))
+    dom = max((t for t in kt if kernel_bytes(t, vb, B.nnz, products) is not None), key=lambda t: t["ms"])
+    per_launch_ms = dom["ms"] / dom["launches"]
+    per_launch_bytes = kernel_bytes(dom, vb, B.nnz, products) / dom["launches"]
+    achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
+    traffic = recorded_traffic(dom["name"], args.workload)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "kernel": "%s (bin %d)" % (dom["name"], dom["bin"]),
+                "share_of_step": dom["ms"] / args.steps / ms,
+                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src}
 
     # end to end through the public API with host buffers
     pinned = {}
     for name, M in (("A", A), ("B", B)):
         pinned[name] = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
                         for x in (M.row_ptr, M.col_idx, M.val)]
-    e2e_times = []
     h2d = sum(t.numel() * t.element_size() for lst in pinned.values() for t in lst)
-    d2h = 0
-    out_host = None
+    e2e_times, d2h, out_host = [], 0, None
     for k in range(args.e2e_steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -265,31 +340,38 @@ def main():
         del dAe, dBe, Ce
     e2e_s = statistics.median(e2e_times)
     if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev if dist.get_backend() == "nccl" else "cpu")
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
+    del out_host, pinned
 
-    peaks, peak_src = load_peaks()
     step_bytes = metrics.spgemm_bytes(A.rows, A.nnz, B.rows, B.nnz, A.rows, c_nnz, vb)
-    gflops = world * metrics.useful_gflops(products, ms / 1e3)
-    achieved_gbs = step_bytes / (ms / 1e3) / 1e9
+    achieved_step = step_bytes / (ms / 1e3) / 1e9
     line = {
-        "metric": METRIC, "value": gflops, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if vb == 8 else "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
-                   "products": products, "nnz_a": A.nnz, "nnz_c": c_nnz,
+        "metric": METRIC, "value": world * metrics.useful_gflops(products, ms / 1e3), "unit": "GFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if vb == 8 else "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "products": products,
+                   "nnz_a": A.nnz, "nnz_c": c_nnz,
                    "l2": "flushed between timed steps (256 MiB write outside the timed region)",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "hbm_gbs": achieved_gbs,
-        "step_roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                          "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": None,
-                          "note": "bytes(A)+bytes(B)+bytes(C) per step over the step time; peak %s" % peak_src},
+        "hbm_gbs": achieved_step,
+        "step_roofline": {"bound": "hbm", "achieved": achieved_step, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                          "frac": achieved_step / peaks["hbm_gbs"],
+                          "note": "bytes(A)+bytes(B)+bytes(C) per step over the step time"},
+        "roofline": roofline,
+        "kernels": [{k: t[k] for k in ("name", "bin", "launches", "rows", "products", "ms")} for t in
+                    sorted(kt, key=lambda t: -t["ms"])[:8]],
         "e2e": {"value": world * metrics.useful_gflops(products, e2e_s), "unit": "GFLOP/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clocks,
-        "gpu_launches": None,
+        "gpu_launches": launches,
     }
+
+    if do_var:
+        line["variants"] = run_variants(h, dev, flush, stream, args, train_mats, gen_train_s, peaks)
+
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(A, B, flop, args.cpu_products)
     if rank == 0:
@@ -298,6 +380,106 @@ def main():
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def run_variants(h, dev, flush, stream, args, train_mats, gen_train_s, peaks):
+    import torch
+    from paper_2105_14156_gb300 import autotune, learned, metrics, smash
+    from paper_2105_14156_gb300.rmat import batched_workload, workload
+    K = max(1, args.variant_steps)
+    out = {}
+
+    def gf(prods, ms_):
+        return metrics.useful_gflops(prods, ms_ / 1e3)
+
+    # learned sizing: R-MAT scale 18, float32
+    t0 = time.perf_counter()
+    model, loss, train_s, nsamp = learned.train(h, train_mats, epochs=8, batch=4096)
+    A18 = workload("rmat18_f32")
+    p18 = int(row_products(A18, A18).sum())
+    d18a, d18b = smash.to_device(A18, dev), smash.to_device(A18, dev)
+    plain = lambda: h.spgemm(d18a, d18b, stream)
+    plain()
+    t_plain = statistics.median(timed(plain, K, flush, stream))
+    stats = {}
+
+    def lstep():
+        C, st, owner = h.spgemm_learned(d18a, d18b, model, margin=0.15, stream=stream)
+        stats.update(st)
+        owner.free()
+
+    lstep()
+    t_learn = statistics.median(timed(lstep, K, flush, stream))
+    out["learned_rmat18_f32"] = {
+        "products": p18, "c_nnz": stats.get("c_nnz"),
+        "plain_ms": t_plain, "learned_ms": t_learn,
+        "plain_gflops": gf(p18, t_plain), "learned_gflops": gf(p18, t_learn),
+        "speedup_vs_plain": t_plain / t_learn,
+        "overflow_rows": stats.get("overflow_rows"), "rows": stats.get("rows"),
+        "staged_over_cnnz": (stats["staged_nnz"] / stats["c_nnz"]) if stats.get("c_nnz") else None,
+        "training": {"matrices": len(train_mats), "samples": nsamp, "final_mse": loss, "device_train_s": train_s,
+                     "cpu_generation_s": gen_train_s, "epochs": 8, "batch": 4096},
+    }
+    del d18a, d18b, A18
+    torch.cuda.empty_cache()
+
+    # batched: 512 products in one persistent launch vs 512 separate plain calls
+    pairs = batched_workload(512, seed=7)
+    dev_pairs = [(smash.to_device(a, dev), smash.to_device(b, dev)) for a, b in pairs]
+    pb = int(sum(row_products(a, b).sum() for a, b in pairs))
+    bits, _ = h.batched_autotune(dev_pairs, stream)
+    bstats = {}
+
+    def bstep():
+        Cs, st, owner = h.spgemm_batched(dev_pairs, stream)
+        bstats.update(st)
+        owner.free()
+
+    bstep()
+    t_batch = statistics.median(timed(bstep, K, flush, stream))
+
+    def sstep():
+        for a, b in dev_pairs:
+            h.spgemm(a, b, stream)
+
+    sstep()
+    t_sep = statistics.median(timed(sstep, max(1, K - 1), flush, stream))
+    out["batched_512"] = {"products_flop": pb, "c_nnz": bstats.get("c_nnz"), "batched_ms": t_batch,
+                          "separate_ms": t_sep, "batched_gflops": gf(pb, t_batch),
+                          "separate_gflops": gf(pb, t_sep), "speedup_vs_separate": t_sep / t_batch,
+                          "table_bits": bits, "big_rows": bstats.get("big_rows"),
+                          "huge_rows": bstats.get("huge_rows")}
+    del dev_pairs, pairs
+
+    # R-MAT scale 20, float32: learned sizing + autotuned planner
+    A20 = workload("rmat20_f32")
+    p20 = int(row_products(A20, A20).sum())
+    d20a, d20b = smash.to_device(A20, dev), smash.to_device(A20, dev)
+    saved = h.params.as_dict()
+    tuned, _ = autotune.tune(h, d20a, d20b, "rmat20_f32", cache_path=None)
+    plain20 = lambda: h.spgemm(d20a, d20b, stream)
+    plain20()
+    t_p20 = statistics.median(timed(plain20, K, flush, stream))
+    st20 = {}
+
+    def l20():
+        C, st, owner = h.spgemm_learned(d20a, d20b, model, margin=0.15, stream=stream)
+        st20.update(st)
+        owner.free()
+
+    l20()
+    t_l20 = statistics.median(timed(l20, K, flush, stream))
+    bytes20 = metrics.spgemm_bytes(A20.rows, A20.nnz, A20.rows, A20.nnz, A20.rows, st20["c_nnz"], 4)
+    best = min(t_p20, t_l20)
+    out["rmat20_f32"] = {"products": p20, "c_nnz": st20["c_nnz"], "plain_autotuned_ms": t_p20, "learned_ms": t_l20,
+                         "plain_gflops": gf(p20, t_p20), "learned_gflops": gf(p20, t_l20),
+                         "hbm_roofline_frac": bytes20 / (best / 1e3) / 1e9 / peaks["hbm_gbs"],
+                         "bytes_a_b_c": bytes20, "autotuned_params": tuned,
+                         "overflow_rows": st20.get("overflow_rows")}
+    h.set_params(**saved)
+    del d20a, d20b
+    model.close()
+    return out
 
 
 if __name__ == "__main__":

@@ -111,6 +111,7 @@ typedef struct {
     int64_t products; /* products of those rows, summed */
     int64_t c_nnz;    /* nnz(C_i) (or symbolic bound) of those rows, summed */
     double ms;        /* summed CUDA-event time between launch and completion on the call's stream */
+    int64_t kernels;  /* CUDA kernels launched by these launches, summed */
 } smash_kernel_time;
 
 typedef struct smash_handle smash_handle;

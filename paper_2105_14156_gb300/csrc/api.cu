@@ -184,7 +184,7 @@ int spgemm_symbolic(smash_handle *h, const smash_csr *A, const smash_csr *B, int
     const RawOperands op = raw_ops(A, B);
     if ((st = run_symbolic(h, op, n, pl, pl.nnz, s, nullptr, 0))) return st;
     {
-        LaunchTimer lt(h, s, "scan_rowptr", -1, 512, n, 0, 0, 0);
+        LaunchTimer lt(h, s, "scan_rowptr", -1, 512, n, 0, 0, 0, 3);
         launch_scan_rowptr(pl.nnz, n, c_row_ptr, pl.total, pl.scan, s);
     }
     if ((st = last_cuda_status())) return st;
@@ -313,7 +313,8 @@ int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const
                 const int cpc = cs == 1 ? (int)((op.ncols + 31) & ~31) : cap;
                 const size_t need = dense_plan_bytes(op, cs, cpc, H, vsz);
                 if ((st = ensure(h, h->split, need, s))) return st;
-                LaunchTimer lt(h, s, "dense_plan", -1, 256, op.b_rows, op.a_nnz, 0, op.b_nnz);
+                LaunchTimer lt(h, s, "dense_plan", -1, 256, op.b_rows, op.a_nnz, 0, op.b_nnz,
+                               4 + (H > 0 ? 1 : 0) + (cs > 1 ? 2 : 0));
                 launch_dense_plan(dt, op, cs, cap, cpc, H, h->params.hot_factor, h->split.ptr, sl, h->sms, s);
                 sl.nslices = cs;
                 sl.cpc = cpc;

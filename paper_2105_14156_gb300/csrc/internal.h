@@ -136,7 +136,7 @@ struct LaunchTimer {
     int slot = -1;
     cudaEvent_t e0 = nullptr;
     LaunchTimer(smash_handle *hh, cudaStream_t ss, const char *name, int bin, int threads, long long rows,
-                long long a_nnz, long long products, long long c_nnz)
+                long long a_nnz, long long products, long long c_nnz, int kernels = 1)
         : h(hh), s(ss) {
         if (!h->timing) return;
         for (size_t k = 0; k < h->totals.size(); ++k)
@@ -157,6 +157,7 @@ struct LaunchTimer {
         kt.a_nnz += a_nnz;
         kt.products += products;
         kt.c_nnz += c_nnz;
+        kt.kernels += kernels;
         e0 = take_event(h);
         cudaEventRecord(e0, s);
     }

@@ -385,7 +385,7 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
         launch_mlp_infer(feats, bound, nullptr, n, m->wb, m->norm, margin, nullptr, cap, h->sms, s);
     }
     {
-        LaunchTimer lt(h, s, "scan_rowptr", -1, 512, n, 0, 0, 0);
+        LaunchTimer lt(h, s, "scan_rowptr", -1, 512, n, 0, 0, 0, 3);
         launch_scan_rowptr(cap, n, stage_rp, ctr, scan, s);
     }
     if ((st = last_cuda_status())) return st;
@@ -428,7 +428,7 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
     }
     // 6. exact row pointer of C, then its arrays
     {
-        LaunchTimer lt(h, s, "scan_rowptr", -1, 512, n, 0, 0, 0);
+        LaunchTimer lt(h, s, "scan_rowptr", -1, 512, n, 0, 0, 0, 3);
         launch_scan_rowptr(row_nnz, n, C->row_ptr, ctr + 2, scan, s);
     }
     if (cudaMemcpyAsync(h->host, ctr + 2, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -103,7 +103,8 @@ class Stats(ctypes.Structure):
 class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("bin", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("launches", ctypes.c_int64), ("rows", ctypes.c_int64), ("a_nnz", ctypes.c_int64),
-                ("products", ctypes.c_int64), ("c_nnz", ctypes.c_int64), ("ms", ctypes.c_double)]
+                ("products", ctypes.c_int64), ("c_nnz", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("kernels", ctypes.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -283,6 +284,30 @@ class Handle:
         s = Stats()
         _check(self.lib.smash_get_stats(self.h, ctypes.byref(s)), "smash_get_stats")
         return s
+
+    def use_torch_allocator(self):
+        """Route the handle's device allocations (scratch, and the C arrays of the
+        learned and batched calls) through torch's caching allocator."""
+        import torch
+        ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+        FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+        dev = self.device
+
+        def _alloc(nbytes, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, torch.cuda.current_stream(dev))
+            except Exception:
+                return None
+
+        def _free(ptr, ctx):
+            if ptr:
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc_cb = ALLOC(_alloc)   # keep the callbacks alive
+        self._free_cb = FREE(_free)
+        _check(self.lib.smash_set_allocator(self.h, ctypes.cast(self._alloc_cb, ctypes.c_void_p),
+                                            ctypes.cast(self._free_cb, ctypes.c_void_p), None),
+               "smash_set_allocator")
 
     def set_timing(self, enable: bool):
         _check(self.lib.smash_set_timing(self.h, 1 if enable else 0), "smash_set_timing")
