@@ -58,15 +58,16 @@ __global__ void __launch_bounds__(256) k_features(RawOperands op, const int *row
         f = warp_sum(f);
         mx = warp_max(mx);
         if (lane == 0) {
-            const double na = (double)(ae - ab);
+            // float arithmetic: the features only need a few significant digits
+            const float na = (float)(ae - ab);
             const long long ub = f < (long long)op.ncols ? f : (long long)op.ncols;
             float *x = feats + (size_t)i * kFeat;
-            x[0] = (float)log1p(na);
-            x[1] = (float)log1p((double)f);
-            x[2] = (float)log1p((double)mx);
-            x[3] = (float)log1p(na > 0 ? (double)f / na : 0.0);
-            x[4] = (float)log1p((double)ub);
-            x[5] = op.ncols > 0 ? (float)((double)ub / (double)op.ncols) : 0.f;
+            x[0] = log1pf(na);
+            x[1] = log1pf((float)f);
+            x[2] = log1pf((float)mx);
+            x[3] = log1pf(na > 0.f ? (float)f / na : 0.f);
+            x[4] = log1pf((float)ub);
+            x[5] = op.ncols > 0 ? (float)ub / (float)op.ncols : 0.f;
             if (bound) bound[i] = ub;
         }
     }
@@ -108,10 +109,10 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const float *feats, const lon
             const long long ub = bound[i];
             long long cap = 0;
             if (ub > 0) {
-                const double pred = expm1((double)fminf(y, 40.f));
-                double c = ceil((1.0 + (double)margin) * pred);
-                if (!(c >= 1.0)) c = 1.0;
-                cap = c > (double)ub ? ub : (long long)c;
+                const float pred = expm1f(fminf(y, 40.f));
+                float c = ceilf((1.f + margin) * pred);
+                if (!(c >= 1.f)) c = 1.f;
+                cap = c >= (float)ub ? ub : (long long)c;
             }
             cap_out[i] = (int)cap;
         }

@@ -274,37 +274,64 @@ void launch_overflow_list(const int *row_nnz, int64_t n, int *list, int *count, 
     k_overflow_list<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(row_nnz, n, list, count, ovf);
 }
 
-// Copy each staged row that fitted to its place in C (one warp per row).
+// Copy each staged row that fitted to its place in C. Work is split by output
+// position: a warp owns a chunk of kCompactChunk consecutive entries of C,
+// finds the first row reaching into it by binary search on C's row pointer
+// and walks the rows of the chunk, copying each overlap with all lanes
+// (coalesced reads and writes, equal work per warp whatever the row lengths).
+constexpr int64_t kCompactChunk = 2048;
+
 template <typename V>
-__global__ void __launch_bounds__(256) k_compact_rows(int64_t n, const int64_t *stage_rp, const int *len,
-                                                      const uint8_t *ovf, const int32_t *sci, const V *sval,
-                                                      const int64_t *c_rp, int32_t *cci, V *cval) {
+__global__ void __launch_bounds__(256) k_compact_rows(int64_t n, int64_t c_nnz, const int64_t *__restrict__ stage_rp,
+                                                      const uint8_t *__restrict__ ovf, const int32_t *__restrict__ sci,
+                                                      const V *__restrict__ sval, const int64_t *__restrict__ c_rp,
+                                                      int32_t *__restrict__ cci, V *__restrict__ cval) {
     const int lane = lane_id();
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
-        if (ovf[i]) continue;
-        const int64_t src = stage_rp[i], dst = c_rp[i];
-        const int m = len[i];
-        for (int k = lane; k < m; k += 32) {
-            cci[dst + k] = sci[src + k];
-            cval[dst + k] = sval[src + k];
+    const int64_t nchunks = (c_nnz + kCompactChunk - 1) / kCompactChunk;
+    for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < nchunks; ch += warps) {
+        const int64_t p0 = ch * kCompactChunk;
+        const int64_t p1 = p0 + kCompactChunk < c_nnz ? p0 + kCompactChunk : c_nnz;
+        int64_t lo = 0, hi = n;   // last row r with c_rp[r] <= p0 (c_rp[n] = c_nnz > p0)
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (__ldg(c_rp + mid) <= p0) lo = mid;
+            else hi = mid;
+        }
+        int64_t p = p0;
+        for (int64_t r = lo; p < p1 && r < n; ++r) {
+            const int64_t rb = __ldg(c_rp + r), re = __ldg(c_rp + r + 1);
+            const int64_t a = p > rb ? p : rb;
+            const int64_t b = p1 < re ? p1 : re;
+            if (b > a && !ovf[r]) {
+                const int64_t src = __ldg(stage_rp + r) + (a - rb);
+                const int64_t m = b - a;
+#pragma unroll 4
+                for (int64_t k = lane; k < m; k += 32) {
+                    cci[a + k] = __ldg(sci + src + k);
+                    cval[a + k] = __ldg(sval + src + k);
+                }
+            }
+            if (re > p) p = re;
         }
     }
 }
 
 void launch_compact_rows(int dtype, int64_t n, const int64_t *stage_rp, const int *row_nnz_final,
                          const uint8_t *ovf, const int32_t *stage_ci, const void *stage_val, const int64_t *c_rp,
-                         int32_t *c_ci, void *c_val, int sms, cudaStream_t s) {
-    if (n == 0) return;
-    const int64_t blocks = (n + 7) / 8;
-    const int64_t cap = (int64_t)sms * 16;
+                         int32_t *c_ci, void *c_val, int64_t c_nnz, int sms, cudaStream_t s) {
+    (void)row_nnz_final;
+    if (n == 0 || c_nnz <= 0) return;
+    const int64_t chunks = (c_nnz + kCompactChunk - 1) / kCompactChunk;
+    const int64_t blocks = (chunks + 7) / 8;
+    const int64_t cap = (int64_t)sms * 8;
     const int grid = (int)(blocks < cap ? blocks : cap);
     if (dtype)
-        k_compact_rows<double><<<grid, 256, 0, s>>>(n, stage_rp, row_nnz_final, ovf, stage_ci,
-                                                    (const double *)stage_val, c_rp, c_ci, (double *)c_val);
+        k_compact_rows<double><<<grid, 256, 0, s>>>(n, c_nnz, stage_rp, ovf, stage_ci, (const double *)stage_val,
+                                                    c_rp, c_ci, (double *)c_val);
     else
-        k_compact_rows<float><<<grid, 256, 0, s>>>(n, stage_rp, row_nnz_final, ovf, stage_ci,
-                                                   (const float *)stage_val, c_rp, c_ci, (float *)c_val);
+        k_compact_rows<float><<<grid, 256, 0, s>>>(n, c_nnz, stage_rp, ovf, stage_ci, (const float *)stage_val,
+                                                   c_rp, c_ci, (float *)c_val);
 }
 
 void launch_bin_scatter(int64_t n, BinBuffers bb, cudaStream_t s) {

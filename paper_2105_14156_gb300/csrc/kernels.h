@@ -54,7 +54,7 @@ void launch_num_rowinfo(const RawOperands &op, const int64_t *c_rp, int64_t c_nn
 void launch_overflow_list(const int *row_nnz, int64_t n, int *list, int *count, uint8_t *ovf, cudaStream_t s);
 void launch_compact_rows(int dtype, int64_t n, const int64_t *stage_rp, const int *row_nnz_final,
                          const uint8_t *ovf, const int32_t *stage_ci, const void *stage_val, const int64_t *c_rp,
-                         int32_t *c_ci, void *c_val, int sms, cudaStream_t s);
+                         int32_t *c_ci, void *c_val, int64_t c_nnz, int sms, cudaStream_t s);
 
 // k_mlp.cu: row-size predictor (see the file for the network).
 constexpr int kMlpParams = 4673;

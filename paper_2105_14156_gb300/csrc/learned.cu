@@ -444,7 +444,7 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
         {
             LaunchTimer lt(h, s, "compact_rows", -1, 256, n, 0, 0, cnnz);
             launch_compact_rows(dt, n, stage_rp, row_nnz, ovf, stage_ci, stage_val, C->row_ptr, C->col_idx, C->val,
-                                h->sms, s);
+                                cnnz, h->sms, s);
         }
         if (novf > 0) {
             Plan pn;
