@@ -4,7 +4,7 @@ Main line (value): one step = the whole plain two-pass path on R-MAT scale 16
 (edge factor 16, Graph500 a,b,c,d, float64 U[-1,1]), C = A*A with A and B
 separate copies resident in HBM: per-row product counts and binning, the
 symbolic hash pass, the row-pointer scan, allocation of C, the numeric pass
-(shared-memory tables, dense rows in thread-block clusters, global-memory
+(shared-memory tables, dense rows as column-window work items, global-memory
 spill, per-row sorted write-out). L2 (129 MB) is flushed between timed steps
 by writing a 256 MiB buffer outside the timed region. value = useful GFLOP/s
 = 2 * products / step time (CUDA events on the launching stream).
@@ -204,10 +204,10 @@ def kernel_bytes(t, vb, nnz_b, total_products):
     """Algorithmic bytes of one timed launch group (measurement)."""
     rows, a_nnz, prods, c_nnz = t["rows"], t["a_nnz"], t["products"], t["c_nnz"]
     share = prods / total_products if total_products else 0.0
+    if t["name"].startswith("sym_") or t["name"] == "num_dense_count":
+        return 12 * rows + 4 * a_nnz + 4 * nnz_b * share
     if t["name"].startswith("num_"):
         return 16 * rows + (4 + vb) * (a_nnz + c_nnz) + (4 + vb) * nnz_b * share
-    if t["name"].startswith("sym_"):
-        return 12 * rows + 4 * a_nnz + 4 * nnz_b * share
     return None
 
 

@@ -78,13 +78,10 @@ typedef struct {
     int32_t spill_blocks_per_sm; /* resident blocks per SM of the spill and dense kernels; default 1 */
     int32_t sym_dense_ratio; /* symbolic phase: a row whose bound b satisfies b * sym_dense_ratio >= cols(B)
                                 counts its columns in a shared-memory bitmap; 0 disables; default 64 */
-    int32_t cluster_max;     /* largest thread-block cluster (1, 2, 4 or 8) whose distributed shared memory
-                                holds a dense row's accumulator; 1 disables clusters; default 8 */
-    int32_t hot_cols;        /* dense rows: per cluster block, up to this many "hot" columns of B (column
-                                count >= hot_factor x average) accumulate in private per-warp slots;
-                                [0, 512], 0 disables; default 128 */
-    int32_t hot_factor;      /* hot-column threshold, multiple of the average column count; default 16 */
-    int32_t reserved[4];
+    int32_t dense_blocks;    /* dense rows: resident blocks per SM of the numeric dense kernel (1, 2 or 4);
+                                each owns one column window of a row (the widest that fits its share of
+                                shared memory); default 1 */
+    int32_t reserved[6];
 } smash_params;
 
 /* Per-call statistics (the last symbolic or numeric call of the handle). */

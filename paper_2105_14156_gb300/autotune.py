@@ -20,7 +20,7 @@ SPACE = [
     ("dense_ratio", [2, 4, 8, 16]),
     ("sym_dense_ratio", [16, 64, 256]),
     ("bitmap_ratio", [1, 4, 16]),
-    ("hot_cols", [0, 128]),
+    ("dense_blocks", [1, 2, 4]),
 ]
 
 

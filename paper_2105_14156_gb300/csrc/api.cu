@@ -19,9 +19,7 @@ int smash_default_params(smash_params *p) {
     p->bitmap_ratio = 4;
     p->spill_blocks_per_sm = 1;
     p->sym_dense_ratio = 64;
-    p->cluster_max = 8;
-    p->hot_cols = 128;
-    p->hot_factor = 16;
+    p->dense_blocks = 1;
     return SMASH_OK;
 }
 
@@ -86,8 +84,9 @@ int smash_destroy(smash_handle *h) {
         h->spare_events.clear();
         release(h, h->ws);
         release(h, h->tables);
-        release(h, h->dense_acc);
         release(h, h->split);
+        release(h, h->wslot);
+        release(h, h->wcnt);
         release(h, h->stage);
         release(h, h->learn);
         batched_release(h);
@@ -116,8 +115,9 @@ int smash_set_allocator(smash_handle *h, smash_alloc_fn alloc, smash_free_fn fre
     cudaDeviceSynchronize();
     release(h, h->ws);
     release(h, h->tables);
-    release(h, h->dense_acc);
     release(h, h->split);
+    release(h, h->wslot);
+    release(h, h->wcnt);
     release(h, h->stage);
     release(h, h->learn);
     batched_release(h);
@@ -237,6 +237,7 @@ int run_symbolic(smash_handle *h, const RawOperands &op, int64_t n, Plan &pl, in
     int st;
     const BinRule rule = sym_rule(h, op.ncols);
     int *err = (int *)h->err.ptr;
+    h->wcache.valid = false;
     if (row_list && cudaMemsetAsync(pl.bb.bin, 0, (size_t)n, s) != cudaSuccess) return SMASH_ERR_CUDA;
     {
         LaunchTimer lt(h, s, "sym_rowinfo", -1, 256, row_list ? list_n : n, op.a_nnz, 0, 0);
@@ -255,8 +256,22 @@ int run_symbolic(smash_handle *h, const RawOperands &op, int64_t n, Plan &pl, in
         const int *rows = pl.bb.rows + offsets[b];
         int *tok = pl.bb.tokens + b;
         if (b == kBinDense) {
-            LaunchTimer lt(h, s, "sym_dense", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
-            launch_sym_dense(op, rows, counts[b], tok, hash_launch(h, 0, op.ncols), nnz_out, err, s);
+            // the bitmap pass also counts each row's columns per block of
+            // kSubCols columns, for the numeric dense kernel
+            const int nsub = (int)((op.ncols + kSubCols - 1) / kSubCols);
+            if ((st = ensure(h, h->wslot, sizeof(int) * (size_t)n, s))) return st;
+            if ((st = ensure(h, h->wcnt, sizeof(uint16_t) * (size_t)counts[b] * nsub, s))) return st;
+            if (cudaMemsetAsync(h->wslot.ptr, 0xff, sizeof(int) * (size_t)n, s) != cudaSuccess) return SMASH_ERR_CUDA;
+            WinCount wc;
+            wc.wslot = (int *)h->wslot.ptr;
+            wc.wcnt = (uint16_t *)h->wcnt.ptr;
+            wc.nsub = nsub;
+            {
+                LaunchTimer lt(h, s, "sym_dense", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
+                launch_sym_dense(op, rows, counts[b], tok, hash_launch(h, 0, op.ncols), wc, nnz_out, NumCheck{}, err,
+                                 s);
+            }
+            wcache_set(h, op, nsub, counts[b]);
         } else if (b == kBinSpill) {
             const int tb = table_bits(maxsize[b], rule.inv_load);
             const HashLaunch hl = hash_launch(h, tb, op.ncols);
@@ -300,28 +315,47 @@ int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const
         int *tok = pl.bb.tokens + b;
         if (b == kBinDense) {
             const HashLaunch hl = hash_launch(h, 0, op.ncols);
-            void *acc = nullptr;
-            const int H = h->params.hot_cols;
-            const int cs = num_dense_cluster_size(dt, op.ncols, h->params.cluster_max, H);
-            BSlices sl;
-            if (cs == 0) {
-                const size_t need = (size_t)num_dense_grid(dt, hl, op.ncols) * (size_t)op.ncols * vsz;
-                if ((st = ensure(h, h->dense_acc, need, s, true))) return st;
-                acc = h->dense_acc.ptr;
-            } else {
-                const int cap = num_dense_cap(dt, H);
-                const int cpc = cs == 1 ? (int)((op.ncols + 31) & ~31) : cap;
-                const size_t need = dense_plan_bytes(op, cs, cpc, H, vsz);
-                if ((st = ensure(h, h->split, need, s))) return st;
-                LaunchTimer lt(h, s, "dense_plan", -1, 256, op.b_rows, op.a_nnz, 0, op.b_nnz,
-                               4 + (H > 0 ? 1 : 0) + (cs > 1 ? 2 : 0));
-                launch_dense_plan(dt, op, cs, cap, cpc, H, h->params.hot_factor, h->split.ptr, sl, h->sms, s);
-                sl.nslices = cs;
-                sl.cpc = cpc;
+            // 1. per-block column counts of the dense rows: from the symbolic
+            //    phase of the same operands, else counted here (and sizes checked)
+            const int nsub = (int)((op.ncols + kSubCols - 1) / kSubCols);
+            if (!wcache_matches(h, op) || h->wcache.nsub != nsub) {
+                if ((st = ensure(h, h->wslot, sizeof(int) * (size_t)n, s))) return st;
+                if (cudaMemsetAsync(h->wslot.ptr, 0xff, sizeof(int) * (size_t)n, s) != cudaSuccess)
+                    return SMASH_ERR_CUDA;
+                wcache_set(h, op, nsub, 0);
             }
-            LaunchTimer lt(h, s, cs ? "num_dense_cluster" : "num_dense_global", b, 1024, counts[b], sums[b],
-                           sums[16 + b], sums[32 + b]);
-            launch_num_dense(dt, op, rows, counts[b], tok, hl, acc, sl, out, err, s);
+            const int64_t base = h->wcache.slots;
+            if ((st = ensure_keep(h, h->wcnt, sizeof(uint16_t) * (size_t)(base + counts[b]) * nsub,
+                                  sizeof(uint16_t) * (size_t)base * nsub, s)))
+                return st;
+            WinCount wc;
+            wc.wslot = (int *)h->wslot.ptr;
+            wc.wcnt = (uint16_t *)h->wcnt.ptr;
+            wc.nsub = nsub;
+            wc.slot_base = base;
+            wc.skip_slotted = 1;
+            NumCheck nc;
+            nc.c_rp = out.c_rp;
+            nc.c_nnz = out.c_nnz;
+            nc.row_nnz = out.row_nnz;
+            {
+                LaunchTimer lt(h, s, "num_dense_count", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
+                launch_sym_dense(op, rows, counts[b], tok, hl, wc, nullptr, nc, err, s);
+            }
+            h->wcache.slots = base + counts[b];
+            // 2. column windows: slices of B
+            const int cpc = num_window_cols(dt, h->params.dense_blocks);
+            const int nw = (int)((op.ncols + cpc - 1) / cpc);
+            if ((st = ensure(h, h->split, 256 + window_plan_bytes(op, nw, vsz), s))) return st;
+            BSlices sl;
+            {
+                LaunchTimer lt(h, s, "dense_plan", -1, 256, op.b_rows, 0, 0, op.b_nnz, nw > 1 ? 2 : 0);
+                launch_window_plan(dt, op, nw, cpc, (char *)h->split.ptr + 256, sl, h->sms, s);
+            }
+            // 3. (row, window) items
+            LaunchTimer lt(h, s, "num_dense_window", b, 1024 / h->params.dense_blocks, counts[b],
+                           sums[b], sums[16 + b], sums[32 + b]);
+            launch_num_window(dt, op, rows, counts[b], (unsigned long long *)h->split.ptr, hl, sl, wc, out, err, s);
         } else if (b == kBinSpill) {
             const int tb = table_bits(maxsize[b], rule.inv_load);
             const HashLaunch hl = hash_launch(h, tb, op.ncols);

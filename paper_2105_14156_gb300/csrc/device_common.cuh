@@ -12,6 +12,7 @@
 //    word instead of faulting.
 #pragma once
 
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -207,14 +208,12 @@ __device__ __forceinline__ bool a_row_range(const Operands<V> &op, int64_t i, in
     return true;
 }
 
-// Loads the A entry e and the range of the row of B it selects (checked).
-template <typename V, bool NUM>
-__device__ __forceinline__ void load_a_entry(const Operands<V> &op, int64_t e, int &len,
-                                             int64_t &bs, V &av, int *err) {
+// The row of B selected by column k of A: start and length (checked; with a
+// sliced B only this block's column window).
+template <typename V>
+__device__ __forceinline__ void b_row_of(const Operands<V> &op, int k, int &len, int64_t &bs, int *err) {
     len = 0;
     bs = 0;
-    av = V(0);
-    int k = __ldg(op.a_ci + e);
     if ((unsigned)k < (unsigned)op.b_rows) {
         int64_t s = __ldg(op.b_rp + k), t = __ldg(op.b_rp + k + 1);
         if (s >= 0 && t >= s && t <= op.b_nnz) {
@@ -235,6 +234,14 @@ __device__ __forceinline__ void load_a_entry(const Operands<V> &op, int64_t e, i
     } else {
         raise_err(err, kErrBadIndex);
     }
+}
+
+// Loads the A entry e and the range of the row of B it selects (checked).
+template <typename V, bool NUM>
+__device__ __forceinline__ void load_a_entry(const Operands<V> &op, int64_t e, int &len,
+                                             int64_t &bs, V &av, int *err) {
+    av = V(0);
+    b_row_of(op, __ldg(op.a_ci + e), len, bs, err);
     if constexpr (NUM) av = op.a_val[e];
 }
 
@@ -243,10 +250,14 @@ __device__ __forceinline__ V shfl_v(V v, int src) {
     return __shfl_sync(kFull, v, src);
 }
 
+// Steps of 32 products whose loads of B are all issued before the first of
+// them reaches the callback: the memory-level parallelism of one warp.
+constexpr int kProdUnroll = 4;
+
 // Every product of A entries [ab, ae) with their rows of B, enumerated by one
 // warp: lane l takes products l, l+32, ... of each batch of 32 A entries.
-// f(j, a, idx) is called for each product: j = column, a = a_ik (0 when
-// !NUM), idx = position of b_kj in B (the callee loads the value if needed).
+// f(j, a, b) is called for each product: j = column, a = a_ik, b = b_kj (both
+// 0 when !NUM).
 template <typename V, bool NUM, typename F>
 __device__ __forceinline__ void warp_products(const Operands<V> &op, int64_t ab, int64_t ae,
                                               int *err, F &&f) {
@@ -259,22 +270,36 @@ __device__ __forceinline__ void warp_products(const Operands<V> &op, int64_t ab,
         const int incl = warp_incl_scan(len);
         const int total = __shfl_sync(kFull, incl, 31);
         const int64_t start = bs - (incl - len);   // product p of this entry reads b[start + p]
-        for (int p0 = 0; p0 < total; p0 += 32) {
-            const int p = p0 + lane;
-            int o = 0;
+        for (int p0 = 0; p0 < total; p0 += 32 * kProdUnroll) {
+            int jv[kProdUnroll];
+            V av_u[kProdUnroll], bv[kProdUnroll];
+            bool act[kProdUnroll];
 #pragma unroll
-            for (int s = 16; s >= 1; s >>= 1) {
-                int c = __shfl_sync(kFull, incl, o + s - 1);
-                if (c <= p) o += s;
+            for (int u = 0; u < kProdUnroll; ++u) {
+                const int p = p0 + 32 * u + lane;
+                act[u] = p < total;
+                int o = 0;
+#pragma unroll
+                for (int s = 16; s >= 1; s >>= 1) {
+                    int c = __shfl_sync(kFull, incl, o + s - 1);
+                    if (c <= p) o += s;
+                }
+                const int64_t st = __shfl_sync(kFull, start, o);
+                av_u[u] = V(0);
+                bv[u] = V(0);
+                if constexpr (NUM) av_u[u] = shfl_v(av, o);
+                jv[u] = 0;
+                if (act[u]) {
+                    jv[u] = __ldg(op.b_ci + st + p);
+                    if constexpr (NUM) bv[u] = __ldg(op.b_val + st + p);
+                }
             }
-            const int64_t st = __shfl_sync(kFull, start, o);
-            V a = V(0);
-            if constexpr (NUM) a = shfl_v(av, o);
-            if (p < total) {
-                const int64_t idx = st + p;
-                const int j = __ldg(op.b_ci + idx);
-                if ((unsigned)j < (unsigned)op.ncols) f(j, a, idx);
-                else raise_err(err, kErrBadIndex);
+#pragma unroll
+            for (int u = 0; u < kProdUnroll; ++u) {
+                if (act[u]) {
+                    if ((unsigned)jv[u] < (unsigned)op.ncols) f(jv[u], av_u[u], bv[u]);
+                    else raise_err(err, kErrBadIndex);
+                }
             }
         }
     }
@@ -313,14 +338,25 @@ __device__ __forceinline__ ProdScratch<V> carve_prod_scratch(unsigned char *p) {
     return s;
 }
 
+// Entry of product q + lane in one step of 32 products of a run of staged
+// entries, every one with at least one product, whose inclusive product ends
+// relative to q are e (lane l: entry c0 + l; lane 0's entry holds product q,
+// so its e >= 1): the number of entries that end at or before q + lane.
+__device__ __forceinline__ int step_entry(int e) {
+    const unsigned ends = __reduce_or_sync(kFull, (e >= 1 && e <= 31) ? (1u << e) : 0u);
+    return __popc(ends & ((2u << lane_id()) - 1u));
+}
+
 // Every product of A entries [ab, ae), enumerated by a group of GS >= 64
 // threads: batches of GS A entries are staged in shared memory (entries with
 // an empty row of B dropped), the batch's products are split into one
 // contiguous range per warp, and each warp walks its range 32 products at a
-// time. A lane finds the entry of its product by binary lifting over a window
-// of 32 staged prefix sums that starts at the entry of the step's first
-// product; the window advances with the walk, so only the first step of a
-// range needs a binary search over the whole batch.
+// time, kProdUnroll steps per round. The window of 32 staged entries that
+// starts at the entry of the step's first product holds every product of the
+// step; a lane finds its entry from the set of entry ends inside the step.
+// Only the first step of a range needs a binary search over the whole batch.
+// The columns of A of the next batch are fetched before the current batch's
+// products are walked.
 template <typename V, bool NUM, int GS, int NT, typename F>
 __device__ __forceinline__ void group_products(const Operands<V> &op, int64_t ab, int64_t ae,
                                                const ProdScratch<V> &sc, int *err, F &&f) {
@@ -328,11 +364,17 @@ __device__ __forceinline__ void group_products(const Operands<V> &op, int64_t ab
     const int t = G::tid();
     const int lane = lane_id();
     const int w = G::wid();
+    int k_next = -1;
+    V av_next = V(0);
+    if (ab + t < ae) {
+        k_next = __ldg(op.a_ci + ab + t);
+        if constexpr (NUM) av_next = op.a_val[ab + t];
+    }
     for (int64_t base = ab; base < ae; base += GS) {
         int len = 0;
         int64_t bs = 0;
-        V av = V(0);
-        if (base + t < ae) load_a_entry<V, NUM>(op, base + t, len, bs, av, err);
+        const V av = av_next;
+        if (base + t < ae) b_row_of(op, k_next, len, bs, err);
         // one scan of (entry has products, product count): count in the high half
         const long long packed = ((long long)(len > 0 ? 1 : 0) << 32) | (long long)len;
         long long tot64;
@@ -346,6 +388,10 @@ __device__ __forceinline__ void group_products(const Operands<V> &op, int64_t ab
             sc.start[cidx] = bs - excl;
             if constexpr (NUM) sc.av[cidx] = av;
         }
+        if (base + GS + t < ae) {
+            k_next = __ldg(op.a_ci + base + GS + t);
+            if constexpr (NUM) av_next = op.a_val[base + GS + t];
+        }
         G::sync();
         const int per = (total + G::kWarps - 1) / G::kWarps;
         const int lo = w * per;
@@ -358,26 +404,40 @@ __device__ __forceinline__ void group_products(const Operands<V> &op, int64_t ab
                 else b = m;
             }
             int c0 = a;
-            for (int pb = lo; pb < hi; pb += 32) {
-                const int w_incl = sc.incl[min(c0 + lane, nf - 1)];
-                const int p = pb + lane;
-                int o = 0;
+            for (int pb = lo; pb < hi; pb += 32 * kProdUnroll) {
+                int jv[kProdUnroll];
+                V av_u[kProdUnroll], bv[kProdUnroll];
+                bool act[kProdUnroll];
 #pragma unroll
-                for (int s = 16; s >= 1; s >>= 1) {
-                    const int c = __shfl_sync(kFull, w_incl, o + s - 1);
-                    if (c <= p) o += s;
+                for (int u = 0; u < kProdUnroll; ++u) {
+                    const int q = pb + 32 * u;
+                    act[u] = false;
+                    jv[u] = 0;
+                    av_u[u] = V(0);
+                    bv[u] = V(0);
+                    if (q < hi) {
+                        const int c = c0 + lane;
+                        const int e = c < nf ? sc.incl[c] - q : INT_MAX;
+                        const int ci = c0 + step_entry(e);
+                        act[u] = q + lane < hi;
+                        if (act[u]) {
+                            const int64_t idx = sc.start[ci] + q + lane;
+                            jv[u] = __ldg(op.b_ci + idx);
+                            if constexpr (NUM) {
+                                bv[u] = __ldg(op.b_val + idx);
+                                av_u[u] = sc.av[ci];
+                            }
+                        }
+                        c0 += __popc(__ballot_sync(kFull, e <= 32));
+                    }
                 }
-                const int o31 = __shfl_sync(kFull, o, 31);
-                const int inc31 = __shfl_sync(kFull, w_incl, o31);
-                if (p < hi) {
-                    const int ci = c0 + o;
-                    const int64_t idx = sc.start[ci] + p;
-                    const int j = __ldg(op.b_ci + idx);
-                    if ((unsigned)j < (unsigned)op.ncols) f(j, NUM ? sc.av[ci] : V(0), idx);
-                    else raise_err(err, kErrBadIndex);
+#pragma unroll
+                for (int u = 0; u < kProdUnroll; ++u) {
+                    if (act[u]) {
+                        if ((unsigned)jv[u] < (unsigned)op.ncols) f(jv[u], av_u[u], bv[u]);
+                        else raise_err(err, kErrBadIndex);
+                    }
                 }
-                // entry of product pb + 32: the entry of pb + 31, or the next one if that ends there
-                c0 += o31 + (inc31 <= pb + 32 ? 1 : 0);
             }
         }
         G::sync();
@@ -390,11 +450,6 @@ __device__ __forceinline__ void row_products(const Operands<V> &op, int64_t ab, 
                                              const ProdScratch<V> &sc, int *err, F &&f) {
     if constexpr (GS == 32) warp_products<V, NUM>(op, ab, ae, err, f);
     else group_products<V, NUM, GS, NT>(op, ab, ae, sc, err, f);
-}
-
-template <typename V>
-__device__ __forceinline__ V b_value(const Operands<V> &op, int64_t idx) {
-    return __ldg(op.b_val + idx);
 }
 
 // ---------------------------------------------------------------------------

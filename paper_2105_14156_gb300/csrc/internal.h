@@ -48,8 +48,20 @@ struct smash_handle {
     void *ctx = nullptr;
     smash::DevBuf ws;         // per-call arrays
     smash::DevBuf tables;     // spill hash tables
-    smash::DevBuf dense_acc;  // dense accumulators (kept zero between rows)
-    smash::DevBuf split;      // dense-row plan: column windows, slices of B, hot columns
+    smash::DevBuf split;      // dense rows: slices of B by column window, item counter
+    smash::DevBuf wslot;      // dense rows: count slot per row of A (-1: none)
+    smash::DevBuf wcnt;       // dense rows: distinct columns per kSubCols block, per slot (uint16)
+    // What wslot / wcnt describe: the structure of the (A, B) pair whose dense
+    // rows they count (device pointers and sizes), the number of column blocks
+    // and the slots in use. Set by the symbolic phase, extended by numeric
+    // count passes, cleared by calls that may change the structure.
+    struct {
+        bool valid = false;
+        const void *ptr[4] = {nullptr, nullptr, nullptr, nullptr};
+        int64_t dims[5] = {0, 0, 0, 0, 0};
+        int nsub = 0;
+        int64_t slots = 0;
+    } wcache;
     smash::DevBuf stage;      // learned path: capacity-padded staging of C
     smash::DevBuf learn;      // learned path: per-row arrays
     smash::DevBuf err;        // kNumErr ints (+ scratch words)
@@ -116,6 +128,50 @@ inline int ensure(smash_handle *h, DevBuf &b, size_t need, cudaStream_t s, bool 
     b.bytes = want;
     if (zero && cudaMemsetAsync(p, 0, want, s) != cudaSuccess) return SMASH_ERR_CUDA;
     return SMASH_OK;
+}
+
+// Grow-only buffer whose first `keep` bytes survive the growth.
+inline int ensure_keep(smash_handle *h, DevBuf &b, size_t need, size_t keep, cudaStream_t s) {
+    if (need == 0) need = 256;
+    if (b.bytes >= need) return SMASH_OK;
+    size_t want = need + need / 4;
+    want = (want + 4095) & ~size_t(4095);
+    void *p = h->alloc(want, h->ctx);
+    if (!p) return SMASH_ERR_ALLOC;
+    if (keep > b.bytes) keep = b.bytes;
+    if (keep && b.ptr && cudaMemcpyAsync(p, b.ptr, keep, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+        h->free_fn(p, h->ctx);
+        return SMASH_ERR_CUDA;
+    }
+    cudaStreamSynchronize(s);
+    if (b.ptr) h->free_fn(b.ptr, h->ctx);
+    b.ptr = p;
+    b.bytes = want;
+    return SMASH_OK;
+}
+
+// Identity of the structure of an operand pair, for the dense-row counts.
+inline bool wcache_matches(const smash_handle *h, const RawOperands &op) {
+    const auto &c = h->wcache;
+    return c.valid && c.ptr[0] == op.a_rp && c.ptr[1] == op.a_ci && c.ptr[2] == op.b_rp && c.ptr[3] == op.b_ci &&
+           c.dims[0] == op.a_rows && c.dims[1] == op.a_nnz && c.dims[2] == op.b_rows && c.dims[3] == op.b_nnz &&
+           c.dims[4] == op.ncols;
+}
+
+inline void wcache_set(smash_handle *h, const RawOperands &op, int nsub, int64_t slots) {
+    auto &c = h->wcache;
+    c.valid = true;
+    c.ptr[0] = op.a_rp;
+    c.ptr[1] = op.a_ci;
+    c.ptr[2] = op.b_rp;
+    c.ptr[3] = op.b_ci;
+    c.dims[0] = op.a_rows;
+    c.dims[1] = op.a_nnz;
+    c.dims[2] = op.b_rows;
+    c.dims[3] = op.b_nnz;
+    c.dims[4] = op.ncols;
+    c.nsub = nsub;
+    c.slots = slots;
 }
 
 inline cudaEvent_t take_event(smash_handle *h) {
@@ -219,9 +275,7 @@ inline int check_params(const smash_params *p) {
     if (p->dense_ratio < 0 || p->bitmap_ratio < 0) return SMASH_ERR_INVALID_ARG;
     if (p->spill_blocks_per_sm < 0 || p->spill_blocks_per_sm > 8) return SMASH_ERR_INVALID_ARG;
     if (p->sym_dense_ratio < 0) return SMASH_ERR_INVALID_ARG;
-    if (p->hot_cols < 0 || p->hot_cols > 512 || p->hot_factor < 1) return SMASH_ERR_INVALID_ARG;
-    if (p->cluster_max != 1 && p->cluster_max != 2 && p->cluster_max != 4 && p->cluster_max != 8)
-        return SMASH_ERR_INVALID_ARG;
+    if (p->dense_blocks != 1 && p->dense_blocks != 2 && p->dense_blocks != 4) return SMASH_ERR_INVALID_ARG;
     return SMASH_OK;
 }
 
@@ -344,8 +398,8 @@ inline int read_flags(smash_handle *h, cudaStream_t s, bool clear) {
     if (clear && cudaMemsetAsync(h->err.ptr, 0, kNumErr * sizeof(int), s) != cudaSuccess) return SMASH_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SMASH_ERR_CUDA;
     const int st = status_from_flags((const long long *)hb);
-    // a row that failed may have left a dense accumulator dirty: drop them
-    if (st != SMASH_OK) release(h, h->dense_acc);
+    // after a failure the dense-row counts may not describe the inputs any more
+    if (st != SMASH_OK) h->wcache.valid = false;
     return st;
 }
 
@@ -370,9 +424,9 @@ inline BinRule sym_rule(const smash_handle *h, int64_t ncols) {
 inline BinRule num_rule(const smash_handle *h, int64_t ncols, int dtype) {
     BinRule r;
     r.inv_load = 1.0f / h->params.max_load;
-    const bool dense_fits = num_dense_cluster_size(dtype, (int)ncols, h->params.cluster_max,
-                                                   h->params.hot_cols) > 0 ||
-                            ncols <= dense_bitmap_max_cols();
+    // dense rows need their columns counted in one bitmap (count pass) and a
+    // column window that fits shared memory
+    const bool dense_fits = ncols <= dense_bitmap_max_cols() && num_window_cols(dtype, h->params.dense_blocks) > 0;
     r.dense_ok = (h->params.dense_ratio > 0 && dense_fits) ? 1 : 0;
     r.dense_min = r.dense_ok ? (ncols + h->params.dense_ratio - 1) / h->params.dense_ratio : (1ll << 62);
     if (r.dense_min < 1) r.dense_min = 1;
@@ -405,7 +459,7 @@ inline HashLaunch hash_launch(const smash_handle *h, int tbits, int64_t ncols) {
     hl.colbits = colbits_of(ncols);
     hl.sms = h->sms;
     hl.blocks_per_sm = h->params.spill_blocks_per_sm > 0 ? h->params.spill_blocks_per_sm : 1;
-    hl.cluster_max = h->params.cluster_max;
+    hl.dense_blocks = h->params.dense_blocks;
     return hl;
 }
 

@@ -161,8 +161,8 @@ __device__ void warp_row(const BatchArgs &p, const BatchMat &M, int64_t g, int64
         if (NUM)
             for (int j = lane; j < M.ncols; j += 32) acc[j] = V(0);
         __syncwarp();
-        warp_products<V, NUM>(op, ab, ae, p.err, [&](int j, V a, int64_t idx) {
-            if (NUM) atomicAdd(acc + j, a * b_value(op, idx));
+        warp_products<V, NUM>(op, ab, ae, p.err, [&](int j, V a, V bkj) {
+            if (NUM) atomicAdd(acc + j, a * bkj);
             const unsigned bit = 1u << (j & 31);
             if (!(*(volatile unsigned *)(bm + (j >> 5)) & bit)) atomicOr(bm + (j >> 5), bit);
         });
@@ -204,14 +204,14 @@ __device__ void warp_row(const BatchArgs &p, const BatchMat &M, int64_t g, int64
     HashCfg hc = p.hc;
     hc.colbits = colbits(M.ncols);
     int cnt = 0;
-    warp_products<V, NUM>(op, ab, ae, p.err, [&](int j, V a, int64_t idx) {
+    warp_products<V, NUM>(op, ab, ae, p.err, [&](int j, V a, V bkj) {
         bool ins;
         const int h = hash_find_or_insert<false>(keys, tb, hc, j, ins);
         if (h < 0) {
             raise_err(p.err, kErrTableFull);
             return;
         }
-        if (NUM) atomicAdd(vals + h, a * b_value(op, idx));
+        if (NUM) atomicAdd(vals + h, a * bkj);
         cnt += ins ? 1 : 0;
     });
     const int tot = warp_sum(cnt);
@@ -248,14 +248,14 @@ __device__ void block_row(const BatchArgs &p, const BatchMat &M, int64_t g, int6
     HashCfg hc = p.hc;
     hc.colbits = colbits(M.ncols);
     int cnt = 0;
-    group_products<V, NUM, kBNT, kBNT>(op, ab, ae, sm.sc, p.err, [&](int j, V a, int64_t idx) {
+    group_products<V, NUM, kBNT, kBNT>(op, ab, ae, sm.sc, p.err, [&](int j, V a, V bkj) {
         bool ins;
         const int h = hash_find_or_insert<false>(keys, tb, hc, j, ins);
         if (h < 0) {
             raise_err(p.err, kErrTableFull);
             return;
         }
-        if (NUM) atomicAdd(vals + h, a * b_value(op, idx));
+        if (NUM) atomicAdd(vals + h, a * bkj);
         cnt += ins ? 1 : 0;
     });
     const int tot = G::template sum<int>(cnt, sm.sc.red);

@@ -12,21 +12,16 @@
 //                  32-bit word gives every tag its position directly;
 //   - bitonic:     the compacted entries are sorted in shared memory.
 // Table placements as in the symbolic phase: shared memory (k_num_hash),
-// dense accumulator for dense rows (k_num_dense: values indexed by column,
-// in shared memory when cols(B) is small, else a global-memory row buffer,
-// occupancy in a shared bitmap), and a global-memory hash table (k_num_spill;
-// Version 3's table in DRAM).
+// dense accumulators for dense rows (k_num_window: one column window of the
+// row per work item, values indexed by column, occupancy in a bitmap), and a
+// global-memory hash table (k_num_spill; Version 3's table in DRAM).
 #include <climits>
-
-#include <cooperative_groups.h>
 
 #include "device_common.cuh"
 #include "kernels.h"
 #include "writeout.cuh"
 
 namespace smash {
-
-namespace cg = cooperative_groups;
 
 // ----- shared-memory hash rows -----------------------------------------------
 template <typename V, int GS, int NT>
@@ -73,8 +68,8 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
         int64_t ab = 0, ae = 0;
         if (ok) a_row_range(op, i, ab, ae, err);
         int cnt = 0, ovf = 0;
-        row_products<V, true, GS, NT>(op, ab, ae, sc, err, [&](int j, V a, int64_t idx) {
-            const V v = a * b_value(op, idx);
+        row_products<V, true, GS, NT>(op, ab, ae, sc, err, [&](int j, V a, V bkj) {
+            const V v = a * bkj;
             bool ins;
             const int h = hash_find_or_insert<false>(keys, tbits, hc, j, ins);
             if (h >= 0) {
@@ -113,205 +108,180 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
     }
 }
 
-// ----- dense rows -------------------------------------------------------------
-template <typename V, int NT, bool SACC>
-__global__ void __launch_bounds__(NT) k_num_dense(Operands<V> op, const int *rows, int count, int *token,
-                                                  int words, V *acc_g, NumOutT<V> out, int *err) {
-    using G = Group<NT, NT>;
+// ----- dense rows: (row, column window) work items ---------------------------
+// A dense row's accumulator is cut into windows of cpc columns; every (row,
+// window) pair is an independent item. The block owns one window's dense
+// accumulator (values indexed by column, occupancy in a bitmap) in shared
+// memory, enumerates only the products that land in the window (B sliced by
+// window), and writes the window's columns in order at the window's offset in
+// the row, known from the per-block column counts of the bitmap pass. No two
+// blocks ever wait on each other.
+
+// Position of the n-th (0-based) set bit of x (n < popc(x)), by halving.
+__device__ __forceinline__ int nth_set_bit(unsigned x, int n) {
+    int pos = 0;
+    int c = __popc(x & 0xffffu);
+    if (n >= c) { n -= c; x >>= 16; pos += 16; }
+    c = __popc(x & 0xffu);
+    if (n >= c) { n -= c; x >>= 8; pos += 8; }
+    c = __popc(x & 0xfu);
+    if (n >= c) { n -= c; x >>= 4; pos += 4; }
+    c = __popc(x & 0x3u);
+    if (n >= c) { n -= c; x >>= 2; pos += 2; }
+    if (n >= (int)(x & 1u)) pos += 1;
+    return pos;
+}
+
+template <typename V, int NT>
+__global__ void __launch_bounds__(NT) k_num_window(Operands<V> op, const int *rows, int count, int nw, int cpc,
+                                                   int subs_per_win, WinCount wc, NumOutT<V> out,
+                                                   unsigned long long *token, int *err) {
+    constexpr int kWarps = NT / 32;
+    constexpr int kMaxChunks = kMaxWinCols / 1024;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_row;
-    unsigned *bm = (unsigned *)smem;
-    int *pre = (int *)(bm + words);
-    V *sacc = (V *)(smem + (size_t)words * 8);
-    const size_t acc_bytes = SACC ? (((size_t)op.ncols * sizeof(V) + 15) & ~size_t(15)) : 0;
-    const ProdScratch<V> sc = carve_prod_scratch<V, NT>(smem + (size_t)words * 8 + acc_bytes);
-    V *acc = SACC ? sacc : acc_g + (size_t)blockIdx.x * (size_t)op.ncols;
+    __shared__ long long s_item;
+    __shared__ int s_off, s_cnt;
+    __shared__ int s_chunk[kMaxChunks + 1];
+    const int words = cpc >> 5;
+    V *acc = (V *)smem;
+    unsigned *bm = (unsigned *)(smem + (size_t)cpc * sizeof(V));
+    const ProdScratch<V> sc = carve_prod_scratch<V, NT>((unsigned char *)(bm + words));
     const int t = threadIdx.x;
+    const int lane = lane_id();
+    const int wp = t >> 5;
+    for (int j = t; j < cpc; j += NT) acc[j] = V(0);
+    for (int w = t; w < words; w += NT) bm[w] = 0u;
+    const int64_t items = (int64_t)count * nw;
     for (;;) {
-        if (t == 0) s_row = atomicAdd(token, 1);
+        if (t == 0) s_item = (long long)atomicAdd(token, 1ull);
         __syncthreads();
-        const int r = s_row;
-        if (r >= count) break;
+        const int64_t item = s_item;
+        if (item >= items) break;
+        const int r = (int)(item / nw);
+        const int w = (int)(item - (int64_t)r * nw);
         const int i = rows[r];
-        int64_t c0;
-        int n_exp;
-        const bool ok = out_range(out, i, c0, n_exp, err);
-        for (int w = t; w < words; w += NT) bm[w] = 0u;
-        if constexpr (SACC)
-            for (int j = t; j < op.ncols; j += NT) sacc[j] = V(0);
-        __syncthreads();
-        int64_t ab = 0, ae = 0;
-        if (ok) a_row_range(op, i, ab, ae, err);
-        row_products<V, true, NT, NT>(op, ab, ae, sc, err, [&](int j, V a, int64_t idx) {
-            const V v = a * b_value(op, idx);
-            atomicAdd(acc + j, v);
-            const unsigned bit = 1u << (j & 31);
-            unsigned *w = bm + (j >> 5);
-            if (!(*(volatile unsigned *)w & bit)) atomicOr(w, bit);
-        });
-        if constexpr (!SACC) __threadfence();
-        __syncthreads();
-        const int tot = bitmap_prefix<NT, NT>(bm, pre, words, sc.red);
-        __syncthreads();
-        if (out.row_nnz) {
-            const bool over = tot > n_exp;
-            if (t == 0) out.row_nnz[i] = over ? -1 : tot;
-            if (over) n_exp = 0;   // still drain the accumulator below, write nothing
-        } else if (t == 0 && tot != n_exp) {
-            raise_err(err, kErrCountMismatch);
+        const int slot = wc.wslot[i];
+        bool skip = out.row_nnz && out.row_nnz[i] < 0;   // capacity mode: the row overflowed
+        if (!skip && slot < 0) {
+            if (t == 0) raise_err(err, kErrCountMismatch);
+            skip = true;
         }
-        for (int w = t; w < words; w += NT) {
-            unsigned bits = bm[w];
-            int pos = pre[w];
-            while (bits) {
-                const int b = __ffs(bits) - 1;
-                bits &= bits - 1u;
-                const int j = (w << 5) + b;
-                V v;
-                if constexpr (SACC) {
-                    v = acc[j];
-                } else {
-                    v = __ldcg(acc + j);
-                    __stcg(acc + j, V(0));
-                }
-                if (pos < n_exp) {
-                    out.c_ci[c0 + pos] = j;
-                    out.c_val[c0 + pos] = v;
-                }
-                ++pos;
+        int64_t c0 = 0;
+        int n_exp = 0;
+        if (!skip && !out_range(out, i, c0, n_exp, err)) skip = true;
+        if (skip) {
+            __syncthreads();
+            continue;
+        }
+        if (wp == 0) {
+            const uint16_t *sub = wc.wcnt + (size_t)slot * wc.nsub;
+            const int s_lo = w * subs_per_win;
+            const int s_hi = min(s_lo + subs_per_win, wc.nsub);
+            int before = 0, mine = 0;
+            for (int q = lane; q < s_hi; q += 32) {
+                const int c = sub[q];
+                if (q < s_lo) before += c;
+                else mine += c;
+            }
+            before = warp_sum(before);
+            mine = warp_sum(mine);
+            if (lane == 0) {
+                s_off = before;
+                s_cnt = mine;
             }
         }
-        if constexpr (!SACC) __threadfence();
+        const int lo = w * cpc;
+        const int width = min(cpc, op.ncols - lo);
+        op.slice = w;
+        int64_t ab = 0, ae = 0;
+        a_row_range(op, i, ab, ae, err);
+        group_products<V, true, NT, NT>(op, ab, ae, sc, err, [&](int j, V a, V bkj) {
+            const unsigned off = (unsigned)(j - lo);
+            if (off < (unsigned)width) {
+                atomicAdd(acc + off, a * bkj);
+                const unsigned bit = 1u << (off & 31);
+                unsigned *bw = bm + (off >> 5);
+                if (!(*(volatile unsigned *)bw & bit)) atomicOr(bw, bit);
+            }
+        });
+        // write-out in chunks of 32 bitmap words (1024 columns): chunk totals,
+        // their prefix, then every chunk's columns in order.
+        const int wwords = (width + 31) >> 5;
+        const int nch = (wwords + 31) >> 5;
+        for (int c = wp; c < nch; c += kWarps) {
+            const int x = 32 * c + lane;
+            const int tot = warp_sum(x < wwords ? __popc(bm[x]) : 0);
+            if (lane == 0) s_chunk[c] = tot;
+        }
+        __syncthreads();
+        if (wp == 0) {
+            int run = 0;
+            for (int c0w = 0; c0w < nch; c0w += 32) {
+                const int c = c0w + lane;
+                const int v = c < nch ? s_chunk[c] : 0;
+                const int incl = warp_incl_scan(v);
+                if (c < nch) s_chunk[c] = run + incl - v;
+                run += __shfl_sync(kFull, incl, 31);
+            }
+            if (lane == 0) s_chunk[nch] = run;
+        }
+        __syncthreads();
+        const int total = s_chunk[nch];
+        const int base = s_off;
+        if (t == 0 && total != s_cnt) raise_err(err, kErrCountMismatch);
+        const bool ok = total == s_cnt && (int64_t)base + total <= (int64_t)n_exp;
+        for (int c = wp; c < nch; c += kWarps) {
+            const int x = 32 * c + lane;
+            const unsigned word = x < wwords ? bm[x] : 0u;
+            const int incl = warp_incl_scan(__popc(word));
+            const int T = __shfl_sync(kFull, incl, 31);
+            const int64_t cb = c0 + base + s_chunk[c];
+            if (T >= 256) {
+                // dense chunk: word by word, lane = bit
+                for (int q = 0; q < 32; ++q) {
+                    const unsigned wq = __shfl_sync(kFull, word, q);
+                    const int pre = __shfl_sync(kFull, incl, q) - __popc(wq);
+                    if ((wq >> lane) & 1u) {
+                        const int col = ((32 * c + q) << 5) + lane;
+                        const V v = acc[col];
+                        acc[col] = V(0);
+                        const int64_t pos = cb + pre + __popc(wq & lanemask_lt());
+                        if (ok) {
+                            out.c_ci[pos] = lo + col;
+                            out.c_val[pos] = v;
+                        }
+                    }
+                }
+            } else {
+                // sparse chunk: 32 consecutive outputs per step; the owner word of
+                // output o is the first lane whose inclusive count exceeds o
+                for (int o0 = 0; o0 < T; o0 += 32) {
+                    const int o = o0 + lane;
+                    int L = 0;
+#pragma unroll
+                    for (int st = 16; st >= 1; st >>= 1) {
+                        const int v = __shfl_sync(kFull, incl, L + st - 1);
+                        if (v <= o) L += st;
+                    }
+                    const unsigned wl = __shfl_sync(kFull, word, L);
+                    const int el = __shfl_sync(kFull, incl, L) - __popc(wl);
+                    if (o < T) {
+                        const int col = ((32 * c + L) << 5) + nth_set_bit(wl, o - el);
+                        const V v = acc[col];
+                        acc[col] = V(0);
+                        if (ok) {
+                            out.c_ci[cb + o] = lo + col;
+                            out.c_val[cb + o] = v;
+                        }
+                    }
+                }
+            }
+            if (x < wwords) bm[x] = 0u;
+        }
         __syncthreads();
     }
 }
 
-// ----- dense rows in a thread-block cluster -----------------------------------
-// The row's accumulator (one value per column of B) is split over the shared
-// memory of the CS blocks of a cluster: block q owns columns
-// [q*cpc, (q+1)*cpc). Every block enumerates all products of the row and keeps
-// those in its own window, so all accumulation uses local shared-memory
-// atomics (a remote, distributed-shared-memory atomic costs about as much as
-// twenty local integer ones). Each block ranks its columns by bitmap prefix
-// counts; the blocks' counts, exchanged through distributed shared memory,
-// give each window's offset, so the row is written sorted without a sort.
-// Accumulator and bitmap are cleared as they are read out.
-// Hot columns (see k_split.cu) accumulate in private per-warp slots instead:
-// their products then contend only within one warp, and the slots are summed
-// into the accumulator once per row.
-template <typename V, int CS>
-__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(1024)
-    k_num_dense_cluster(Operands<V> op, const int *rows, int count, int *token, int cpc, const int *splits,
-                        NumOutT<V> out, const unsigned *hot_bm_g, const int *hot_col_g, const int *hot_n_g, int H,
-                        int *err) {
-    constexpr int NT = 1024;
-    cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_row[2];
-    __shared__ int s_cnt[2];
-    __shared__ int s_base, s_total;
-    const int words = cpc >> 5;
-    V *acc = (V *)smem;
-    V *priv = (V *)(smem + (size_t)cpc * sizeof(V));           // [32 warps][H]
-    unsigned *bm = (unsigned *)(priv + (size_t)32 * H);
-    int *pre = (int *)(bm + words);
-    unsigned *hbm = (unsigned *)(pre + words);                   // H > 0 only
-    int *hpre = (int *)(hbm + (H > 0 ? words : 0));
-    int *hcol = hpre + (H > 0 ? words : 0);
-    const ProdScratch<V> sc = carve_prod_scratch<V, NT>((unsigned char *)(hcol + H));
-    const int t = threadIdx.x;
-    const int wp = t >> 5;
-    const unsigned lo = (unsigned)splits[rank];
-    const unsigned width = (unsigned)(splits[rank + 1] - splits[rank]);   // <= cpc
-    op.slice = rank;   // with a sliced B, enumerate this block's window only
-    for (int j = t; j < cpc; j += NT) acc[j] = V(0);
-    for (int w = t; w < words; w += NT) bm[w] = 0u;
-    int hn = 0;
-    if (H > 0) {
-        for (int k = t; k < 32 * H; k += NT) priv[k] = V(0);
-        for (int w = t; w < words; w += NT) hbm[w] = hot_bm_g[(size_t)rank * words + w];
-        hn = hot_n_g[rank];
-        for (int k = t; k < hn; k += NT) hcol[k] = hot_col_g[(size_t)rank * H + k];
-        __syncthreads();
-        bitmap_prefix<NT, NT>(hbm, hpre, words, sc.red);
-    }
-    for (int it = 0;; ++it) {
-        const int par = it & 1;
-        if (rank == 0 && t == 0) s_row[par] = atomicAdd(token, 1);
-        cl.sync();
-        const int r = *cl.map_shared_rank(&s_row[par], 0);
-        if (r >= count) break;
-        const int i = rows[r];
-        int64_t c0;
-        int n_exp;
-        const bool ok = out_range(out, i, c0, n_exp, err);
-        int64_t ab = 0, ae = 0;
-        if (ok) a_row_range(op, i, ab, ae, err);
-        group_products<V, true, NT, NT>(op, ab, ae, sc, err, [&](int j, V a, int64_t idx) {
-            const unsigned off = (unsigned)j - lo;
-            if (off < width) {
-                const V v = a * b_value(op, idx);
-                const unsigned bit = 1u << (off & 31);
-                const int w = (int)(off >> 5);
-                if (H > 0 && (hbm[w] & bit)) atomicAdd(priv + wp * H + hpre[w] + __popc(hbm[w] & (bit - 1u)), v);
-                else atomicAdd(acc + off, v);
-                if (!(*(volatile unsigned *)(bm + w) & bit)) atomicOr(bm + w, bit);
-            }
-        });
-        __syncthreads();
-        for (int k = t; k < hn; k += NT) {
-            V sum = V(0);
-            for (int q = 0; q < 32; ++q) {
-                sum += priv[q * H + k];
-                priv[q * H + k] = V(0);
-            }
-            acc[hcol[k]] = sum;
-        }
-        if (H > 0) __syncthreads();
-        const int cnt = bitmap_prefix<NT, NT>(bm, pre, words, sc.red);
-        if (t == 0) s_cnt[par] = cnt;
-        cl.sync();
-        if (t == 0) {
-            int base = 0, total = 0;
-            for (int q = 0; q < CS; ++q) {
-                const int c = *cl.map_shared_rank(&s_cnt[par], q);
-                if (q < rank) base += c;
-                total += c;
-            }
-            s_base = base;
-            s_total = total;
-        }
-        __syncthreads();
-        const int base = s_base;
-        if (out.row_nnz) {
-            const bool over = s_total > n_exp;
-            if (rank == 0 && t == 0) out.row_nnz[i] = over ? -1 : s_total;
-            if (over) n_exp = 0;   // still drain the accumulator below, write nothing
-        } else if (rank == 0 && t == 0 && s_total != n_exp) {
-            raise_err(err, kErrCountMismatch);
-        }
-        for (int w = t; w < words; w += NT) {
-            unsigned bits = bm[w];
-            int pos = base + pre[w];
-            bm[w] = 0u;
-            while (bits) {
-                const int b = __ffs(bits) - 1;
-                bits &= bits - 1u;
-                const int jl = (w << 5) + b;
-                const V v = acc[jl];
-                acc[jl] = V(0);
-                if (pos < n_exp) {
-                    out.c_ci[c0 + pos] = (int)lo + jl;
-                    out.c_val[c0 + pos] = v;
-                }
-                ++pos;
-            }
-        }
-        __syncthreads();
-    }
-    cl.sync();
-}
 
 // ----- global-memory hash rows ------------------------------------------------
 template <int NT>
@@ -372,8 +342,8 @@ __global__ void __launch_bounds__(NT) k_num_spill(Operands<V> op, const int *row
         int64_t ab = 0, ae = 0;
         if (ok) a_row_range(op, i, ab, ae, err);
         int cnt = 0, ovf = 0;
-        row_products<V, true, NT, NT>(op, ab, ae, sc, err, [&](int j, V a, int64_t idx) {
-            const V v = a * b_value(op, idx);
+        row_products<V, true, NT, NT>(op, ab, ae, sc, err, [&](int j, V a, V bkj) {
+            const V v = a * bkj;
             bool ins;
             const int h = hash_find_or_insert<true>(keys, tb, hc, j, ins);
             if (h >= 0) {
@@ -449,6 +419,18 @@ int max_smem_per_block() {
         int v = 0;
         cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cached = v > 0 ? v : 232448;
+    }
+    return cached;
+}
+
+int max_smem_per_sm() {
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cached = v > 0 ? v : 233472;
     }
     return cached;
 }
@@ -557,117 +539,82 @@ void launch_num_hash(int dtype, const RawOperands &r, const int *rows, int count
     else num_hash_typed<float>(r, rows, count, token, hl, bitmap_ratio, out, err, s);
 }
 
-template <typename V>
-static size_t dense_smem(int ncols, bool sacc) {
-    const int words = (ncols + 31) / 32;
-    size_t b = (size_t)words * 8 + num_scratch_bytes<V, 1024>();
-    if (sacc) b += ((size_t)ncols * sizeof(V) + 15) & ~size_t(15);
-    return b;
-}
-
-bool num_dense_uses_smem_acc(int dtype, int ncols) {
-    const size_t s = dtype ? dense_smem<double>(ncols, true) : dense_smem<float>(ncols, true);
-    return s <= (size_t)max_smem_per_block() / 2;   // leave room for two blocks per SM
-}
-
 int dense_bitmap_max_cols() {
-    const size_t avail = (size_t)max_smem_per_block() - num_scratch_bytes<double, 1024>() - 64;
-    return (int)((avail / 8) * 32);
+    const size_t avail = (size_t)max_smem_per_block() - prod_scratch_bytes<float, 1024>() - 64;
+    return (int)((avail / 4) * 32);
 }
 
-int num_dense_grid(int dtype, const HashLaunch &hl, int ncols) {
-    (void)ncols;
-    (void)dtype;
-    const int per = hl.blocks_per_sm > 0 ? hl.blocks_per_sm : 1;
-    return hl.sms * per;
+static int window_threads(int blocks_per_sm) { return blocks_per_sm <= 1 ? 1024 : blocks_per_sm == 2 ? 512 : 256; }
+
+template <typename V, int NT>
+static size_t window_smem(int cpc) {
+    return (size_t)cpc * sizeof(V) + (size_t)(cpc / 32) * 4 + num_scratch_bytes<V, NT>();
 }
 
 template <typename V>
-static size_t dense_cluster_smem(int cpc, int H) {
-    size_t b = (size_t)cpc * sizeof(V) + (size_t)32 * H * sizeof(V) + (size_t)(cpc / 32) * 8 +
-               num_scratch_bytes<V, 1024>();
-    if (H > 0) b += (size_t)(cpc / 32) * 8 + (size_t)H * 4;
-    return b;
+static size_t window_smem_nt(int cpc, int nt) {
+    return nt == 1024 ? window_smem<V, 1024>(cpc) : nt == 512 ? window_smem<V, 512>(cpc) : window_smem<V, 256>(cpc);
 }
 
-// Widest window (multiple of 32 columns) one 1024-thread block can accumulate.
-int num_dense_cap(int dtype, int H) {
-    int lo = 0, hi = 1 << 22;
-    while (hi - lo > 32) {
-        const int mid = ((lo + hi) / 2) & ~31;
-        const size_t need = dtype ? dense_cluster_smem<double>(mid, H) : dense_cluster_smem<float>(mid, H);
-        if (need <= (size_t)max_smem_per_block()) lo = mid;
-        else hi = mid;
+int num_window_cols(int dtype, int blocks_per_sm) {
+    const int bps = blocks_per_sm < 1 ? 1 : blocks_per_sm;
+    const int nt = window_threads(bps);
+    // per-block budget: the SM's shared memory shared by bps blocks (1 KB
+    // reserved per block, ~1 KB of static shared variables)
+    long long budget = (long long)max_smem_per_sm() / bps - 1024 - 1024;
+    if (budget > max_smem_per_block() - 1024) budget = max_smem_per_block() - 1024;
+    int best = 0;
+    for (int cpc = kSubCols; cpc <= kMaxWinCols; cpc += kSubCols) {
+        const size_t need = dtype ? window_smem_nt<double>(cpc, nt) : window_smem_nt<float>(cpc, nt);
+        if ((long long)need <= budget) best = cpc;
     }
-    return lo;
+    return best;
 }
 
-// Smallest cluster whose blocks together cover all columns (0: none up to 8).
-int num_dense_cluster_size(int dtype, int ncols, int cluster_max, int H) {
-    const long long cap = num_dense_cap(dtype, H);
-    for (int cs = 1; cs <= 8 && cs <= cluster_max; cs <<= 1)
-        if (cap * cs >= ncols) return cs;
-    return 0;
-}
-
-template <typename V, int CS>
-static void dense_cluster_go(Operands<V> op, const BSlices &sl, int cpc, const int *rows, int count, int *token,
-                             const NumOutT<V> &out, int *err, cudaStream_t s) {
-    const int H = sl.hot_n ? sl.hot_h : 0;
-    const size_t smem = dense_cluster_smem<V>(cpc, H);
-    if (CS > 1 && sl.woff) {
+template <typename V, int NT>
+static void num_window_go(Operands<V> op, const BSlices &sl, const int *rows, int count, unsigned long long *token,
+                          const HashLaunch &hl, const WinCount &wc, const NumOutT<V> &out, int *err,
+                          cudaStream_t s) {
+    int cpc = sl.cpc;
+    int subs = cpc / kSubCols;
+    if (sl.nslices <= 1) {
+        cpc = (op.ncols + 31) & ~31;   // one window holds every column
+        subs = wc.nsub;
+    } else {
         op.b_ci = sl.ci;
         op.b_val = (const V *)sl.val;
         op.b_woff = sl.woff;
-        op.nslices = CS;
+        op.nslices = sl.nslices;
     }
-    auto kern = k_num_dense_cluster<V, CS>;
+    const size_t smem = window_smem<V, NT>(cpc);
+    auto kern = k_num_window<V, NT>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(CS, 1, 1);
-    cfg.blockDim = dim3(1024, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
-        cudaGetLastError();
-        nclusters = 1;
-    }
-    if (nclusters > count) nclusters = count;
-    kern<<<nclusters * CS, 1024, smem, s>>>(op, rows, count, token, cpc, sl.splits, out, sl.hot_bm, sl.hot_col,
-                                            sl.hot_n, H, err);
+    const int nw = sl.nslices <= 1 ? 1 : sl.nslices;
+    const long long items = (long long)count * nw;
+    const int grid = resident_grid(kern, NT, smem, hl.sms, items);
+    kern<<<grid, NT, smem, s>>>(op, rows, count, nw, cpc, subs, wc, out, token, err);
 }
 
 template <typename V>
-static void num_dense_typed(const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
-                            void *acc, const BSlices &sl, const NumOut &o, int *err, cudaStream_t s) {
+static void num_window_typed(const RawOperands &r, const int *rows, int count, unsigned long long *token,
+                             const HashLaunch &hl,
+                             const BSlices &sl, const WinCount &wc, const NumOut &o, int *err, cudaStream_t s) {
     const Operands<V> op = num_operands<V>(r);
     const NumOutT<V> out = num_out<V>(o);
-    const int words = (r.ncols + 31) / 32;
-    const int cs = sl.splits ? sl.nslices : 0;
-    if (cs > 0) {
-        switch (cs) {
-            case 1: dense_cluster_go<V, 1>(op, sl, sl.cpc, rows, count, token, out, err, s); break;
-            case 2: dense_cluster_go<V, 2>(op, sl, sl.cpc, rows, count, token, out, err, s); break;
-            case 4: dense_cluster_go<V, 4>(op, sl, sl.cpc, rows, count, token, out, err, s); break;
-            default: dense_cluster_go<V, 8>(op, sl, sl.cpc, rows, count, token, out, err, s); break;
-        }
-    } else {
-        const size_t smem = dense_smem<V>(r.ncols, false);
-        auto kern = k_num_dense<V, 1024, false>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int grid = num_dense_grid(sizeof(V) == 8, hl, r.ncols);
-        if (grid > count) grid = count;
-        kern<<<grid, 1024, smem, s>>>(op, rows, count, token, words, (V *)acc, out, err);
+    switch (window_threads(hl.dense_blocks)) {
+        case 1024: num_window_go<V, 1024>(op, sl, rows, count, token, hl, wc, out, err, s); break;
+        case 512: num_window_go<V, 512>(op, sl, rows, count, token, hl, wc, out, err, s); break;
+        default: num_window_go<V, 256>(op, sl, rows, count, token, hl, wc, out, err, s); break;
     }
 }
 
-void launch_num_dense(int dtype, const RawOperands &r, const int *rows, int count, int *token,
-                      const HashLaunch &hl, void *acc, const BSlices &sl, const NumOut &out, int *err,
-                      cudaStream_t s) {
+void launch_num_window(int dtype, const RawOperands &r, const int *rows, int count, unsigned long long *token,
+                       const HashLaunch &hl, const BSlices &sl, const WinCount &wc, const NumOut &out, int *err,
+                       cudaStream_t s) {
     if (count <= 0) return;
-    if (dtype) num_dense_typed<double>(r, rows, count, token, hl, acc, sl, out, err, s);
-    else num_dense_typed<float>(r, rows, count, token, hl, acc, sl, out, err, s);
+    cudaMemsetAsync(token, 0, sizeof(unsigned long long), s);
+    if (dtype) num_window_typed<double>(r, rows, count, token, hl, sl, wc, out, err, s);
+    else num_window_typed<float>(r, rows, count, token, hl, sl, wc, out, err, s);
 }
 
 int num_spill_grid(int dtype, const HashLaunch &hl) {

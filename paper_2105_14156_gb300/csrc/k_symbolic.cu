@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(NT) k_sym_hash(Operands<float> op, const int *
         int64_t ab, ae;
         a_row_range(op, i, ab, ae, err);
         int cnt = 0;
-        row_products<float, false, GS, NT>(op, ab, ae, sc, err, [&](int j, float, int64_t) {
+        row_products<float, false, GS, NT>(op, ab, ae, sc, err, [&](int j, float, float) {
             bool ins;
             if (hash_find_or_insert<false>(keys, tbits, hc, j, ins) < 0) raise_err(err, kErrTableFull);
             cnt += ins ? 1 : 0;
@@ -59,27 +59,55 @@ __global__ void __launch_bounds__(NT) k_sym_hash(Operands<float> op, const int *
     }
 }
 
-// Dense rows: a bitmap over the columns of B; count = popcount.
+// Size check of the numeric count pass (see NumCheck).
+__device__ __forceinline__ void count_check(const NumCheck &nc, int i, int tot, int *err) {
+    const int64_t s = nc.c_rp[i], t = nc.c_rp[i + 1];
+    if (s < 0 || t < s || t > nc.c_nnz) {
+        raise_err(err, kErrBadRowPtr);
+        if (nc.row_nnz) nc.row_nnz[i] = -1;
+        return;
+    }
+    if (nc.row_nnz) nc.row_nnz[i] = (int64_t)tot <= t - s ? tot : -1;
+    else if ((int64_t)tot != t - s) raise_err(err, kErrCountMismatch);
+}
+
+// Dense rows: a bitmap over the columns of B; count = popcount. With wc.wcnt
+// the row's distinct columns are also counted per block of kSubCols columns
+// (slot = wc.slot_base + r), for the numeric dense kernel.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_sym_dense(Operands<float> op, const int *rows, int count, int *token,
-                                                  int words, int *nnz_out, int *err) {
+                                                  int words, WinCount wc, int *nnz_out, NumCheck nc, int *err) {
     using G = Group<NT, NT>;
+    constexpr int kWarps = NT / 32;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_row;
     unsigned *bm = (unsigned *)smem;
     const ProdScratch<float> sc = carve_prod_scratch<float, NT>(smem + (size_t)words * 4);
     const int t = threadIdx.x;
+    const int lane = lane_id();
+    const int wp = t >> 5;
     for (;;) {
         if (t == 0) s_row = atomicAdd(token, 1);
         __syncthreads();
         const int r = s_row;
         if (r >= count) break;
         const int i = rows[r];
+        int64_t slot = -1;
+        if (wc.wcnt && wc.skip_slotted) slot = wc.wslot[i];
+        if (slot >= 0) {
+            // counted before: only the size check
+            int c = 0;
+            for (int q = t; q < wc.nsub; q += NT) c += wc.wcnt[slot * wc.nsub + q];
+            const int tot = G::template sum<int>(c, sc.red);
+            if (t == 0) count_check(nc, i, tot, err);
+            __syncthreads();
+            continue;
+        }
         for (int w = t; w < words; w += NT) bm[w] = 0u;
         __syncthreads();
         int64_t ab, ae;
         a_row_range(op, i, ab, ae, err);
-        row_products<float, false, NT, NT>(op, ab, ae, sc, err, [&](int j, float, int64_t) {
+        row_products<float, false, NT, NT>(op, ab, ae, sc, err, [&](int j, float, float) {
             const unsigned bit = 1u << (j & 31);
             unsigned *w = bm + (j >> 5);
             if (!(*(volatile unsigned *)w & bit)) atomicOr(w, bit);
@@ -88,7 +116,22 @@ __global__ void __launch_bounds__(NT) k_sym_dense(Operands<float> op, const int 
         int cnt = 0;
         for (int w = t; w < words; w += NT) cnt += __popc(bm[w]);
         const int tot = G::template sum<int>(cnt, sc.red);
-        if (t == 0) nnz_out[i] = tot;
+        if (wc.wcnt) {
+            slot = wc.slot_base + r;
+            constexpr int kSubWords = kSubCols / 32;
+            for (int q = wp; q < wc.nsub; q += kWarps) {
+                const int w1 = min((q + 1) * kSubWords, words);
+                int c = 0;
+                for (int x = q * kSubWords + lane; x < w1; x += 32) c += __popc(bm[x]);
+                c = warp_sum(c);
+                if (lane == 0) wc.wcnt[slot * wc.nsub + q] = (uint16_t)c;
+            }
+            if (t == 0) wc.wslot[i] = (int)slot;
+        }
+        if (t == 0) {
+            if (nnz_out) nnz_out[i] = tot;
+            else count_check(nc, i, tot, err);
+        }
         __syncthreads();
     }
 }
@@ -121,7 +164,7 @@ __global__ void __launch_bounds__(NT) k_sym_spill(Operands<float> op, const int 
         int64_t ab, ae;
         a_row_range(op, i, ab, ae, err);
         int cnt = 0;
-        row_products<float, false, NT, NT>(op, ab, ae, sc, err, [&](int j, float, int64_t) {
+        row_products<float, false, NT, NT>(op, ab, ae, sc, err, [&](int j, float, float) {
             bool ins;
             if (hash_find_or_insert<true>(keys, tb, hc, j, ins) < 0) raise_err(err, kErrTableFull);
             cnt += ins ? 1 : 0;
@@ -195,15 +238,15 @@ void launch_sym_hash(const RawOperands &r, const int *rows, int count, int *toke
 }
 
 void launch_sym_dense(const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
-                      int *nnz_out, int *err, cudaStream_t s) {
+                      const WinCount &wc, int *nnz_out, const NumCheck &nc, int *err, cudaStream_t s) {
     if (count <= 0) return;
     const Operands<float> op = sym_operands(r);
     const int words = (r.ncols + 31) / 32;
     const size_t smem = (size_t)words * 4 + prod_scratch_bytes<float, 1024>();
     auto kern = k_sym_dense<1024>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int grid = resident_grid(kern, 1024, smem, hl.sms, count, hl.blocks_per_sm > 0 ? hl.blocks_per_sm : 2);
-    kern<<<grid, 1024, smem, s>>>(op, rows, count, token, words, nnz_out, err);
+    const int grid = resident_grid(kern, 1024, smem, hl.sms, count, 2);
+    kern<<<grid, 1024, smem, s>>>(op, rows, count, token, words, wc, nnz_out, nc, err);
 }
 
 int sym_spill_grid(const HashLaunch &hl) {

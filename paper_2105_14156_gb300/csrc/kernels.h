@@ -83,15 +83,37 @@ struct HashLaunch {
     int hash_kind;
     int colbits;
     int sms;
-    int blocks_per_sm;  // for dense / spill kernels
-    int cluster_max;    // largest cluster for dense rows
+    int blocks_per_sm;  // for the spill kernels
+    int dense_blocks;   // resident blocks per SM of the dense kernels
+};
+
+// Distinct columns of the dense rows, counted per block of kSubCols columns
+// (the numeric dense kernel places each column window's outputs with them).
+// wslot[i]: slot of row i (-1: not counted); wcnt[slot][nsub]: the counts.
+constexpr int kSubCols = 4096;
+struct WinCount {
+    int *wslot = nullptr;
+    uint16_t *wcnt = nullptr;
+    int nsub = 0;
+    int64_t slot_base = 0;   // slot of the r-th listed row = slot_base + r
+    int skip_slotted = 0;    // rows that already have a slot are not counted again
+};
+// Size check of a numeric count pass: exact (row length of c_rp must equal
+// the count) or capacity mode (row_nnz[i] = count, or -1 when it exceeds the
+// row's capacity).
+struct NumCheck {
+    const int64_t *c_rp = nullptr;
+    int64_t c_nnz = 0;
+    int *row_nnz = nullptr;
 };
 
 // k_symbolic.cu
 void launch_sym_hash(const RawOperands &op, const int *rows, int count, int *token, const HashLaunch &hl,
                      int *nnz_out, int *err, cudaStream_t s);
+// Dense rows: bitmap over all columns of B. Symbolic use: nnz_out != nullptr.
+// Numeric count pass: nnz_out == nullptr, sizes checked by nc.
 void launch_sym_dense(const RawOperands &op, const int *rows, int count, int *token, const HashLaunch &hl,
-                      int *nnz_out, int *err, cudaStream_t s);
+                      const WinCount &wc, int *nnz_out, const NumCheck &nc, int *err, cudaStream_t s);
 int sym_spill_grid(const HashLaunch &hl);
 void launch_sym_spill(const RawOperands &op, const int *rows, int count, int *token, const HashLaunch &hl,
                       float inv_load, const long long *bound, int spill_tbits, int *tables, int *nnz_out,
@@ -108,32 +130,27 @@ struct NumOut {
 void launch_num_hash(int dtype, const RawOperands &op, const int *rows, int count, int *token,
                      const HashLaunch &hl, float inv_load, int bitmap_ratio, const NumOut &out, int *err,
                      cudaStream_t s);
-int num_dense_grid(int dtype, const HashLaunch &hl, int ncols);
-bool num_dense_uses_smem_acc(int dtype, int ncols);
-int num_dense_cluster_size(int dtype, int ncols, int cluster_max, int H);  // 0: none fits
-int num_dense_cap(int dtype, int H);  // widest column window of one block
-// Plan of the dense cluster kernel (k_split.cu): window split points
-// splits[ns+1] on the device; slices of B (woff[B.rows][ns+1], regrouped
-// col/val copies; ns > 1 only); hot columns per window: hot_bm[ns][cpc/32],
-// hot_col[ns][hot_h], hot_n[ns].
+// Column windows of the dense rows (k_split.cu): slices of B regrouped by
+// window of cpc columns; woff[B.rows][nslices+1] (nslices > 1 only).
 struct BSlices {
     int nslices = 0;
     int cpc = 0;
-    const int *splits = nullptr;
     const int32_t *woff = nullptr;
     const int32_t *ci = nullptr;
     const void *val = nullptr;
-    const unsigned *hot_bm = nullptr;
-    const int *hot_col = nullptr;
-    const int *hot_n = nullptr;
-    int hot_h = 0;
 };
-size_t dense_plan_bytes(const RawOperands &op, int ns, int cpc, int H, size_t vsz);
-void launch_dense_plan(int dtype, const RawOperands &op, int ns, int cap, int cpc, int H, int hot_factor, void *ws,
-                       BSlices &sl, int sms, cudaStream_t s);
-void launch_num_dense(int dtype, const RawOperands &op, const int *rows, int count, int *token,
-                      const HashLaunch &hl, void *acc, const BSlices &sl, const NumOut &out, int *err,
-                      cudaStream_t s);
+size_t window_plan_bytes(const RawOperands &op, int nw, size_t vsz);
+void launch_window_plan(int dtype, const RawOperands &op, int nw, int cpc, void *ws, BSlices &sl, int sms,
+                        cudaStream_t s);
+// Widest column window (a multiple of kSubCols, at most kMaxWinCols) of the
+// numeric dense kernel at `blocks_per_sm` resident blocks per SM; 0: none.
+constexpr int kMaxWinCols = 65536;
+int num_window_cols(int dtype, int blocks_per_sm);
+// (row, window) work items of the dense rows; counts from wc; token: a
+// 64-bit item counter (zeroed here).
+void launch_num_window(int dtype, const RawOperands &op, const int *rows, int count, unsigned long long *token,
+                       const HashLaunch &hl, const BSlices &sl, const WinCount &wc, const NumOut &out, int *err,
+                       cudaStream_t s);
 int num_spill_grid(int dtype, const HashLaunch &hl);
 void launch_num_spill(int dtype, const RawOperands &op, const int *rows, int count, int *token,
                       const HashLaunch &hl, float inv_load, int spill_tbits, void *tables,
@@ -141,6 +158,7 @@ void launch_num_spill(int dtype, const RawOperands &op, const int *rows, int cou
 
 // Shared-memory limits used by the planner.
 int max_smem_per_block();
+int max_smem_per_sm();
 int dense_bitmap_max_cols();          // widest B whose column bitmap fits one block
 bool num_hash_bitmap_fits(int dtype, int tbits, int ncols);
 

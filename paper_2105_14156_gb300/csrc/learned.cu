@@ -351,6 +351,9 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
     }
     const RawOperands op = raw_ops(A, B);
     int *err = (int *)h->err.ptr;
+    // the dense rows of this call are counted by this call (no reuse of an
+    // earlier symbolic phase's counts)
+    h->wcache.valid = false;
     // per-row arrays
     size_t need = 0;
     carve_size<float>(need, (size_t)n * 6);

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kNaThreads) k_na_count(Operands<float> op, int
         for (int s = t; s < T; s += kNaThreads) __stcg(keys + s, kEmpty);
         __syncthreads();
         int cnt = 0;
-        group_products<float, false, kNaThreads, kNaThreads>(op, ab, ae, sc, err, [&](int j, float, int64_t) {
+        group_products<float, false, kNaThreads, kNaThreads>(op, ab, ae, sc, err, [&](int j, float, float) {
             bool ins;
             if (hash_find_or_insert<true>(keys, tb, hc, j, ins) < 0) raise_err(err, kErrTableFull);
             cnt += ins ? 1 : 0;

@@ -17,8 +17,7 @@ from tests.helpers import identity, random_csr
 pytestmark = pytest.mark.gpu
 
 DEFAULT = dict(hash_kind=1, max_load=0.5, sym_max_tbits=15, num_max_tbits=14, group_shift=3, dense_ratio=4,
-               bitmap_ratio=4, spill_blocks_per_sm=1, sym_dense_ratio=64, cluster_max=8, hot_cols=128,
-               hot_factor=16)
+               bitmap_ratio=4, spill_blocks_per_sm=1, sym_dense_ratio=64, dense_blocks=1)
 
 # Parameter sets that force each path.
 PATHS = {
@@ -26,10 +25,10 @@ PATHS = {
     "warp_only_small_tables": dict(sym_max_tbits=7, num_max_tbits=7, dense_ratio=0, sym_dense_ratio=0),
     "spill_everything": dict(sym_max_tbits=5, num_max_tbits=5, dense_ratio=0, sym_dense_ratio=0),
     "dense_everything": dict(dense_ratio=1 << 20, sym_dense_ratio=1 << 20),
-    "dense_single_block": dict(dense_ratio=1 << 20, cluster_max=1, num_max_tbits=5),
+    "dense_four_blocks_per_sm": dict(dense_ratio=1 << 20, dense_blocks=4, num_max_tbits=5),
     "no_symbolic_dense": dict(sym_dense_ratio=0),
-    "dense_no_hot_columns": dict(dense_ratio=1 << 20, hot_cols=0),
-    "dense_all_hot_columns": dict(dense_ratio=1 << 20, hot_cols=512, hot_factor=1),
+    "dense_counted_in_numeric": dict(dense_ratio=1 << 20, sym_dense_ratio=0),
+    "dense_two_blocks_per_sm": dict(dense_ratio=1 << 20, dense_blocks=2),
     "group_per_row": dict(group_shift=0),
     "bitonic_only": dict(bitmap_ratio=0),
     "bitmap_always": dict(bitmap_ratio=1 << 20),
@@ -149,16 +148,34 @@ def test_congruent_columns_defeat_low_bits(handle):
         assert_matches_oracle(C, A, B)
 
 
-@pytest.mark.parametrize("ncols,cluster_max", [(20000, 8), (40000, 8), (80000, 8), (110000, 8), (110000, 1),
-                                               (40000, 2)])
-def test_dense_rows_cluster_sizes(handle, ncols, cluster_max):
-    """Dense rows whose accumulator needs 1, 2, 4 or 8 blocks of a cluster (or,
-    with clusters disabled, the global-memory accumulator)."""
-    A = random_csr(96, 64, 0.3, 51, values="f64")
-    B = random_csr(64, ncols, 800.0 / ncols, 52, values="f64")
-    for hot in (0, 128, 512):
-        C = run(handle, A, B, dense_ratio=1 << 20, cluster_max=cluster_max, hot_cols=hot, hot_factor=1)
-        assert_matches_oracle(C, A, B)
+@pytest.mark.parametrize("ncols,dense_blocks", [(3000, 1), (20000, 1), (40000, 1), (110000, 1), (110000, 4),
+                                                (40000, 2), (70001, 4)])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_dense_rows_windows(handle, ncols, dense_blocks, dtype):
+    """Dense rows split into one or many column windows (the last one ragged),
+    at 1, 2 or 4 blocks per SM (wider or narrower windows)."""
+    A = random_csr(96, 64, 0.3, 51, values=dtype)
+    B = random_csr(64, ncols, 800.0 / ncols, 52, values=dtype)
+    C = run(handle, A, B, dense_ratio=1 << 20, dense_blocks=dense_blocks)
+    assert_matches_oracle(C, A, B)
+
+
+def test_dense_counts_of_other_operands_not_reused(handle):
+    """The numeric phase reuses the symbolic phase's dense-row counts only for
+    the operands they were made for: symbolic(A1, B1), symbolic(A2, B2), then
+    numeric(A1, B1) counts A1*B1's dense rows itself."""
+    from paper_2105_14156_gb300 import smash
+    handle.set_params(**dict(DEFAULT, dense_ratio=1 << 20))
+    A1 = random_csr(80, 64, 0.3, 61, values="f64")
+    B1 = random_csr(64, 9000, 0.05, 62, values="f64")
+    A2 = random_csr(70, 64, 0.4, 63, values="f64")
+    B2 = random_csr(64, 9000, 0.07, 64, values="f64")
+    d = [smash.to_device(M) for M in (A1, B1, A2, B2)]
+    c_rp1, nnz1 = handle.symbolic(d[0], d[1])
+    handle.symbolic(d[2], d[3])
+    C1 = handle.numeric(d[0], d[1], c_rp1, nnz1)
+    handle.check()
+    assert_matches_oracle(C1.to_host(), A1, B1)
 
 
 def test_identity(handle):
