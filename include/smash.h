@@ -80,8 +80,11 @@ typedef struct {
                                 counts its columns in a shared-memory bitmap; 0 disables; default 64 */
     int32_t dense_blocks;    /* dense rows: resident blocks per SM of the numeric dense kernel (1, 2 or 4);
                                 each owns one column window of a row (the widest that fits its share of
-                                shared memory); default 1 */
-    int32_t reserved[6];
+                                shared memory); 0 (default): 2 for float64, 4 for float32 */
+    int32_t sym_dense_blocks; /* symbolic dense rows: resident blocks per SM of the bitmap kernel (1, 2, 4
+                                 or 8; fewer when their bitmaps do not fit); 0 (default): the most resident
+                                 threads, then the most blocks */
+    int32_t reserved[5];
 } smash_params;
 
 /* Per-call statistics (the last symbolic or numeric call of the handle). */

@@ -19,7 +19,8 @@ int smash_default_params(smash_params *p) {
     p->bitmap_ratio = 4;
     p->spill_blocks_per_sm = 1;
     p->sym_dense_ratio = 64;
-    p->dense_blocks = 1;
+    p->dense_blocks = 0;
+    p->sym_dense_blocks = 0;
     return SMASH_OK;
 }
 
@@ -267,9 +268,10 @@ int run_symbolic(smash_handle *h, const RawOperands &op, int64_t n, Plan &pl, in
             wc.wcnt = (uint16_t *)h->wcnt.ptr;
             wc.nsub = nsub;
             {
-                LaunchTimer lt(h, s, "sym_dense", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
-                launch_sym_dense(op, rows, counts[b], tok, hash_launch(h, 0, op.ncols), wc, nnz_out, NumCheck{}, err,
-                                 s);
+                const HashLaunch hl = hash_launch(h, 0, op.ncols);
+                LaunchTimer lt(h, s, "sym_dense", b, sym_dense_threads(hl, op.ncols), counts[b], sums[b], sums[16 + b],
+                               sums[32 + b]);
+                launch_sym_dense(op, rows, counts[b], tok, hl, wc, nnz_out, NumCheck{}, err, s);
             }
             wcache_set(h, op, nsub, counts[b]);
         } else if (b == kBinSpill) {
@@ -314,7 +316,8 @@ int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const
         const int *rows = pl.bb.rows + offsets[b];
         int *tok = pl.bb.tokens + b;
         if (b == kBinDense) {
-            const HashLaunch hl = hash_launch(h, 0, op.ncols);
+            HashLaunch hl = hash_launch(h, 0, op.ncols);
+            hl.dense_blocks = dense_blocks_of(h, dt);
             // 1. per-block column counts of the dense rows: from the symbolic
             //    phase of the same operands, else counted here (and sizes checked)
             const int nsub = (int)((op.ncols + kSubCols - 1) / kSubCols);
@@ -339,12 +342,13 @@ int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const
             nc.c_nnz = out.c_nnz;
             nc.row_nnz = out.row_nnz;
             {
-                LaunchTimer lt(h, s, "num_dense_count", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
+                LaunchTimer lt(h, s, "num_dense_count", b, sym_dense_threads(hl, op.ncols), counts[b], sums[b],
+                               sums[16 + b], sums[32 + b]);
                 launch_sym_dense(op, rows, counts[b], tok, hl, wc, nullptr, nc, err, s);
             }
             h->wcache.slots = base + counts[b];
             // 2. column windows: slices of B
-            const int cpc = num_window_cols(dt, h->params.dense_blocks);
+            const int cpc = num_window_cols(dt, hl.dense_blocks);
             const int nw = (int)((op.ncols + cpc - 1) / cpc);
             if ((st = ensure(h, h->split, 256 + window_plan_bytes(op, nw, vsz), s))) return st;
             BSlices sl;
@@ -353,7 +357,7 @@ int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const
                 launch_window_plan(dt, op, nw, cpc, (char *)h->split.ptr + 256, sl, h->sms, s);
             }
             // 3. (row, window) items
-            LaunchTimer lt(h, s, "num_dense_window", b, 1024 / h->params.dense_blocks, counts[b],
+            LaunchTimer lt(h, s, "num_dense_window", b, 1024 / hl.dense_blocks, counts[b],
                            sums[b], sums[16 + b], sums[32 + b]);
             launch_num_window(dt, op, rows, counts[b], (unsigned long long *)h->split.ptr, hl, sl, wc, out, err, s);
         } else if (b == kBinSpill) {

@@ -275,7 +275,11 @@ inline int check_params(const smash_params *p) {
     if (p->dense_ratio < 0 || p->bitmap_ratio < 0) return SMASH_ERR_INVALID_ARG;
     if (p->spill_blocks_per_sm < 0 || p->spill_blocks_per_sm > 8) return SMASH_ERR_INVALID_ARG;
     if (p->sym_dense_ratio < 0) return SMASH_ERR_INVALID_ARG;
-    if (p->dense_blocks != 1 && p->dense_blocks != 2 && p->dense_blocks != 4) return SMASH_ERR_INVALID_ARG;
+    if (p->dense_blocks != 0 && p->dense_blocks != 1 && p->dense_blocks != 2 && p->dense_blocks != 4)
+        return SMASH_ERR_INVALID_ARG;
+    if (p->sym_dense_blocks != 0 && p->sym_dense_blocks != 1 && p->sym_dense_blocks != 2 &&
+        p->sym_dense_blocks != 4 && p->sym_dense_blocks != 8)
+        return SMASH_ERR_INVALID_ARG;
     return SMASH_OK;
 }
 
@@ -408,6 +412,12 @@ inline int last_cuda_status() {
     return e == cudaSuccess ? SMASH_OK : SMASH_ERR_CUDA;
 }
 
+// Resident blocks per SM of the numeric dense kernel.
+inline int dense_blocks_of(const smash_handle *h, int dtype) {
+    const int b = h->params.dense_blocks;
+    return b > 0 ? b : (dtype ? 2 : 4);
+}
+
 inline BinRule sym_rule(const smash_handle *h, int64_t ncols) {
     BinRule r;
     r.inv_load = 1.0f / h->params.max_load;
@@ -426,7 +436,7 @@ inline BinRule num_rule(const smash_handle *h, int64_t ncols, int dtype) {
     r.inv_load = 1.0f / h->params.max_load;
     // dense rows need their columns counted in one bitmap (count pass) and a
     // column window that fits shared memory
-    const bool dense_fits = ncols <= dense_bitmap_max_cols() && num_window_cols(dtype, h->params.dense_blocks) > 0;
+    const bool dense_fits = ncols <= dense_bitmap_max_cols() && num_window_cols(dtype, dense_blocks_of(h, dtype)) > 0;
     r.dense_ok = (h->params.dense_ratio > 0 && dense_fits) ? 1 : 0;
     r.dense_min = r.dense_ok ? (ncols + h->params.dense_ratio - 1) / h->params.dense_ratio : (1ll << 62);
     if (r.dense_min < 1) r.dense_min = 1;
@@ -459,7 +469,8 @@ inline HashLaunch hash_launch(const smash_handle *h, int tbits, int64_t ncols) {
     hl.colbits = colbits_of(ncols);
     hl.sms = h->sms;
     hl.blocks_per_sm = h->params.spill_blocks_per_sm > 0 ? h->params.spill_blocks_per_sm : 1;
-    hl.dense_blocks = h->params.dense_blocks;
+    hl.dense_blocks = h->params.dense_blocks > 0 ? h->params.dense_blocks : 2;
+    hl.sym_dense_blocks = h->params.sym_dense_blocks;
     return hl;
 }
 

@@ -237,16 +237,68 @@ void launch_sym_hash(const RawOperands &r, const int *rows, int count, int *toke
     }
 }
 
+// Block size and blocks per SM of the bitmap kernel: as many resident
+// threads as the bitmaps allow, then as many rows in flight as possible (or
+// the requested blocks per SM).
+static void sym_dense_shape(const HashLaunch &hl, int64_t ncols, int &nt, int &per_sm) {
+    const size_t words = (size_t)((ncols + 31) / 32);
+    const int sm_smem = max_smem_per_sm();
+    const int nts[3] = {1024, 512, 256};
+    const size_t scr[3] = {prod_scratch_bytes<float, 1024>(), prod_scratch_bytes<float, 512>(),
+                           prod_scratch_bytes<float, 256>()};
+    int best_nt = 1024, best_b = 1, best_thr = 0;
+    for (int q = 0; q < 3; ++q) {
+        if (best_thr == (1 << 30)) break;
+        const size_t per_block = words * 4 + scr[q] + 1024;
+        if (per_block > (size_t)max_smem_per_block() + 1024) continue;
+        int b = (int)((size_t)sm_smem / per_block);
+        if (b > 2048 / nts[q]) b = 2048 / nts[q];
+        if (b < 1) continue;
+        if (hl.sym_dense_blocks > 0) {
+            if (b >= hl.sym_dense_blocks && nts[q] * hl.sym_dense_blocks <= 2048) {
+                best_nt = nts[q];
+                best_b = hl.sym_dense_blocks;
+                best_thr = 1 << 30;
+            }
+            continue;
+        }
+        if (b * nts[q] > best_thr || (b * nts[q] == best_thr && b > best_b)) {
+            best_thr = b * nts[q];
+            best_nt = nts[q];
+            best_b = b;
+        }
+    }
+    nt = best_nt;
+    per_sm = best_b;
+}
+
+int sym_dense_threads(const HashLaunch &hl, int64_t ncols) {
+    int nt, b;
+    sym_dense_shape(hl, ncols, nt, b);
+    return nt;
+}
+
+template <int NT>
+static void sym_dense_go(const Operands<float> &op, const int *rows, int count, int *token, int per_sm,
+                         const HashLaunch &hl, const WinCount &wc, int *nnz_out, const NumCheck &nc, int *err,
+                         cudaStream_t s) {
+    const int words = (op.ncols + 31) / 32;
+    const size_t smem = (size_t)words * 4 + prod_scratch_bytes<float, NT>();
+    auto kern = k_sym_dense<NT>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = resident_grid(kern, NT, smem, hl.sms, count, per_sm);
+    kern<<<grid, NT, smem, s>>>(op, rows, count, token, words, wc, nnz_out, nc, err);
+}
+
 void launch_sym_dense(const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
                       const WinCount &wc, int *nnz_out, const NumCheck &nc, int *err, cudaStream_t s) {
     if (count <= 0) return;
     const Operands<float> op = sym_operands(r);
-    const int words = (r.ncols + 31) / 32;
-    const size_t smem = (size_t)words * 4 + prod_scratch_bytes<float, 1024>();
-    auto kern = k_sym_dense<1024>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int grid = resident_grid(kern, 1024, smem, hl.sms, count, 2);
-    kern<<<grid, 1024, smem, s>>>(op, rows, count, token, words, wc, nnz_out, nc, err);
+    int nt, per_sm;
+    sym_dense_shape(hl, r.ncols, nt, per_sm);
+    if (nt == 256) sym_dense_go<256>(op, rows, count, token, per_sm, hl, wc, nnz_out, nc, err, s);
+    else if (nt == 512) sym_dense_go<512>(op, rows, count, token, per_sm, hl, wc, nnz_out, nc, err, s);
+    else sym_dense_go<1024>(op, rows, count, token, per_sm, hl, wc, nnz_out, nc, err, s);
 }
 
 int sym_spill_grid(const HashLaunch &hl) {

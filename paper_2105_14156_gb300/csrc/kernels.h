@@ -84,7 +84,8 @@ struct HashLaunch {
     int colbits;
     int sms;
     int blocks_per_sm;  // for the spill kernels
-    int dense_blocks;   // resident blocks per SM of the dense kernels
+    int dense_blocks;   // resident blocks per SM of the numeric dense kernel
+    int sym_dense_blocks;  // of the bitmap (symbolic dense) kernel; 0: automatic
 };
 
 // Distinct columns of the dense rows, counted per block of kSubCols columns
@@ -114,6 +115,7 @@ void launch_sym_hash(const RawOperands &op, const int *rows, int count, int *tok
 // Numeric count pass: nnz_out == nullptr, sizes checked by nc.
 void launch_sym_dense(const RawOperands &op, const int *rows, int count, int *token, const HashLaunch &hl,
                       const WinCount &wc, int *nnz_out, const NumCheck &nc, int *err, cudaStream_t s);
+int sym_dense_threads(const HashLaunch &hl, int64_t ncols);   // block size launch_sym_dense picks
 int sym_spill_grid(const HashLaunch &hl);
 void launch_sym_spill(const RawOperands &op, const int *rows, int count, int *token, const HashLaunch &hl,
                       float inv_load, const long long *bound, int spill_tbits, int *tables, int *nnz_out,

@@ -86,7 +86,8 @@ class Params(ctypes.Structure):
                 ("num_max_tbits", ctypes.c_int32), ("group_shift", ctypes.c_int32),
                 ("dense_ratio", ctypes.c_int32), ("bitmap_ratio", ctypes.c_int32),
                 ("spill_blocks_per_sm", ctypes.c_int32), ("sym_dense_ratio", ctypes.c_int32),
-                ("dense_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("dense_blocks", ctypes.c_int32), ("sym_dense_blocks", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

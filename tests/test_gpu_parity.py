@@ -17,7 +17,8 @@ from tests.helpers import identity, random_csr
 pytestmark = pytest.mark.gpu
 
 DEFAULT = dict(hash_kind=1, max_load=0.5, sym_max_tbits=15, num_max_tbits=14, group_shift=3, dense_ratio=4,
-               bitmap_ratio=4, spill_blocks_per_sm=1, sym_dense_ratio=64, dense_blocks=1)
+               bitmap_ratio=4, spill_blocks_per_sm=1, sym_dense_ratio=64, dense_blocks=0,
+               sym_dense_blocks=0)
 
 # Parameter sets that force each path.
 PATHS = {
@@ -29,6 +30,9 @@ PATHS = {
     "no_symbolic_dense": dict(sym_dense_ratio=0),
     "dense_counted_in_numeric": dict(dense_ratio=1 << 20, sym_dense_ratio=0),
     "dense_two_blocks_per_sm": dict(dense_ratio=1 << 20, dense_blocks=2),
+    "dense_one_block_per_sm": dict(dense_ratio=1 << 20, dense_blocks=1),
+    "symbolic_dense_one_block_per_sm": dict(sym_dense_ratio=1 << 20, sym_dense_blocks=1),
+    "symbolic_dense_eight_blocks_per_sm": dict(sym_dense_ratio=1 << 20, sym_dense_blocks=8),
     "group_per_row": dict(group_shift=0),
     "bitonic_only": dict(bitmap_ratio=0),
     "bitmap_always": dict(bitmap_ratio=1 << 20),
