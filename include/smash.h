@@ -70,7 +70,7 @@ typedef struct {
     float max_load;         /* table sized to next_pow2(bound / max_load) slots; (0.05, 0.95]; default 0.5 */
     int32_t sym_max_tbits;  /* largest shared-memory symbolic table, log2 slots; [5, 15]; default 15 */
     int32_t num_max_tbits;  /* largest shared-memory numeric table, log2 slots; [5, 14]; default 14 */
-    int32_t group_shift;    /* threads per row = clamp(T >> group_shift, 32, 1024); [0, 10]; default 3 */
+    int32_t group_shift;    /* threads per row = clamp(T >> group_shift, 32, 1024); [0, 10]; default 4 */
     int32_t dense_ratio;    /* a row whose bound b satisfies b * dense_ratio >= cols(B) uses the dense
                                accumulator (the paper's "dense row"); 0 disables; default 4 */
     int32_t bitmap_ratio;   /* numeric write-out ranks by a column bitmap when cols(B)/32 <=

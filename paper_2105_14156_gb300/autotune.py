@@ -15,7 +15,7 @@ import json
 import os
 
 SPACE = [
-    ("group_shift", [2, 3, 4]),
+    ("group_shift", [3, 4, 5]),
     ("max_load", [0.5, 0.7]),
     ("dense_ratio", [2, 4, 8, 16]),
     ("sym_dense_ratio", [16, 64, 256]),

@@ -14,7 +14,7 @@ int smash_default_params(smash_params *p) {
     p->max_load = 0.5f;
     p->sym_max_tbits = 15;
     p->num_max_tbits = 14;
-    p->group_shift = 3;
+    p->group_shift = 4;
     p->dense_ratio = 4;
     p->bitmap_ratio = 4;
     p->spill_blocks_per_sm = 1;
@@ -241,7 +241,7 @@ int run_symbolic(smash_handle *h, const RawOperands &op, int64_t n, Plan &pl, in
     h->wcache.valid = false;
     if (row_list && cudaMemsetAsync(pl.bb.bin, 0, (size_t)n, s) != cudaSuccess) return SMASH_ERR_CUDA;
     {
-        LaunchTimer lt(h, s, "sym_rowinfo", -1, 256, row_list ? list_n : n, op.a_nnz, 0, 0);
+        LaunchTimer lt(h, s, "sym_rowinfo", -1, 256, row_list ? list_n : n, op.a_nnz, 0, 0, 2);
         launch_sym_rowinfo(op, rule, pl.bb, pl.bound, nnz_out, err, h->sms, s, row_list, list_n);
     }
     {
@@ -299,7 +299,7 @@ int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const
     int *err = (int *)h->err.ptr;
     if (row_list && cudaMemsetAsync(pl.bb.bin, 0, (size_t)n, s) != cudaSuccess) return SMASH_ERR_CUDA;
     {
-        LaunchTimer lt(h, s, "num_rowinfo", -1, 256, row_list ? list_n : n, op.a_nnz, 0, out.c_nnz);
+        LaunchTimer lt(h, s, "num_rowinfo", -1, 256, row_list ? list_n : n, op.a_nnz, 0, out.c_nnz, 2);
         launch_num_rowinfo(op, out.c_rp, out.c_nnz, rule, pl.bb, err, h->sms, s, row_list, list_n);
     }
     {
@@ -315,7 +315,17 @@ int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const
         if (!counts[b]) continue;
         const int *rows = pl.bb.rows + offsets[b];
         int *tok = pl.bb.tokens + b;
+        // Dense rows take column windows when their products pay for slicing
+        // B (a pass over B's rows and entries); otherwise the global hash.
+        bool windows = false;
+        int cpc = 0, nw = 0;
         if (b == kBinDense) {
+            cpc = num_window_cols(dt, dense_blocks_of(h, dt));
+            nw = (int)((op.ncols + cpc - 1) / cpc);
+            const double plan = nw > 1 ? 4.0 * (double)op.b_rows * (nw + 1) + 2.0 * (4 + vsz) * (double)op.b_nnz : 0.0;
+            windows = 16.0 * (double)sums[16 + b] >= plan;
+        }
+        if (b == kBinDense && windows) {
             HashLaunch hl = hash_launch(h, 0, op.ncols);
             hl.dense_blocks = dense_blocks_of(h, dt);
             // 1. per-block column counts of the dense rows: from the symbolic
@@ -348,8 +358,6 @@ int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const
             }
             h->wcache.slots = base + counts[b];
             // 2. column windows: slices of B
-            const int cpc = num_window_cols(dt, hl.dense_blocks);
-            const int nw = (int)((op.ncols + cpc - 1) / cpc);
             if ((st = ensure(h, h->split, 256 + window_plan_bytes(op, nw, vsz), s))) return st;
             BSlices sl;
             {
@@ -360,7 +368,7 @@ int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const
             LaunchTimer lt(h, s, "num_dense_window", b, 1024 / hl.dense_blocks, counts[b],
                            sums[b], sums[16 + b], sums[32 + b]);
             launch_num_window(dt, op, rows, counts[b], (unsigned long long *)h->split.ptr, hl, sl, wc, out, err, s);
-        } else if (b == kBinSpill) {
+        } else if (b == kBinSpill || b == kBinDense) {
             const int tb = table_bits(maxsize[b], rule.inv_load);
             const HashLaunch hl = hash_launch(h, tb, op.ncols);
             const size_t need = ((size_t)num_spill_grid(dt, hl) << tb) * (4 + vsz);

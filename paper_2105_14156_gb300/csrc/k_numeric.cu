@@ -26,19 +26,23 @@ namespace smash {
 // ----- shared-memory hash rows -----------------------------------------------
 template <typename V, int GS, int NT>
 __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows, int count, int *token,
-                                                 int tbits, HashCfg hc, int bm_words, int bitmap_ratio,
+                                                 int tbits, HashCfg hc, int bsh, int bm_words, int bitmap_ratio,
                                                  NumOutT<V> out, int *err) {
+    // bsh >= 0: bucket-rank write-out (its T/4 counters and T/2 grouped keys
+    // follow each group's table); bsh < 0: bitonic.
     using G = Group<GS, NT>;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_row[G::kGroups];
     const int T = 1 << tbits;
-    const size_t tab_bytes = (size_t)T * (4 + sizeof(V));
-    unsigned char *gb = smem + (size_t)G::gid() * tab_bytes;
+    const size_t grp_bytes = (size_t)T * (4 + sizeof(V)) + (bsh >= 0 ? bucket_bytes(T) : 0);
+    unsigned char *gb = smem + (size_t)G::gid() * grp_bytes;
     int *keys = (int *)gb;
     V *vals = (V *)(gb + (size_t)T * 4);
-    unsigned char *scr = smem + (size_t)G::kGroups * tab_bytes + (size_t)G::gid() * num_scratch_bytes<V, GS>();
+    int *bc = (int *)(gb + (size_t)T * (4 + sizeof(V)));   // T/4 bucket counters
+    int *gk = bc + (T >> 2);                               // T/2 grouped keys
+    unsigned char *scr = smem + (size_t)G::kGroups * grp_bytes + (size_t)G::gid() * num_scratch_bytes<V, GS>();
     const ProdScratch<V> sc = carve_prod_scratch<V, GS>(scr);
-    unsigned *bm = (unsigned *)(smem + (size_t)G::kGroups * (tab_bytes + num_scratch_bytes<V, GS>()));
+    unsigned *bm = (unsigned *)(smem + (size_t)G::kGroups * (grp_bytes + num_scratch_bytes<V, GS>()));
     int *pre = (int *)(bm + bm_words);
     const int t = G::tid();
     for (;;) {
@@ -62,6 +66,8 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
             keys[s] = kEmpty;
             vals[s] = V(0);
         }
+        if (bsh >= 0)
+            for (int s = t; s < (T >> 2); s += GS) bc[s] = 0;
         if (use_bm)
             for (int w = t; w < bm_words; w += GS) bm[w] = 0u;
         G::sync();
@@ -102,6 +108,8 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
         if (!over) {
             if (GS == 32 && tot <= 32) writeout_warp_rank<V>(keys, vals, T, tot, n_exp, out, c0);
             else if (use_bm) writeout_bitmap<V, GS, NT>(keys, vals, T, bm, pre, bm_words, n_exp, out, c0, sc.red);
+            else if (bsh >= 0 && tot <= (T >> 1))
+                writeout_bucket<V, GS, NT>(keys, vals, tbits, hc, bc, gk, bsh, tot, n_exp, out, c0, sc.red);
             else writeout_bitonic<V, GS, NT>(keys, vals, T, n_exp, out, c0, sc.red);
         }
         G::sync();
@@ -463,10 +471,10 @@ static int threads_per_row(int tbits, int shift) {
     return t;
 }
 
-static int block_threads(int gs) { return gs < 256 ? 256 : gs; }
+static int block_threads(int gs) { return gs < 64 ? 256 : gs; }
 
 template <typename V>
-static size_t num_hash_smem(int tbits, int gs, int bm_words) {
+static size_t num_hash_smem(int tbits, int gs, int bm_words, bool buckets = false) {
     const int nt = block_threads(gs);
     const int groups = nt / gs;
     size_t scr = 0;
@@ -478,7 +486,9 @@ static size_t num_hash_smem(int tbits, int gs, int bm_words) {
         case 512: scr = num_scratch_bytes<V, 512>(); break;
         default: scr = num_scratch_bytes<V, 1024>(); break;
     }
-    return (size_t)groups * (((size_t)(4 + sizeof(V))) << tbits) + (size_t)groups * scr + (size_t)bm_words * 8;
+    const int T = 1 << tbits;
+    return (size_t)groups * ((size_t)(4 + sizeof(V)) * T + (buckets ? bucket_bytes(T) : 0)) +
+           (size_t)groups * scr + (size_t)bm_words * 8;
 }
 
 bool num_hash_bitmap_fits(int dtype, int tbits, int ncols) {
@@ -500,19 +510,24 @@ static int resident_grid(K kernel, int nt, size_t smem, int sms, long long want_
 template <typename V, int GS>
 static void num_hash_go(const Operands<V> &op, const int *rows, int count, int *token, const HashLaunch &hl,
                         int bitmap_ratio, const NumOutT<V> &out, int *err, cudaStream_t s) {
-    constexpr int NT = GS < 256 ? 256 : GS;
+    // one group per block from 64 threads up (block barriers, no named ones)
+    constexpr int NT = GS < 64 ? 256 : GS;
     constexpr int groups = NT / GS;
     int bm_words = 0;
     if (GS == NT && bitmap_ratio > 0) {
         const int words = (op.ncols + 31) / 32;
-        if (num_hash_smem<V>(hl.tbits, GS, words) <= (size_t)max_smem_per_block()) bm_words = words;
+        if (num_hash_smem<V>(hl.tbits, GS, words, true) <= (size_t)max_smem_per_block()) bm_words = words;
     }
-    const size_t smem = num_hash_smem<V>(hl.tbits, GS, bm_words);
+    // bucket-rank write-out when its arrays fit next to the tables
+    const bool buckets = num_hash_smem<V>(hl.tbits, GS, bm_words, true) <= (size_t)max_smem_per_block();
+    const size_t smem = num_hash_smem<V>(hl.tbits, GS, bm_words, buckets);
     auto kern = k_num_hash<V, GS, NT>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int grid = resident_grid(kern, NT, smem, hl.sms, (count + groups - 1) / groups);
     const HashCfg hc{hl.hash_kind, hl.colbits};
-    kern<<<grid, NT, smem, s>>>(op, rows, count, token, hl.tbits, hc, bm_words, bitmap_ratio, out, err);
+    // buckets: T/4 of them over the column range, by the high bits
+    const int bsh = !buckets ? -1 : hl.colbits > hl.tbits - 2 ? hl.colbits - (hl.tbits - 2) : 0;
+    kern<<<grid, NT, smem, s>>>(op, rows, count, token, hl.tbits, hc, bsh, bm_words, bitmap_ratio, out, err);
 }
 
 template <typename V>

@@ -19,87 +19,169 @@ __device__ __forceinline__ int bin_for(long long size, const BinRule &r) {
     return r.dense_ok ? kBinDense : kBinSpill;
 }
 
-// One warp per row of A: flop_i and nnz(A_i). The size that bins the row is
-// the bound min(flop_i, cols(B)) in the symbolic phase (c_rp == nullptr) and
-// the exact length c_rp[i+1] - c_rp[i] in the numeric phase.
+// flop_i and nnz(A_i) of every planned row. k_rowinfo: one thread per row;
+// rows longer than kLongRow entries go to a list (the long rows of R-MAT sit
+// together at small row ids) that k_rowinfo_long spreads over all warps, one
+// warp per row. The size that bins the row is the bound min(flop_i, cols(B))
+// in the symbolic phase (c_rp == nullptr) and the exact length
+// c_rp[i+1] - c_rp[i] in the numeric phase. Per-bin statistics are combined
+// over each warp's rows of the same bin before they reach the block's shared
+// counters, and the blocks' counters reach the global ones once per block.
+constexpr int kLongRow = 64;
+
+__device__ __forceinline__ long long b_row_len(const RawOperands &op, int k, int *err) {
+    if ((unsigned)k >= (unsigned)op.b_rows) {
+        raise_err(err, kErrBadIndex);
+        return 0;
+    }
+    const int64_t s = __ldg(op.b_rp + k), t = __ldg(op.b_rp + k + 1);
+    if (s >= 0 && t >= s && t <= op.b_nnz) return t - s;
+    raise_err(err, kErrBadRowPtr);
+    return 0;
+}
+
+struct RowStats {
+    int cnt[kNumBins];
+    long long max[kNumBins];
+    long long sum[3][kNumBins];
+    long long prod, maxrow;
+
+    __device__ __forceinline__ void init() {
+        if (threadIdx.x < kNumBins) {
+            cnt[threadIdx.x] = 0;
+            max[threadIdx.x] = 0;
+            sum[0][threadIdx.x] = sum[1][threadIdx.x] = sum[2][threadIdx.x] = 0;
+        }
+        if (threadIdx.x == 0) {
+            prod = 0;
+            maxrow = 0;
+        }
+    }
+    __device__ __forceinline__ void flush(BinBuffers &bb) {
+        if (threadIdx.x < kNumBins && cnt[threadIdx.x]) {
+            const int b = threadIdx.x;
+            atomicAdd(bb.counts + b, cnt[b]);
+            atomicMax(bb.maxsize + b, max[b]);
+            for (int q = 0; q < 3; ++q)
+                atomicAdd((unsigned long long *)(bb.sums + q * 16 + b), (unsigned long long)sum[q][b]);
+        }
+        if (threadIdx.x == 0) {
+            atomicAdd((unsigned long long *)bb.stats, (unsigned long long)prod);
+            atomicMax(bb.stats + 1, maxrow);
+        }
+    }
+};
+
+// Bins the warp's valid rows (one per lane) and adds them to the block's
+// statistics. Called by all 32 lanes.
+__device__ __forceinline__ void bin_rows(bool valid, int64_t i, int64_t len, long long f, const RawOperands &op,
+                                         const int64_t *c_rp, int64_t c_nnz, const BinRule &rule, BinBuffers &bb,
+                                         long long *bound_out, int *nnz_out, int *err, RowStats &st) {
+    const int lane = lane_id();
+    long long size = 0;
+    int b = kBinEmpty;
+    if (valid) {
+        if (c_rp) {
+            const int64_t s = c_rp[i], t = c_rp[i + 1];
+            if (s < 0 || t < s || t > c_nnz) raise_err(err, kErrBadRowPtr);
+            else size = t - s;
+        } else {
+            size = f < (long long)op.ncols ? f : (long long)op.ncols;
+            bound_out[i] = size;
+        }
+        b = bin_for(size, rule);
+        bb.bin[i] = (uint8_t)b;
+        if (!c_rp && b == kBinEmpty) nnz_out[i] = 0;
+    }
+    const long long wp = warp_sum(valid ? f : 0ll);
+    const long long wm = warp_max(valid ? f : 0ll);
+    if (lane == 0) {
+        atomicAdd((unsigned long long *)&st.prod, (unsigned long long)wp);
+        atomicMax(&st.maxrow, wm);
+    }
+    for (unsigned todo = __ballot_sync(kFull, valid); todo;) {
+        const int b0 = __shfl_sync(kFull, b, __ffs(todo) - 1);
+        const bool mine = valid && b == b0;
+        const unsigned m = __ballot_sync(kFull, mine);
+        todo &= ~m;
+        const long long s0 = warp_sum(mine ? (long long)len : 0ll);
+        const long long s1 = warp_sum(mine ? f : 0ll);
+        const long long s2 = warp_sum(mine ? size : 0ll);
+        const long long mx = warp_max(mine ? size : 0ll);
+        if (lane == 0) {
+            atomicAdd(&st.cnt[b0], __popc(m));
+            atomicMax(&st.max[b0], mx);
+            atomicAdd((unsigned long long *)&st.sum[0][b0], (unsigned long long)s0);
+            atomicAdd((unsigned long long *)&st.sum[1][b0], (unsigned long long)s1);
+            atomicAdd((unsigned long long *)&st.sum[2][b0], (unsigned long long)s2);
+        }
+    }
+}
+
+// Short rows: one thread per row. Long rows: appended to long_list.
 __global__ void __launch_bounds__(256) k_rowinfo(RawOperands op, const int64_t *c_rp, int64_t c_nnz, BinRule rule,
                                                  BinBuffers bb, long long *bound_out, int *nnz_out, int *err,
-                                                 const int *row_list, int64_t nrows) {
-    __shared__ int s_cnt[kNumBins];
-    __shared__ long long s_max[kNumBins];
-    __shared__ long long s_sum[3][kNumBins];
-    __shared__ long long s_prod, s_maxrow;
-    if (threadIdx.x < kNumBins) {
-        s_cnt[threadIdx.x] = 0;
-        s_max[threadIdx.x] = 0;
-        s_sum[0][threadIdx.x] = s_sum[1][threadIdx.x] = s_sum[2][threadIdx.x] = 0;
-    }
-    if (threadIdx.x == 0) {
-        s_prod = 0;
-        s_maxrow = 0;
-    }
+                                                 const int *row_list, int64_t nrows, int *long_list,
+                                                 unsigned long long *long_count) {
+    __shared__ RowStats st;
+    st.init();
     __syncthreads();
     const int lane = lane_id();
-    long long my_prod = 0, my_max = 0;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += warps) {
-        const int64_t i = row_list ? row_list[r] : r;
-        int64_t ab = __ldg(op.a_rp + i), ae = __ldg(op.a_rp + i + 1);
-        if (ab < 0 || ae < ab || ae > op.a_nnz) {
-            if (lane == 0) raise_err(err, kErrBadRowPtr);
-            ab = ae = 0;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (int64_t base = gw * 32; base < nrows; base += warps * 32) {
+        const int64_t r = base + lane;
+        bool valid = r < nrows;
+        int64_t i = 0, ab = 0, ae = 0;
+        if (valid) {
+            i = row_list ? row_list[r] : r;
+            ab = __ldg(op.a_rp + i);
+            ae = __ldg(op.a_rp + i + 1);
+            if (ab < 0 || ae < ab || ae > op.a_nnz) {
+                raise_err(err, kErrBadRowPtr);
+                ab = ae = 0;
+            }
         }
+        const bool longrow = ae - ab > kLongRow;
+        const unsigned lm = __ballot_sync(kFull, longrow);
+        if (lm) {
+            unsigned long long at = 0;
+            if (lane == 0) at = atomicAdd(long_count, (unsigned long long)__popc(lm));
+            at = __shfl_sync(kFull, at, 0);
+            if (longrow) long_list[at + __popc(lm & lanemask_lt())] = (int)i;
+        }
+        valid = valid && !longrow;
         long long f = 0;
-        for (int64_t e = ab + lane; e < ae; e += 32) {
-            const int k = __ldg(op.a_ci + e);
-            if ((unsigned)k < (unsigned)op.b_rows) {
-                const int64_t s = __ldg(op.b_rp + k), t = __ldg(op.b_rp + k + 1);
-                if (s >= 0 && t >= s && t <= op.b_nnz) f += t - s;
-                else raise_err(err, kErrBadRowPtr);
-            } else {
-                raise_err(err, kErrBadIndex);
-            }
-        }
-        f = warp_sum(f);
-        if (lane == 0) {
-            long long size;
-            if (c_rp) {
-                const int64_t s = c_rp[i], t = c_rp[i + 1];
-                size = 0;
-                if (s < 0 || t < s || t > c_nnz) raise_err(err, kErrBadRowPtr);
-                else size = t - s;
-            } else {
-                size = f < (long long)op.ncols ? f : (long long)op.ncols;
-                bound_out[i] = size;
-            }
-            const int b = bin_for(size, rule);
-            bb.bin[i] = (uint8_t)b;
-            atomicAdd(&s_cnt[b], 1);
-            atomicMax(&s_max[b], size);
-            atomicAdd((unsigned long long *)&s_sum[0][b], (unsigned long long)(ae - ab));
-            atomicAdd((unsigned long long *)&s_sum[1][b], (unsigned long long)f);
-            atomicAdd((unsigned long long *)&s_sum[2][b], (unsigned long long)size);
-            if (!c_rp && b == kBinEmpty) nnz_out[i] = 0;
-            my_prod += f;
-            my_max = f > my_max ? f : my_max;
-        }
-    }
-    if (lane == 0) {
-        atomicAdd((unsigned long long *)&s_prod, (unsigned long long)my_prod);
-        atomicMax(&s_maxrow, my_max);
+#pragma unroll 4
+        for (int64_t e = ab; e < (longrow ? ab : ae); ++e) f += b_row_len(op, __ldg(op.a_ci + e), err);
+        bin_rows(valid, i, ae - ab, f, op, c_rp, c_nnz, rule, bb, bound_out, nnz_out, err, st);
     }
     __syncthreads();
-    if (threadIdx.x < kNumBins && s_cnt[threadIdx.x]) {
-        const int b = threadIdx.x;
-        atomicAdd(bb.counts + b, s_cnt[b]);
-        atomicMax(bb.maxsize + b, s_max[b]);
-        for (int q = 0; q < 3; ++q)
-            atomicAdd((unsigned long long *)(bb.sums + q * 16 + b), (unsigned long long)s_sum[q][b]);
+    st.flush(bb);
+}
+
+// The long rows: one warp per row.
+__global__ void __launch_bounds__(256) k_rowinfo_long(RawOperands op, const int64_t *c_rp, int64_t c_nnz,
+                                                      BinRule rule, BinBuffers bb, long long *bound_out, int *nnz_out,
+                                                      int *err, const int *long_list,
+                                                      const unsigned long long *long_count) {
+    __shared__ RowStats st;
+    st.init();
+    __syncthreads();
+    const int lane = lane_id();
+    const int64_t n = (int64_t)*long_count;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < n; q += warps) {
+        const int64_t i = long_list[q];
+        const int64_t ab = __ldg(op.a_rp + i), ae = __ldg(op.a_rp + i + 1);   // checked by k_rowinfo
+        long long f = 0;
+#pragma unroll 4
+        for (int64_t e = ab + lane; e < ae; e += 32) f += b_row_len(op, __ldg(op.a_ci + e), err);
+        f = warp_sum(f);
+        bin_rows(lane == 0, i, ae - ab, f, op, c_rp, c_nnz, rule, bb, bound_out, nnz_out, err, st);
     }
-    if (threadIdx.x == 0) {
-        atomicAdd((unsigned long long *)bb.stats, (unsigned long long)s_prod);
-        atomicMax(bb.stats + 1, s_maxrow);
-    }
+    __syncthreads();
+    st.flush(bb);
 }
 
 // Scatter row ids into their bins. Each block reserves one range per bin.
@@ -231,23 +313,40 @@ __global__ void __launch_bounds__(kScanNT) k_scan_down(const int *nnz, int64_t n
 
 // ---------------------------------------------------------------------------
 static int rowinfo_grid(int64_t rows, int sms) {
-    const int64_t blocks = (rows + 7) / 8;
+    const int64_t blocks = (rows + 255) / 256;
     const int64_t cap = (int64_t)sms * 8;
     return (int)(blocks < cap ? blocks : cap);
+}
+
+// bb.rows (filled later by the bin scatter) holds the long-row list meanwhile;
+// bb.stats[2] counts it.
+static void rowinfo(const RawOperands &op, const int64_t *c_rp, int64_t c_nnz, const BinRule &rule, BinBuffers bb,
+                    long long *bound_out, int *nnz_out, int *err, int sms, cudaStream_t s, const int *row_list,
+                    int64_t n) {
+    unsigned long long *lc = (unsigned long long *)(bb.stats + 2);
+    k_rowinfo<<<rowinfo_grid(n, sms), 256, 0, s>>>(op, c_rp, c_nnz, rule, bb, bound_out, nnz_out, err, row_list, n,
+                                                    bb.rows, lc);
+    // at most min(n, nnz(A) / (kLongRow + 1)) long rows, 8 per block
+    int64_t most = op.a_nnz / (kLongRow + 1) + 1;
+    if (most > n) most = n;
+    const int64_t blocks = (most + 7) / 8;
+    const int64_t cap = (int64_t)sms * 8;
+    k_rowinfo_long<<<(int)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap), 256, 0, s>>>(
+        op, c_rp, c_nnz, rule, bb, bound_out, nnz_out, err, bb.rows, lc);
 }
 
 void launch_sym_rowinfo(const RawOperands &op, const BinRule &rule, BinBuffers bb, long long *bound_out,
                         int *nnz_out, int *err, int sms, cudaStream_t s, const int *row_list, int64_t list_n) {
     const int64_t n = row_list ? list_n : op.a_rows;
     if (n == 0) return;
-    k_rowinfo<<<rowinfo_grid(n, sms), 256, 0, s>>>(op, nullptr, 0, rule, bb, bound_out, nnz_out, err, row_list, n);
+    rowinfo(op, nullptr, 0, rule, bb, bound_out, nnz_out, err, sms, s, row_list, n);
 }
 
 void launch_num_rowinfo(const RawOperands &op, const int64_t *c_rp, int64_t c_nnz, const BinRule &rule,
                         BinBuffers bb, int *err, int sms, cudaStream_t s, const int *row_list, int64_t list_n) {
     const int64_t n = row_list ? list_n : op.a_rows;
     if (n == 0) return;
-    k_rowinfo<<<rowinfo_grid(n, sms), 256, 0, s>>>(op, c_rp, c_nnz, rule, bb, nullptr, nullptr, err, row_list, n);
+    rowinfo(op, c_rp, c_nnz, rule, bb, nullptr, nullptr, err, sms, s, row_list, n);
 }
 
 // Rows whose staged result did not fit (row_nnz < 0): appended to list.

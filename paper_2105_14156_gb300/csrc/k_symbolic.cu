@@ -229,8 +229,8 @@ void launch_sym_hash(const RawOperands &r, const int *rows, int count, int *toke
     const HashCfg hc{hl.hash_kind, hl.colbits};
     switch (threads_per_row(hl.tbits, hl.group_shift)) {
         case 32: sym_hash_launch<32, 256>(op, rows, count, token, hl.tbits, hc, hl.sms, nnz_out, err, s); break;
-        case 64: sym_hash_launch<64, 256>(op, rows, count, token, hl.tbits, hc, hl.sms, nnz_out, err, s); break;
-        case 128: sym_hash_launch<128, 256>(op, rows, count, token, hl.tbits, hc, hl.sms, nnz_out, err, s); break;
+        case 64: sym_hash_launch<64, 64>(op, rows, count, token, hl.tbits, hc, hl.sms, nnz_out, err, s); break;
+        case 128: sym_hash_launch<128, 128>(op, rows, count, token, hl.tbits, hc, hl.sms, nnz_out, err, s); break;
         case 256: sym_hash_launch<256, 256>(op, rows, count, token, hl.tbits, hc, hl.sms, nnz_out, err, s); break;
         case 512: sym_hash_launch<512, 512>(op, rows, count, token, hl.tbits, hc, hl.sms, nnz_out, err, s); break;
         default: sym_hash_launch<1024, 1024>(op, rows, count, token, hl.tbits, hc, hl.sms, nnz_out, err, s); break;

@@ -118,6 +118,68 @@ __device__ __forceinline__ void writeout_bitonic(int *keys, V *vals, int T, int 
     }
 }
 
+// ----- write-out: bucket rank ------------------------------------------------
+// Counting sort by the high bits of the column, then a rank inside each
+// (small) bucket: NB = T/4 buckets, bucket(j) = j >> sh (monotone in j).
+// bc[NB]: per-bucket counters (zero on entry), gk[T/2]: the keys grouped by
+// bucket. A key's final position is its bucket's start plus the number of
+// smaller keys in its bucket; its value is found again by probing the table.
+// Needs tot <= T/2 (the row's distinct columns).
+__host__ __device__ constexpr size_t bucket_bytes(int T) {
+    return (size_t)T * 3;   // bc: T/4 ints, gk: T/2 ints
+}
+
+template <typename V, int GS, int NT>
+__device__ __forceinline__ void writeout_bucket(const int *keys, const V *vals, int tbits, HashCfg hc, int *bc,
+                                                int *gk, int sh, int tot, int n_exp, const NumOutT<V> &out,
+                                                int64_t c0, int *red) {
+    using G = Group<GS, NT>;
+    const int t = G::tid();
+    const int T = 1 << tbits;
+    const int NB = T >> 2;
+    for (int s = t; s < T; s += GS) {
+        const int k = keys[s];
+        if (k != kEmpty) atomicAdd(bc + (k >> sh), 1);
+    }
+    G::sync();
+    {
+        const int per = (NB + GS - 1) / GS;
+        const int b0 = min(t * per, NB), b1 = min(b0 + per, NB);
+        int loc = 0;
+        for (int b = b0; b < b1; ++b) loc += bc[b];
+        int tsum;
+        int run = G::template excl_scan<int>(loc, red, &tsum);
+        for (int b = b0; b < b1; ++b) {
+            const int c = bc[b];
+            bc[b] = run;
+            run += c;
+        }
+    }
+    G::sync();
+    for (int s = t; s < T; s += GS) {
+        const int k = keys[s];
+        if (k != kEmpty) gk[atomicAdd(bc + (k >> sh), 1)] = k;
+    }
+    G::sync();
+    // bc[b] is now the end of bucket b
+    const uint32_t mask = (uint32_t)T - 1u;
+    for (int q = t; q < tot; q += GS) {
+        const int k = gk[q];
+        const int b = k >> sh;
+        const int e = bc[b];
+        const int s0 = b ? bc[b - 1] : 0;
+        int r = 0;
+        for (int x = s0; x < e; ++x) r += gk[x] < k ? 1 : 0;
+        uint32_t h = hash_slot(k, tbits, hc) & mask;
+        for (uint32_t n = 0; n <= mask && keys[h] != k; ++n) h = (h + 1u) & mask;
+        const int pos = s0 + r;
+        if (pos < n_exp) {
+            out.c_ci[c0 + pos] = k;
+            out.c_val[c0 + pos] = vals[h];
+        }
+    }
+}
+
 // Exclusive prefix of popcounts over words [0, nwords) of bm (contiguous
 // chunk per thread); returns the total.
 template <int GS, int NT>

@@ -16,7 +16,7 @@ from tests.helpers import identity, random_csr
 
 pytestmark = pytest.mark.gpu
 
-DEFAULT = dict(hash_kind=1, max_load=0.5, sym_max_tbits=15, num_max_tbits=14, group_shift=3, dense_ratio=4,
+DEFAULT = dict(hash_kind=1, max_load=0.5, sym_max_tbits=15, num_max_tbits=14, group_shift=4, dense_ratio=4,
                bitmap_ratio=4, spill_blocks_per_sm=1, sym_dense_ratio=64, dense_blocks=0,
                sym_dense_blocks=0)
 
@@ -98,6 +98,15 @@ def test_unsorted_and_duplicate_columns(handle):
         assert_matches_oracle(C, A, B)
 
 
+def test_unsorted_and_duplicate_columns_many_windows(handle):
+    """B's rows regrouped by column window when they are unsorted and hold
+    duplicate columns."""
+    A = random_csr(120, 200, 0.1, 43, values="f64", sort_cols=False, dup_frac=0.3)
+    B = random_csr(200, 50000, 0.004, 44, values="f64", sort_cols=False, dup_frac=0.3)
+    C = run(handle, A, B, dense_ratio=1 << 20, dense_blocks=4)
+    assert_matches_oracle(C, A, B)
+
+
 def test_empty_inputs(handle):
     from paper_2105_14156_gb300 import smash
     E = Csr(0, 5, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
@@ -161,6 +170,15 @@ def test_dense_rows_windows(handle, ncols, dense_blocks, dtype):
     A = random_csr(96, 64, 0.3, 51, values=dtype)
     B = random_csr(64, ncols, 800.0 / ncols, 52, values=dtype)
     C = run(handle, A, B, dense_ratio=1 << 20, dense_blocks=dense_blocks)
+    assert_matches_oracle(C, A, B)
+
+
+def test_dense_rows_without_windows(handle):
+    """Dense rows whose few products do not pay for slicing a tall B by column
+    window take the global-memory hash instead."""
+    A = random_csr(40, 100000, 5e-5, 71, values="f64")
+    B = random_csr(100000, 200000, 5e-5, 72, values="f64")
+    C = run(handle, A, B, dense_ratio=1 << 20)
     assert_matches_oracle(C, A, B)
 
 
