@@ -89,6 +89,8 @@ int smash_destroy(smash_handle *h) {
         release(h, h->wslot);
         release(h, h->wcnt);
         release(h, h->stage);
+    release(h, h->arena);
+        release(h, h->arena);
         release(h, h->learn);
         batched_release(h);
         release(h, h->err);
@@ -120,6 +122,7 @@ int smash_set_allocator(smash_handle *h, smash_alloc_fn alloc, smash_free_fn fre
     release(h, h->wslot);
     release(h, h->wcnt);
     release(h, h->stage);
+    release(h, h->arena);
     release(h, h->learn);
     batched_release(h);
     // the error words move to the new allocator as well
@@ -212,6 +215,7 @@ int spgemm_numeric(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
     const int64_t n = A->rows;
     memset(&h->stats, 0, sizeof(h->stats));
     h->stats.c_nnz = C->nnz;
+    h->plan_cache.valid = false;   // B's values may have changed since the last call
     if (n == 0 || C->nnz == 0) return SMASH_OK;
     Plan pl;
     if ((st = plan_buffers(h, n, false, s, pl))) return st;
@@ -294,7 +298,6 @@ int run_symbolic(smash_handle *h, const RawOperands &op, int64_t n, Plan &pl, in
 
 int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const NumOut &out, Plan &pl,
                 cudaStream_t s, const int *row_list, int64_t list_n) {
-    int st;
     const BinRule rule = num_rule(h, op.ncols, dt);
     int *err = (int *)h->err.ptr;
     if (row_list && cudaMemsetAsync(pl.bb.bin, 0, (size_t)n, s) != cudaSuccess) return SMASH_ERR_CUDA;
@@ -306,10 +309,61 @@ int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const
         LaunchTimer lt(h, s, "bin_scatter", -1, 256, n, 0, 0, 0);
         launch_bin_scatter(n, pl.bb, s);
     }
+    int st;
     if ((st = last_cuda_status())) return st;
-    int counts[16], offsets[17];
-    long long maxsize[16], stats[4], sums[48];
-    if ((st = fetch_bins(h, pl, s, counts, offsets, maxsize, stats, sums))) return st;
+    BinPlan bp;
+    if ((st = fetch_bins(h, pl, s, bp.counts, bp.offsets, bp.maxsize, bp.stats, bp.sums))) return st;
+    return run_bins(h, op, n, dt, out, pl, bp, s, nullptr);
+}
+
+bool dense_windows(const smash_handle *h, const RawOperands &op, int dt, long long products, int &cpc, int &nw) {
+    cpc = num_window_cols(dt, dense_blocks_of(h, dt));
+    if (cpc <= 0) return false;
+    nw = (int)((op.ncols + cpc - 1) / cpc);
+    const double vsz = dt ? 8.0 : 4.0;
+    const double plan = nw > 1 ? 4.0 * (double)op.b_rows * (nw + 1) + 2.0 * (4 + vsz) * (double)op.b_nnz : 0.0;
+    return 16.0 * (double)products >= plan;
+}
+
+int window_plan(smash_handle *h, const RawOperands &op, int dt, int cpc, int nw, cudaStream_t s, BSlices &sl) {
+    auto &pc = h->plan_cache;
+    if (pc.valid && pc.b_rp == op.b_rp && pc.b_ci == op.b_ci && pc.b_val == op.b_val && pc.b_nnz == op.b_nnz &&
+        pc.b_rows == op.b_rows && pc.ncols == op.ncols && pc.cpc == cpc && pc.nw == nw && pc.dt == dt) {
+        sl = pc.sl;
+        return SMASH_OK;
+    }
+    const size_t vsz = dt ? 8 : 4;
+    const void *before = h->split.ptr;
+    int st;
+    if ((st = ensure(h, h->split, 256 + window_plan_bytes(op, nw, vsz), s))) return st;
+    (void)before;
+    {
+        LaunchTimer lt(h, s, "dense_plan", -1, 256, op.b_rows, 0, 0, op.b_nnz, nw > 1 ? 2 : 0);
+        launch_window_plan(dt, op, nw, cpc, (char *)h->split.ptr + 256, sl, h->sms, s);
+    }
+    pc.valid = true;
+    pc.b_rp = op.b_rp;
+    pc.b_ci = op.b_ci;
+    pc.b_val = op.b_val;
+    pc.b_nnz = op.b_nnz;
+    pc.b_rows = op.b_rows;
+    pc.ncols = op.ncols;
+    pc.cpc = cpc;
+    pc.nw = nw;
+    pc.dt = dt;
+    pc.sl = sl;
+    return SMASH_OK;
+}
+
+int run_bins(smash_handle *h, const RawOperands &op, int64_t n, int dt, const NumOut &out, Plan &pl,
+             const BinPlan &bp, cudaStream_t s, const WinArena *arena) {
+    int st;
+    const BinRule rule = num_rule(h, op.ncols, dt);
+    int *err = (int *)h->err.ptr;
+    const int *counts = bp.counts;
+    const int *offsets = bp.offsets;
+    const long long *maxsize = bp.maxsize;
+    const long long *sums = bp.sums;
     const size_t vsz = dt ? 8 : 4;
     for (int b = 1; b < kNumBins; ++b) {
         if (!counts[b]) continue;
@@ -317,57 +371,50 @@ int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const
         int *tok = pl.bb.tokens + b;
         // Dense rows take column windows when their products pay for slicing
         // B (a pass over B's rows and entries); otherwise the global hash.
-        bool windows = false;
         int cpc = 0, nw = 0;
-        if (b == kBinDense) {
-            cpc = num_window_cols(dt, dense_blocks_of(h, dt));
-            nw = (int)((op.ncols + cpc - 1) / cpc);
-            const double plan = nw > 1 ? 4.0 * (double)op.b_rows * (nw + 1) + 2.0 * (4 + vsz) * (double)op.b_nnz : 0.0;
-            windows = 16.0 * (double)sums[16 + b] >= plan;
-        }
+        const bool windows = b == kBinDense && dense_windows(h, op, dt, sums[16 + b], cpc, nw);
         if (b == kBinDense && windows) {
             HashLaunch hl = hash_launch(h, 0, op.ncols);
             hl.dense_blocks = dense_blocks_of(h, dt);
-            // 1. per-block column counts of the dense rows: from the symbolic
-            //    phase of the same operands, else counted here (and sizes checked)
-            const int nsub = (int)((op.ncols + kSubCols - 1) / kSubCols);
-            if (!wcache_matches(h, op) || h->wcache.nsub != nsub) {
-                if ((st = ensure(h, h->wslot, sizeof(int) * (size_t)n, s))) return st;
-                if (cudaMemsetAsync(h->wslot.ptr, 0xff, sizeof(int) * (size_t)n, s) != cudaSuccess)
-                    return SMASH_ERR_CUDA;
-                wcache_set(h, op, nsub, 0);
-            }
-            const int64_t base = h->wcache.slots;
-            if ((st = ensure_keep(h, h->wcnt, sizeof(uint16_t) * (size_t)(base + counts[b]) * nsub,
-                                  sizeof(uint16_t) * (size_t)base * nsub, s)))
-                return st;
             WinCount wc;
-            wc.wslot = (int *)h->wslot.ptr;
-            wc.wcnt = (uint16_t *)h->wcnt.ptr;
-            wc.nsub = nsub;
-            wc.slot_base = base;
-            wc.skip_slotted = 1;
-            NumCheck nc;
-            nc.c_rp = out.c_rp;
-            nc.c_nnz = out.c_nnz;
-            nc.row_nnz = out.row_nnz;
-            {
-                LaunchTimer lt(h, s, "num_dense_count", b, sym_dense_threads(hl, op.ncols), counts[b], sums[b],
-                               sums[16 + b], sums[32 + b]);
-                launch_sym_dense(op, rows, counts[b], tok, hl, wc, nullptr, nc, err, s);
+            if (!arena) {
+                // 1. per-block column counts of the dense rows: from the symbolic
+                //    phase of the same operands, else counted here (and sizes checked)
+                const int nsub = (int)((op.ncols + kSubCols - 1) / kSubCols);
+                if (!wcache_matches(h, op) || h->wcache.nsub != nsub) {
+                    if ((st = ensure(h, h->wslot, sizeof(int) * (size_t)n, s))) return st;
+                    if (cudaMemsetAsync(h->wslot.ptr, 0xff, sizeof(int) * (size_t)n, s) != cudaSuccess)
+                        return SMASH_ERR_CUDA;
+                    wcache_set(h, op, nsub, 0);
+                }
+                const int64_t base = h->wcache.slots;
+                if ((st = ensure_keep(h, h->wcnt, sizeof(uint16_t) * (size_t)(base + counts[b]) * nsub,
+                                      sizeof(uint16_t) * (size_t)base * nsub, s)))
+                    return st;
+                wc.wslot = (int *)h->wslot.ptr;
+                wc.wcnt = (uint16_t *)h->wcnt.ptr;
+                wc.nsub = nsub;
+                wc.slot_base = base;
+                wc.skip_slotted = 1;
+                NumCheck nc;
+                nc.c_rp = out.c_rp;
+                nc.c_nnz = out.c_nnz;
+                nc.row_nnz = out.row_nnz;
+                {
+                    LaunchTimer lt(h, s, "num_dense_count", b, sym_dense_threads(hl, op.ncols), counts[b], sums[b],
+                                   sums[16 + b], sums[32 + b]);
+                    launch_sym_dense(op, rows, counts[b], tok, hl, wc, nullptr, nc, err, s);
+                }
+                h->wcache.slots = base + counts[b];
             }
-            h->wcache.slots = base + counts[b];
             // 2. column windows: slices of B
-            if ((st = ensure(h, h->split, 256 + window_plan_bytes(op, nw, vsz), s))) return st;
             BSlices sl;
-            {
-                LaunchTimer lt(h, s, "dense_plan", -1, 256, op.b_rows, 0, 0, op.b_nnz, nw > 1 ? 2 : 0);
-                launch_window_plan(dt, op, nw, cpc, (char *)h->split.ptr + 256, sl, h->sms, s);
-            }
+            if ((st = window_plan(h, op, dt, cpc, nw, s, sl))) return st;
             // 3. (row, window) items
-            LaunchTimer lt(h, s, "num_dense_window", b, 1024 / hl.dense_blocks, counts[b],
-                           sums[b], sums[16 + b], sums[32 + b]);
-            launch_num_window(dt, op, rows, counts[b], (unsigned long long *)h->split.ptr, hl, sl, wc, out, err, s);
+            LaunchTimer lt(h, s, "num_dense_window", b, 1024 / hl.dense_blocks, counts[b], sums[b], sums[16 + b],
+                           sums[32 + b]);
+            launch_num_window(dt, op, rows, counts[b], (unsigned long long *)h->split.ptr, hl, sl, wc,
+                              arena ? *arena : WinArena{}, out, err, s);
         } else if (b == kBinSpill || b == kBinDense) {
             const int tb = table_bits(maxsize[b], rule.inv_load);
             const HashLaunch hl = hash_launch(h, tb, op.ncols);

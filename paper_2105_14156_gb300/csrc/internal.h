@@ -62,7 +62,17 @@ struct smash_handle {
         int nsub = 0;
         int64_t slots = 0;
     } wcache;
+    // The slices of B by column window last built in h->split (reused within
+    // one call only: B's values may change between calls).
+    struct {
+        bool valid = false;
+        const void *b_rp = nullptr, *b_ci = nullptr, *b_val = nullptr;
+        int64_t b_nnz = 0, b_rows = 0, ncols = 0;
+        int cpc = 0, nw = 0, dt = 0;
+        smash::BSlices sl;
+    } plan_cache;
     smash::DevBuf stage;      // learned path: capacity-padded staging of C
+    smash::DevBuf arena;      // learned path: dense rows' windows
     smash::DevBuf learn;      // learned path: per-row arrays
     smash::DevBuf err;        // kNumErr ints (+ scratch words)
     long long *host = nullptr;  // pinned host staging
@@ -489,6 +499,18 @@ int run_symbolic(smash_handle *h, const RawOperands &op, int64_t n, Plan &pl, in
                  const int *row_list, int64_t list_n);
 int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const NumOut &out, Plan &pl,
                 cudaStream_t s, const int *row_list, int64_t list_n);
+// The two halves of run_numeric: bins of the planned rows (fetched to the
+// host), then one launch per bin. arena != nullptr: the dense bin runs in
+// arena mode (capacity mode only).
+struct BinPlan {
+    int counts[16], offsets[17];
+    long long maxsize[16], stats[4], sums[48];
+};
+int run_bins(smash_handle *h, const RawOperands &op, int64_t n, int dt, const NumOut &out, Plan &pl,
+             const BinPlan &bp, cudaStream_t s, const WinArena *arena);
+// Whether the dense bin (with `products` products) takes column windows, and
+// their width and number.
+bool dense_windows(const smash_handle *h, const RawOperands &op, int dt, long long products, int &cpc, int &nw);
 
 }  // namespace host
 }  // namespace smash

@@ -1,36 +1,13 @@
-// Row-size predictor: features, inference and training kernels.
-//
-// Not part of the paper: a multilayer perceptron predicts y_i = log(1 +
-// nnz(C_i)) of every output row from six features of the row, so that hash
-// tables, bins and C's staging allocation can be sized without the exact
-// symbolic pass (rows whose prediction proves too small fall back to the exact
-// path). Network: x = (f - mean) * inv_std (6 inputs), h1 = relu(W1 x + b1),
-// h2 = relu(W2 h1 + b2) (64 units each), y = w3 . h2 + b3. Parameters are one
-// flat float vector W1 (64x6, row-major), b1, W2 (64x64, row-major), b2, w3,
-// b3. Inference reads a bfloat16 copy of the weights and accumulates in fp32;
-// training keeps fp32 master weights and Adam moments.
-//
-// The features of row i are computed from the row pointers alone (the same
-// information as the flop count of the Window Distribution Phase):
-//   f0 = log1p(nnz(A_i))            f1 = log1p(flop_i)
-//   f2 = log1p(max_k |B_k|)         f3 = log1p(flop_i / nnz(A_i))
-//   f4 = log1p(min(flop_i, cols))   f5 = min(flop_i, cols) / cols
+// Row-size predictor: features, inference and training kernels (the network
+// and its features are described in mlp.cuh). Training keeps fp32 master
+// weights and Adam moments; inference reads the bf16 copy.
 #include <cuda_bf16.h>
 
 #include "device_common.cuh"
 #include "kernels.h"
+#include "mlp.cuh"
 
 namespace smash {
-
-constexpr int kHid = 64;
-constexpr int kFeat = 6;
-constexpr int kOffW1 = 0;
-constexpr int kOffB1 = kOffW1 + kHid * kFeat;
-constexpr int kOffW2 = kOffB1 + kHid;
-constexpr int kOffB2 = kOffW2 + kHid * kHid;
-constexpr int kOffW3 = kOffB2 + kHid;
-constexpr int kOffB3 = kOffW3 + kHid;
-static_assert(kOffB3 + 1 == kMlpParams, "parameter layout");
 
 // One warp per row (all rows, or the rows of a list).
 __global__ void __launch_bounds__(256) k_features(RawOperands op, const int *row_list, int64_t nrows, float *feats,
@@ -58,64 +35,29 @@ __global__ void __launch_bounds__(256) k_features(RawOperands op, const int *row
         f = warp_sum(f);
         mx = warp_max(mx);
         if (lane == 0) {
-            // float arithmetic: the features only need a few significant digits
-            const float na = (float)(ae - ab);
-            const long long ub = f < (long long)op.ncols ? f : (long long)op.ncols;
-            float *x = feats + (size_t)i * kFeat;
-            x[0] = log1pf(na);
-            x[1] = log1pf((float)f);
-            x[2] = log1pf((float)mx);
-            x[3] = log1pf(na > 0.f ? (float)f / na : 0.f);
-            x[4] = log1pf((float)ub);
-            x[5] = op.ncols > 0 ? (float)ub / (float)op.ncols : 0.f;
-            if (bound) bound[i] = ub;
+            row_features(ae - ab, f, mx, op.ncols, feats + (size_t)i * kFeat);
+            if (bound) bound[i] = f < (long long)op.ncols ? f : (long long)op.ncols;
         }
     }
 }
 
-// Inference: one thread per row. cap_i = clamp(ceil((1+margin) expm1(y_i)), 1, bound_i);
-// rows with bound 0 get cap 0. Weights: bf16 in global memory, fp32 in shared.
+// Inference: one thread per row. cap_i = cap_of(y_i, margin, bound_i).
+// Weights: bf16 in global memory, fp32 in shared.
 __global__ void __launch_bounds__(256) k_mlp_infer(const float *feats, const long long *bound, const int *row_list,
                                                    int64_t nrows, const __nv_bfloat16 *wb, const float *norm,
                                                    float margin, float *y_out, int *cap_out) {
-    __shared__ float w[kMlpParams];
-    __shared__ float nm[2 * kFeat];
-    for (int k = threadIdx.x; k < kMlpParams; k += blockDim.x) w[k] = __bfloat162float(wb[k]);
-    if (threadIdx.x < 2 * kFeat) nm[threadIdx.x] = norm[threadIdx.x];
+    __shared__ __align__(16) float sm[kSmFloats];
+    load_mlp(sm, wb, norm);
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += stride) {
         const int64_t i = row_list ? row_list[r] : r;
-        float x[kFeat];
+        float f[kFeat];
 #pragma unroll
-        for (int c = 0; c < kFeat; ++c) x[c] = (feats[(size_t)i * kFeat + c] - nm[c]) * nm[kFeat + c];
-        float h1[kHid];
-#pragma unroll
-        for (int u = 0; u < kHid; ++u) {
-            float a = w[kOffB1 + u];
-#pragma unroll
-            for (int c = 0; c < kFeat; ++c) a = fmaf(w[kOffW1 + u * kFeat + c], x[c], a);
-            h1[u] = fmaxf(a, 0.f);
-        }
-        float y = w[kOffB3];
-        for (int u = 0; u < kHid; ++u) {
-            float a = w[kOffB2 + u];
-#pragma unroll
-            for (int v = 0; v < kHid; ++v) a = fmaf(w[kOffW2 + u * kHid + v], h1[v], a);
-            y = fmaf(w[kOffW3 + u], fmaxf(a, 0.f), y);
-        }
+        for (int c = 0; c < kFeat; ++c) f[c] = feats[(size_t)i * kFeat + c];
+        const float y = mlp_forward(sm, f);
         if (y_out) y_out[r] = y;
-        if (cap_out) {
-            const long long ub = bound[i];
-            long long cap = 0;
-            if (ub > 0) {
-                const float pred = expm1f(fminf(y, 40.f));
-                float c = ceilf((1.f + margin) * pred);
-                if (!(c >= 1.f)) c = 1.f;
-                cap = c >= (float)ub ? ub : (long long)c;
-            }
-            cap_out[i] = (int)cap;
-        }
+        if (cap_out) cap_out[i] = (int)cap_of(y, margin, bound[i]);
     }
 }
 

@@ -5,12 +5,15 @@
 // +1 linear probing), an atomic add accumulates the value (the "atomic fetch
 // and add" merge). Write-back Phase: the occupied slots are gathered, ordered
 // by column and streamed to C's row (Version 1 sorts the table before
-// streaming it out; the sort here is one of three, chosen per row):
+// streaming it out; the sort here is one of four, chosen per row):
 //   - warp rank:   rows of <= 32 entries held by one warp; each entry's rank is
 //                  the number of smaller tags (register shuffles);
 //   - bitmap rank: a bitmap over the columns of B plus a prefix count per
 //                  32-bit word gives every tag its position directly;
-//   - bitonic:     the compacted entries are sorted in shared memory.
+//   - bucket rank: counting sort of the tags by their high bits, then each
+//                  tag's rank inside its (small) bucket (writeout.cuh);
+//   - bitonic:     the compacted entries are sorted in shared memory (when
+//                  the bucket arrays do not fit next to the tables).
 // Table placements as in the symbolic phase: shared memory (k_num_hash),
 // dense accumulators for dense rows (k_num_window: one column window of the
 // row per work item, values indexed by column, occupancy in a bitmap), and a
@@ -87,18 +90,20 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
                 raise_err(err, kErrTableFull);
             }
         });
-        int tot;
+        // one reduction of (overflow flags, inserts): a row has at most
+        // T <= 2^14 distinct columns, so the inserts fit the low 16 bits
+        int tot, o;
         if constexpr (GS == 32) {
             tot = warp_sum(cnt);
+            o = __any_sync(kFull, ovf);
             __syncwarp();
         } else {
-            tot = G::template sum<int>(cnt, sc.red);
+            const int packed = G::template sum<int>(cnt | (ovf << 16), sc.red);
+            tot = packed & 0xffff;
+            o = packed >> 16;
         }
         bool over = false;
         if (out.row_nnz) {
-            int o;
-            if constexpr (GS == 32) o = __any_sync(kFull, ovf);
-            else o = G::template sum<int>(ovf, sc.red);
             over = o != 0 || tot > n_exp;
             if (t == 0) out.row_nnz[i] = over ? -1 : tot;
             n_exp = tot;
@@ -142,12 +147,13 @@ __device__ __forceinline__ int nth_set_bit(unsigned x, int n) {
 
 template <typename V, int NT>
 __global__ void __launch_bounds__(NT) k_num_window(Operands<V> op, const int *rows, int count, int nw, int cpc,
-                                                   int subs_per_win, WinCount wc, NumOutT<V> out,
+                                                   int subs_per_win, WinCount wc, WinArena ar, NumOutT<V> out,
                                                    unsigned long long *token, int *err) {
+    const bool arena = ar.ci != nullptr;
     constexpr int kWarps = NT / 32;
     constexpr int kMaxChunks = kMaxWinCols / 1024;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ long long s_item;
+    __shared__ long long s_item, s_aoff;
     __shared__ int s_off, s_cnt;
     __shared__ int s_chunk[kMaxChunks + 1];
     const int words = cpc >> 5;
@@ -168,20 +174,28 @@ __global__ void __launch_bounds__(NT) k_num_window(Operands<V> op, const int *ro
         const int r = (int)(item / nw);
         const int w = (int)(item - (int64_t)r * nw);
         const int i = rows[r];
-        const int slot = wc.wslot[i];
-        bool skip = out.row_nnz && out.row_nnz[i] < 0;   // capacity mode: the row overflowed
-        if (!skip && slot < 0) {
-            if (t == 0) raise_err(err, kErrCountMismatch);
-            skip = true;
-        }
+        // capacity mode: skip a row that overflowed. In arena mode other blocks
+        // update row_nnz[i] meanwhile: one thread reads it for the whole block.
+        if (t == 0) s_off = (out.row_nnz && out.row_nnz[i] < 0) ? 1 : 0;
+        __syncthreads();
+        bool skip = s_off != 0;
+        __syncthreads();
+        int slot = -1;
         int64_t c0 = 0;
         int n_exp = 0;
-        if (!skip && !out_range(out, i, c0, n_exp, err)) skip = true;
+        if (!arena) {
+            slot = wc.wslot[i];
+            if (!skip && slot < 0) {
+                if (t == 0) raise_err(err, kErrCountMismatch);
+                skip = true;
+            }
+            if (!skip && !out_range(out, i, c0, n_exp, err)) skip = true;
+        }
         if (skip) {
             __syncthreads();
             continue;
         }
-        if (wp == 0) {
+        if (!arena && wp == 0) {
             const uint16_t *sub = wc.wcnt + (size_t)slot * wc.nsub;
             const int s_lo = w * subs_per_win;
             const int s_hi = min(s_lo + subs_per_win, wc.nsub);
@@ -235,9 +249,29 @@ __global__ void __launch_bounds__(NT) k_num_window(Operands<V> op, const int *ro
         }
         __syncthreads();
         const int total = s_chunk[nch];
-        const int base = s_off;
-        if (t == 0 && total != s_cnt) raise_err(err, kErrCountMismatch);
-        const bool ok = total == s_cnt && (int64_t)base + total <= (int64_t)n_exp;
+        int base = 0;
+        bool ok;
+        if (arena) {
+            // reserve the window's room in the arena
+            if (t == 0) {
+                const long long off = (long long)atomicAdd(ar.top, (unsigned long long)total);
+                const bool fits = off + total <= ar.cap;
+                s_aoff = fits ? off : -1;
+                ar.desc_off[item] = fits ? off : -1;
+                ar.desc_cnt[item] = total;
+                if (fits) atomicAdd(out.row_nnz + i, total);
+                else atomicOr(out.row_nnz + i, INT_MIN);
+            }
+            __syncthreads();
+            ok = s_aoff >= 0;
+            c0 = ok ? s_aoff : 0;
+        } else {
+            base = s_off;
+            if (t == 0 && total != s_cnt) raise_err(err, kErrCountMismatch);
+            ok = total == s_cnt && (int64_t)base + total <= (int64_t)n_exp;
+        }
+        int32_t *dst_ci = arena ? ar.ci : out.c_ci;
+        V *dst_val = arena ? (V *)ar.val : out.c_val;
         for (int c = wp; c < nch; c += kWarps) {
             const int x = 32 * c + lane;
             const unsigned word = x < wwords ? bm[x] : 0u;
@@ -255,8 +289,8 @@ __global__ void __launch_bounds__(NT) k_num_window(Operands<V> op, const int *ro
                         acc[col] = V(0);
                         const int64_t pos = cb + pre + __popc(wq & lanemask_lt());
                         if (ok) {
-                            out.c_ci[pos] = lo + col;
-                            out.c_val[pos] = v;
+                            dst_ci[pos] = lo + col;
+                            dst_val[pos] = v;
                         }
                     }
                 }
@@ -278,8 +312,8 @@ __global__ void __launch_bounds__(NT) k_num_window(Operands<V> op, const int *ro
                         const V v = acc[col];
                         acc[col] = V(0);
                         if (ok) {
-                            out.c_ci[cb + o] = lo + col;
-                            out.c_val[cb + o] = v;
+                            dst_ci[cb + o] = lo + col;
+                            dst_val[cb + o] = v;
                         }
                     }
                 }
@@ -588,8 +622,8 @@ int num_window_cols(int dtype, int blocks_per_sm) {
 
 template <typename V, int NT>
 static void num_window_go(Operands<V> op, const BSlices &sl, const int *rows, int count, unsigned long long *token,
-                          const HashLaunch &hl, const WinCount &wc, const NumOutT<V> &out, int *err,
-                          cudaStream_t s) {
+                          const HashLaunch &hl, const WinCount &wc, const WinArena &ar, const NumOutT<V> &out,
+                          int *err, cudaStream_t s) {
     int cpc = sl.cpc;
     int subs = cpc / kSubCols;
     if (sl.nslices <= 1) {
@@ -607,29 +641,94 @@ static void num_window_go(Operands<V> op, const BSlices &sl, const int *rows, in
     const int nw = sl.nslices <= 1 ? 1 : sl.nslices;
     const long long items = (long long)count * nw;
     const int grid = resident_grid(kern, NT, smem, hl.sms, items);
-    kern<<<grid, NT, smem, s>>>(op, rows, count, nw, cpc, subs, wc, out, token, err);
+    kern<<<grid, NT, smem, s>>>(op, rows, count, nw, cpc, subs, wc, ar, out, token, err);
 }
 
 template <typename V>
 static void num_window_typed(const RawOperands &r, const int *rows, int count, unsigned long long *token,
-                             const HashLaunch &hl,
-                             const BSlices &sl, const WinCount &wc, const NumOut &o, int *err, cudaStream_t s) {
+                             const HashLaunch &hl, const BSlices &sl, const WinCount &wc, const WinArena &ar,
+                             const NumOut &o, int *err, cudaStream_t s) {
     const Operands<V> op = num_operands<V>(r);
     const NumOutT<V> out = num_out<V>(o);
     switch (window_threads(hl.dense_blocks)) {
-        case 1024: num_window_go<V, 1024>(op, sl, rows, count, token, hl, wc, out, err, s); break;
-        case 512: num_window_go<V, 512>(op, sl, rows, count, token, hl, wc, out, err, s); break;
-        default: num_window_go<V, 256>(op, sl, rows, count, token, hl, wc, out, err, s); break;
+        case 1024: num_window_go<V, 1024>(op, sl, rows, count, token, hl, wc, ar, out, err, s); break;
+        case 512: num_window_go<V, 512>(op, sl, rows, count, token, hl, wc, ar, out, err, s); break;
+        default: num_window_go<V, 256>(op, sl, rows, count, token, hl, wc, ar, out, err, s); break;
     }
 }
 
 void launch_num_window(int dtype, const RawOperands &r, const int *rows, int count, unsigned long long *token,
-                       const HashLaunch &hl, const BSlices &sl, const WinCount &wc, const NumOut &out, int *err,
-                       cudaStream_t s) {
+                       const HashLaunch &hl, const BSlices &sl, const WinCount &wc, const WinArena &ar,
+                       const NumOut &out, int *err, cudaStream_t s) {
     if (count <= 0) return;
     cudaMemsetAsync(token, 0, sizeof(unsigned long long), s);
-    if (dtype) num_window_typed<double>(r, rows, count, token, hl, sl, wc, out, err, s);
-    else num_window_typed<float>(r, rows, count, token, hl, sl, wc, out, err, s);
+    if (dtype) num_window_typed<double>(r, rows, count, token, hl, sl, wc, ar, out, err, s);
+    else num_window_typed<float>(r, rows, count, token, hl, sl, wc, ar, out, err, s);
+}
+
+// One warp per (row, window) item of the arena rows: the window's columns go
+// to C after those of the row's earlier windows.
+template <typename V>
+__global__ void __launch_bounds__(256) k_arena_compact(const int *rows, int count, int nw, WinArena ar,
+                                                       const uint8_t *ovf, const int64_t *c_rp, int32_t *c_ci,
+                                                       V *c_val) {
+    const int lane = lane_id();
+    const int64_t items = (int64_t)count * nw;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += warps) {
+        const int r = (int)(it / nw);
+        const int w = (int)(it - (int64_t)r * nw);
+        const int i = rows[r];
+        if (ovf[i] != 2) continue;
+        int before = 0;
+        for (int q = lane; q < w; q += 32) before += ar.desc_cnt[(int64_t)r * nw + q];
+        before = warp_sum(before);
+        const int n = ar.desc_cnt[it];
+        const int64_t src = ar.desc_off[it];
+        const int64_t dst = c_rp[i] + before;
+        // read-only sources (no aliasing with C): several loads in flight
+        const int32_t *__restrict__ sci = ar.ci + src;
+        const V *__restrict__ sv = (const V *)ar.val + src;
+        int32_t *__restrict__ dci = c_ci + dst;
+        V *__restrict__ dv = c_val + dst;
+#pragma unroll 4
+        for (int k = lane; k < n; k += 32) {
+            dci[k] = __ldg(sci + k);
+            dv[k] = __ldg(sv + k);
+        }
+    }
+}
+
+void launch_arena_compact(int dtype, const int *rows, int count, int nw, const WinArena &ar, const uint8_t *ovf,
+                          const int64_t *c_rp, int32_t *c_ci, void *c_val, int sms, cudaStream_t s) {
+    if (count <= 0) return;
+    const int64_t items = (int64_t)count * nw;
+    const int64_t blocks = (items + 7) / 8;
+    const int64_t cap = (int64_t)sms * 8;
+    const int grid = (int)(blocks < cap ? blocks : cap);
+    if (dtype) k_arena_compact<double><<<grid, 256, 0, s>>>(rows, count, nw, ar, ovf, c_rp, c_ci, (double *)c_val);
+    else k_arena_compact<float><<<grid, 256, 0, s>>>(rows, count, nw, ar, ovf, c_rp, c_ci, (float *)c_val);
+}
+
+__global__ void k_mark_rows(const int *rows, int count, const int *row_nnz, uint8_t *ovf) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < count) {
+        const int i = rows[r];
+        if (row_nnz[i] >= 0) ovf[i] = 2;
+    }
+}
+
+void launch_mark_rows(const int *rows, int count, const int *row_nnz, uint8_t *ovf, cudaStream_t s) {
+    if (count > 0) k_mark_rows<<<(count + 255) / 256, 256, 0, s>>>(rows, count, row_nnz, ovf);
+}
+
+__global__ void k_zero_rows(const int *rows, int count, int *a) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < count) a[rows[r]] = 0;
+}
+
+void launch_zero_rows(const int *rows, int count, int *a, cudaStream_t s) {
+    if (count > 0) k_zero_rows<<<(count + 255) / 256, 256, 0, s>>>(rows, count, a);
 }
 
 int num_spill_grid(int dtype, const HashLaunch &hl) {

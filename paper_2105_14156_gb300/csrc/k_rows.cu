@@ -6,8 +6,11 @@
 // on that count. Rows are then grouped by the table size they need, so that one
 // kernel launch serves rows of similar cost (the GPU counterpart of packing
 // rows into windows sized to the scratchpad).
+#include <climits>
+
 #include "device_common.cuh"
 #include "kernels.h"
+#include "mlp.cuh"
 
 namespace smash {
 
@@ -72,26 +75,16 @@ struct RowStats {
     }
 };
 
-// Bins the warp's valid rows (one per lane) and adds them to the block's
-// statistics. Called by all 32 lanes.
-__device__ __forceinline__ void bin_rows(bool valid, int64_t i, int64_t len, long long f, const RawOperands &op,
-                                         const int64_t *c_rp, int64_t c_nnz, const BinRule &rule, BinBuffers &bb,
-                                         long long *bound_out, int *nnz_out, int *err, RowStats &st) {
+// Bins the warp's valid rows (one per lane) by `size` and adds them to the
+// block's statistics. Called by all 32 lanes.
+__device__ __forceinline__ void bin_rows(bool valid, int64_t i, int64_t len, long long f, long long size,
+                                         const BinRule &rule, BinBuffers &bb, int *nnz_out, RowStats &st) {
     const int lane = lane_id();
-    long long size = 0;
     int b = kBinEmpty;
     if (valid) {
-        if (c_rp) {
-            const int64_t s = c_rp[i], t = c_rp[i + 1];
-            if (s < 0 || t < s || t > c_nnz) raise_err(err, kErrBadRowPtr);
-            else size = t - s;
-        } else {
-            size = f < (long long)op.ncols ? f : (long long)op.ncols;
-            bound_out[i] = size;
-        }
         b = bin_for(size, rule);
         bb.bin[i] = (uint8_t)b;
-        if (!c_rp && b == kBinEmpty) nnz_out[i] = 0;
+        if (nnz_out && b == kBinEmpty) nnz_out[i] = 0;
     }
     const long long wp = warp_sum(valid ? f : 0ll);
     const long long wm = warp_max(valid ? f : 0ll);
@@ -118,11 +111,62 @@ __device__ __forceinline__ void bin_rows(bool valid, int64_t i, int64_t len, lon
     }
 }
 
+// Size that bins row i: symbolic phase: the bound min(flop_i, cols(B))
+// (written to bound_out); numeric phase: c_rp's row length.
+__device__ __forceinline__ long long row_size(int64_t i, long long f, const RawOperands &op, const int64_t *c_rp,
+                                              int64_t c_nnz, long long *bound_out, int *err) {
+    if (c_rp) {
+        const int64_t s = c_rp[i], t = c_rp[i + 1];
+        if (s < 0 || t < s || t > c_nnz) {
+            raise_err(err, kErrBadRowPtr);
+            return 0;
+        }
+        return t - s;
+    }
+    const long long ub = f < (long long)op.ncols ? f : (long long)op.ncols;
+    bound_out[i] = ub;
+    return ub;
+}
+
+// Learned planning, second pass: one warp per 32 rows through the predictor
+// (mlp_forward_warp), capacity cap_i = cap_of(y_i, margin, min(flop_i,
+// cols(B))), bin of the row by cap_i.
+__global__ void __launch_bounds__(256) k_learned_bin(RawOperands op, BinRule rule, BinBuffers bb, LearnArgs la,
+                                                     int64_t nrows) {
+    __shared__ RowStats st;
+    extern __shared__ __align__(16) float s_mlp[];   // the predictor's weights (mlp.cuh)
+    st.init();
+    load_mlp_tc(s_mlp, (const __nv_bfloat16 *)la.wb, la.norm);
+    __syncthreads();
+    const int lane = lane_id();
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (int64_t base = gw * 32; base < nrows; base += warps * 32) {
+        const int64_t i = base + lane;
+        const bool valid = i < nrows;
+        RowGather rg{0, 0, 0};
+        if (valid) rg = la.gather[i];
+        float x[kFeat];
+        row_features(rg.na, rg.f, rg.mx, op.ncols, x);
+        const float y = mlp_forward_warp(s_mlp, x, (uint32_t *)(s_mlp + kSmH1) + (threadIdx.x >> 5) * kH1Words);
+        long long size = 0;
+        if (valid) {
+            const long long ub = rg.f < (long long)op.ncols ? rg.f : (long long)op.ncols;
+            size = cap_of(y, la.margin, ub);
+            la.cap[i] = (int)size;
+        }
+        bin_rows(valid, i, rg.na, rg.f, size, rule, bb, nullptr, st);
+    }
+    __syncthreads();
+    st.flush(bb);
+}
+
 // Short rows: one thread per row. Long rows: appended to long_list.
+template <bool LEARN>
 __global__ void __launch_bounds__(256) k_rowinfo(RawOperands op, const int64_t *c_rp, int64_t c_nnz, BinRule rule,
                                                  BinBuffers bb, long long *bound_out, int *nnz_out, int *err,
                                                  const int *row_list, int64_t nrows, int *long_list,
-                                                 unsigned long long *long_count) {
+                                                 unsigned long long *long_count, LearnArgs la) {
     __shared__ RowStats st;
     st.init();
     __syncthreads();
@@ -151,20 +195,33 @@ __global__ void __launch_bounds__(256) k_rowinfo(RawOperands op, const int64_t *
             if (longrow) long_list[at + __popc(lm & lanemask_lt())] = (int)i;
         }
         valid = valid && !longrow;
-        long long f = 0;
+        long long f = 0, mx = 0;
 #pragma unroll 4
-        for (int64_t e = ab; e < (longrow ? ab : ae); ++e) f += b_row_len(op, __ldg(op.a_ci + e), err);
-        bin_rows(valid, i, ae - ab, f, op, c_rp, c_nnz, rule, bb, bound_out, nnz_out, err, st);
+        for (int64_t e = ab; e < (longrow ? ab : ae); ++e) {
+            const long long l = b_row_len(op, __ldg(op.a_ci + e), err);
+            f += l;
+            mx = l > mx ? l : mx;
+        }
+        if constexpr (LEARN) {
+            // learned planning: only the row's flop count and longest row of B
+            // here; k_learned_bin runs the predictor and bins the rows
+            if (valid) la.gather[i] = RowGather{f, (int)(ae - ab), (int)(mx < INT_MAX ? mx : INT_MAX)};
+        } else {
+            long long size = 0;
+            if (valid) size = row_size(i, f, op, c_rp, c_nnz, bound_out, err);
+            bin_rows(valid, i, ae - ab, f, size, rule, bb, c_rp ? nullptr : nnz_out, st);
+        }
     }
     __syncthreads();
     st.flush(bb);
 }
 
 // The long rows: one warp per row.
+template <bool LEARN>
 __global__ void __launch_bounds__(256) k_rowinfo_long(RawOperands op, const int64_t *c_rp, int64_t c_nnz,
                                                       BinRule rule, BinBuffers bb, long long *bound_out, int *nnz_out,
                                                       int *err, const int *long_list,
-                                                      const unsigned long long *long_count) {
+                                                      const unsigned long long *long_count, LearnArgs la) {
     __shared__ RowStats st;
     st.init();
     __syncthreads();
@@ -174,11 +231,22 @@ __global__ void __launch_bounds__(256) k_rowinfo_long(RawOperands op, const int6
     for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < n; q += warps) {
         const int64_t i = long_list[q];
         const int64_t ab = __ldg(op.a_rp + i), ae = __ldg(op.a_rp + i + 1);   // checked by k_rowinfo
-        long long f = 0;
+        long long f = 0, mx = 0;
 #pragma unroll 4
-        for (int64_t e = ab + lane; e < ae; e += 32) f += b_row_len(op, __ldg(op.a_ci + e), err);
+        for (int64_t e = ab + lane; e < ae; e += 32) {
+            const long long l = b_row_len(op, __ldg(op.a_ci + e), err);
+            f += l;
+            mx = l > mx ? l : mx;
+        }
         f = warp_sum(f);
-        bin_rows(lane == 0, i, ae - ab, f, op, c_rp, c_nnz, rule, bb, bound_out, nnz_out, err, st);
+        mx = warp_max(mx);
+        if constexpr (LEARN) {
+            if (lane == 0) la.gather[i] = RowGather{f, (int)(ae - ab), (int)(mx < INT_MAX ? mx : INT_MAX)};
+        } else {
+            long long size = 0;
+            if (lane == 0) size = row_size(i, f, op, c_rp, c_nnz, bound_out, err);
+            bin_rows(lane == 0, i, ae - ab, f, size, rule, bb, c_rp ? nullptr : nnz_out, st);
+        }
     }
     __syncthreads();
     st.flush(bb);
@@ -320,33 +388,55 @@ static int rowinfo_grid(int64_t rows, int sms) {
 
 // bb.rows (filled later by the bin scatter) holds the long-row list meanwhile;
 // bb.stats[2] counts it.
+template <bool LEARN>
 static void rowinfo(const RawOperands &op, const int64_t *c_rp, int64_t c_nnz, const BinRule &rule, BinBuffers bb,
                     long long *bound_out, int *nnz_out, int *err, int sms, cudaStream_t s, const int *row_list,
-                    int64_t n) {
+                    int64_t n, const LearnArgs &la = LearnArgs{}) {
     unsigned long long *lc = (unsigned long long *)(bb.stats + 2);
-    k_rowinfo<<<rowinfo_grid(n, sms), 256, 0, s>>>(op, c_rp, c_nnz, rule, bb, bound_out, nnz_out, err, row_list, n,
-                                                    bb.rows, lc);
+    k_rowinfo<LEARN><<<rowinfo_grid(n, sms), 256, 0, s>>>(op, c_rp, c_nnz, rule, bb, bound_out, nnz_out, err,
+                                                             row_list, n, bb.rows, lc, la);
     // at most min(n, nnz(A) / (kLongRow + 1)) long rows, 8 per block
     int64_t most = op.a_nnz / (kLongRow + 1) + 1;
     if (most > n) most = n;
     const int64_t blocks = (most + 7) / 8;
     const int64_t cap = (int64_t)sms * 8;
-    k_rowinfo_long<<<(int)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap), 256, 0, s>>>(
-        op, c_rp, c_nnz, rule, bb, bound_out, nnz_out, err, bb.rows, lc);
+    k_rowinfo_long<LEARN><<<(int)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap), 256, 0, s>>>(
+        op, c_rp, c_nnz, rule, bb, bound_out, nnz_out, err, bb.rows, lc, la);
+}
+
+void launch_learned_gather(const RawOperands &op, const BinRule &rule, BinBuffers bb, const LearnArgs &la,
+                           int *err, int sms, cudaStream_t s) {
+    if (op.a_rows == 0) return;
+    rowinfo<true>(op, nullptr, 0, rule, bb, nullptr, nullptr, err, sms, s, nullptr, op.a_rows, la);
+}
+
+void launch_learned_bin(const RawOperands &op, const BinRule &rule, BinBuffers bb, const LearnArgs &la, int sms,
+                        cudaStream_t s) {
+    if (op.a_rows == 0) return;
+    const int64_t blocks = (op.a_rows + 255) / 256;
+    const int64_t cap = (int64_t)sms * 4;
+    static bool attr = false;
+    const size_t smem = (size_t)mlp_tc_words(256 / 32) * 4;
+    if (!attr) {
+        cudaFuncSetAttribute(k_learned_bin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    k_learned_bin<<<(int)(blocks < cap ? blocks : cap), 256, smem, s>>>(
+        op, rule, bb, la, op.a_rows);
 }
 
 void launch_sym_rowinfo(const RawOperands &op, const BinRule &rule, BinBuffers bb, long long *bound_out,
                         int *nnz_out, int *err, int sms, cudaStream_t s, const int *row_list, int64_t list_n) {
     const int64_t n = row_list ? list_n : op.a_rows;
     if (n == 0) return;
-    rowinfo(op, nullptr, 0, rule, bb, bound_out, nnz_out, err, sms, s, row_list, n);
+    rowinfo<false>(op, nullptr, 0, rule, bb, bound_out, nnz_out, err, sms, s, row_list, n);
 }
 
 void launch_num_rowinfo(const RawOperands &op, const int64_t *c_rp, int64_t c_nnz, const BinRule &rule,
                         BinBuffers bb, int *err, int sms, cudaStream_t s, const int *row_list, int64_t list_n) {
     const int64_t n = row_list ? list_n : op.a_rows;
     if (n == 0) return;
-    rowinfo(op, c_rp, c_nnz, rule, bb, nullptr, nullptr, err, sms, s, row_list, n);
+    rowinfo<false>(op, c_rp, c_nnz, rule, bb, nullptr, nullptr, err, sms, s, row_list, n);
 }
 
 // Rows whose staged result did not fit (row_nnz < 0): appended to list.

@@ -49,6 +49,27 @@ void launch_sym_rowinfo(const RawOperands &op, const BinRule &rule, BinBuffers b
 void launch_num_rowinfo(const RawOperands &op, const int64_t *c_rp, int64_t c_nnz, const BinRule &rule,
                         BinBuffers bb, int *err, int sms, cudaStream_t s, const int *row_list = nullptr,
                         int64_t list_n = 0);
+// Learned planning (k_rows.cu): features, the predictor and each row's
+// capacity cap_i (mlp.cuh) in the planning passes; rows binned by cap_i.
+// Two passes: the rows' flop counts and longest rows of B (gather, one row
+// per thread, long rows per warp), then the predictor on the tensor cores
+// and the bins.
+struct RowGather {
+    long long f;   // flop_i
+    int na;        // nnz(A_i)
+    int mx;        // longest selected row of B
+};
+struct LearnArgs {
+    const void *wb = nullptr;     // bf16 weights (device)
+    const float *norm = nullptr;  // mean[6], inv_std[6] (device)
+    float margin = 0.f;
+    int *cap = nullptr;           // out: capacity per row
+    RowGather *gather = nullptr;  // scratch: one per row
+};
+void launch_learned_gather(const RawOperands &op, const BinRule &rule, BinBuffers bb, const LearnArgs &la,
+                           int *err, int sms, cudaStream_t s);
+void launch_learned_bin(const RawOperands &op, const BinRule &rule, BinBuffers bb, const LearnArgs &la, int sms,
+                        cudaStream_t s);
 // Learned path helpers (k_rows.cu): rows with row_nnz < 0 -> list; copy the
 // staged rows that fitted into C.
 void launch_overflow_list(const int *row_nnz, int64_t n, int *list, int *count, uint8_t *ovf, cudaStream_t s);
@@ -148,11 +169,31 @@ void launch_window_plan(int dtype, const RawOperands &op, int nw, int cpc, void 
 // numeric dense kernel at `blocks_per_sm` resident blocks per SM; 0: none.
 constexpr int kMaxWinCols = 65536;
 int num_window_cols(int dtype, int blocks_per_sm);
-// (row, window) work items of the dense rows; counts from wc; token: a
-// 64-bit item counter (zeroed here).
+// Arena mode of the dense kernel (learned path, capacity mode): no counts;
+// each (row, window) item reserves room for its columns in one arena by an
+// atomic add on *top, writes them there in order and records (offset, count)
+// in desc_off / desc_cnt[item]; out.row_nnz[i] accumulates the row's total,
+// or gets its sign bit set when the arena ran out (the row falls back).
+struct WinArena {
+    unsigned long long *top = nullptr;
+    int64_t cap = 0;            // entries
+    int32_t *ci = nullptr;
+    void *val = nullptr;
+    int64_t *desc_off = nullptr;
+    int *desc_cnt = nullptr;
+};
+// (row, window) work items of the dense rows; counts from wc (or arena mode
+// when ar.ci != nullptr); token: a 64-bit item counter (zeroed here).
 void launch_num_window(int dtype, const RawOperands &op, const int *rows, int count, unsigned long long *token,
-                       const HashLaunch &hl, const BSlices &sl, const WinCount &wc, const NumOut &out, int *err,
-                       cudaStream_t s);
+                       const HashLaunch &hl, const BSlices &sl, const WinCount &wc, const WinArena &ar,
+                       const NumOut &out, int *err, cudaStream_t s);
+// Copies the arena rows (ovf[i] == 2) of the dense bin into C.
+void launch_arena_compact(int dtype, const int *rows, int count, int nw, const WinArena &ar, const uint8_t *ovf,
+                          const int64_t *c_rp, int32_t *c_ci, void *c_val, int sms, cudaStream_t s);
+// ovf[i] = 2 for the listed rows with row_nnz[i] >= 0.
+void launch_mark_rows(const int *rows, int count, const int *row_nnz, uint8_t *ovf, cudaStream_t s);
+// a[rows[r]] = 0 for r < count.
+void launch_zero_rows(const int *rows, int count, int *a, cudaStream_t s);
 int num_spill_grid(int dtype, const HashLaunch &hl);
 void launch_num_spill(int dtype, const RawOperands &op, const int *rows, int count, int *token,
                       const HashLaunch &hl, float inv_load, int spill_tbits, void *tables,

@@ -352,12 +352,12 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
     const RawOperands op = raw_ops(A, B);
     int *err = (int *)h->err.ptr;
     // the dense rows of this call are counted by this call (no reuse of an
-    // earlier symbolic phase's counts)
+    // earlier symbolic phase's counts), and B is sliced afresh
     h->wcache.valid = false;
+    h->plan_cache.valid = false;
     // per-row arrays
     size_t need = 0;
-    carve_size<float>(need, (size_t)n * 6);
-    carve_size<long long>(need, (size_t)n);       // bound
+    carve_size<RowGather>(need, (size_t)n);       // planning scratch
     carve_size<int>(need, (size_t)n);             // cap
     carve_size<int64_t>(need, (size_t)n + 1);     // stage_rp
     carve_size<int>(need, (size_t)n);             // row_nnz
@@ -367,8 +367,7 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
     carve_size<char>(need, scan_scratch_bytes(n));
     if ((st = ensure(h, h->learn, need, s))) return st;
     Carver c(h->learn.ptr);
-    float *feats = c.take<float>((size_t)n * 6);
-    long long *bound = c.take<long long>((size_t)n);
+    RowGather *gather = c.take<RowGather>((size_t)n);
     int *cap = c.take<int>((size_t)n);
     int64_t *stage_rp = c.take<int64_t>((size_t)n + 1);
     int *row_nnz = c.take<int>((size_t)n);
@@ -378,14 +377,63 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
     void *scan = c.take<char>(scan_scratch_bytes(n));
     cudaMemsetAsync(ctr, 0, 4 * sizeof(long long), s);
     cudaMemsetAsync(row_nnz, 0, sizeof(int) * (size_t)n, s);
-    // 1-3. features, predicted capacities, staging layout
+    // 1. one planning pass: features, predicted capacity, bin of every row
+    Plan pl;
+    if ((st = plan_buffers(h, n, false, s, pl))) return st;
     {
-        LaunchTimer lt(h, s, "features", -1, 256, n, A->nnz, 0, 0);
-        launch_features(op, nullptr, n, feats, bound, err, h->sms, s);
+        LearnArgs la;
+        la.wb = m->wb;
+        la.norm = m->norm;
+        la.margin = margin;
+        la.cap = cap;
+        la.gather = gather;
+        const BinRule rule = num_rule(h, op.ncols, dt);
+        {
+            LaunchTimer lt(h, s, "learned_gather", -1, 256, n, A->nnz, 0, 0, 2);
+            launch_learned_gather(op, rule, pl.bb, la, err, h->sms, s);
+        }
+        LaunchTimer lt(h, s, "learned_bin", -1, 256, n, 0, 0, 0);
+        launch_learned_bin(op, rule, pl.bb, la, h->sms, s);
     }
     {
-        LaunchTimer lt(h, s, "mlp_infer", -1, 256, n, 0, 0, 0);
-        launch_mlp_infer(feats, bound, nullptr, n, m->wb, m->norm, margin, nullptr, cap, h->sms, s);
+        LaunchTimer lt(h, s, "bin_scatter", -1, 256, n, 0, 0, 0);
+        launch_bin_scatter(n, pl.bb, s);
+    }
+    if ((st = last_cuda_status())) return st;
+    BinPlan bp;
+    if ((st = fetch_bins(h, pl, s, bp.counts, bp.offsets, bp.maxsize, bp.stats, bp.sums))) return st;
+    // 2. dense rows with column windows write into an arena sized by their
+    //    predicted capacities; the other rows get staging ranges
+    const int nd = bp.counts[kBinDense];
+    const int *drows = pl.bb.rows + bp.offsets[kBinDense];   // valid until the next plan_buffers()
+    int cpc = 0, nw = 0;
+    const bool use_arena = nd > 0 && dense_windows(h, op, dt, bp.sums[16 + kBinDense], cpc, nw);
+    WinArena ar;
+    const int *arena_rows = nullptr;
+    if (use_arena) {
+        ar.cap = bp.sums[32 + kBinDense] > 0 ? bp.sums[32 + kBinDense] : 1;
+        size_t aneed = 0;
+        carve_size<unsigned long long>(aneed, 1);
+        carve_size<int32_t>(aneed, (size_t)ar.cap);
+        carve_size<char>(aneed, (size_t)ar.cap * vsz);
+        carve_size<int64_t>(aneed, (size_t)nd * nw);
+        carve_size<int>(aneed, (size_t)nd * nw);
+        carve_size<int>(aneed, (size_t)nd);
+        if ((st = ensure(h, h->arena, aneed, s))) return st;
+        Carver ac(h->arena.ptr);
+        ar.top = ac.take<unsigned long long>(1);
+        ar.ci = ac.take<int32_t>((size_t)ar.cap);
+        ar.val = ac.take<char>((size_t)ar.cap * vsz);
+        ar.desc_off = ac.take<int64_t>((size_t)nd * nw);
+        ar.desc_cnt = ac.take<int>((size_t)nd * nw);
+        // the dense rows' list outlives the plan buffers (the fallback's plans
+        // reuse them before the arena is compacted)
+        int *dcopy = ac.take<int>((size_t)nd);
+        if (cudaMemcpyAsync(dcopy, drows, sizeof(int) * (size_t)nd, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return SMASH_ERR_CUDA;
+        arena_rows = dcopy;
+        cudaMemsetAsync(ar.top, 0, sizeof(unsigned long long), s);
+        launch_zero_rows(drows, nd, cap, s);
     }
     {
         LaunchTimer lt(h, s, "scan_rowptr", -1, 512, n, 0, 0, 0, 3);
@@ -396,7 +444,7 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
         cudaStreamSynchronize(s) != cudaSuccess)
         return SMASH_ERR_CUDA;
     const long long staged = h->host[0];
-    ls.staged_nnz = staged;
+    ls.staged_nnz = staged + (use_arena ? ar.cap : 0);
     size_t sneed = 0;
     carve_size<int32_t>(sneed, (size_t)staged);
     carve_size<char>(sneed, (size_t)staged * vsz);
@@ -404,20 +452,19 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
     Carver sc(h->stage.ptr);
     int32_t *stage_ci = sc.take<int32_t>((size_t)staged);
     void *stage_val = sc.take<char>((size_t)staged * vsz);
-    // 4. one hashing pass with predicted capacities
-    Plan pl;
-    if ((st = plan_buffers(h, n, false, s, pl))) return st;
+    // 3. one hashing pass with predicted capacities
     NumOut so;
     so.c_rp = stage_rp;
     so.c_ci = stage_ci;
     so.c_val = stage_val;
     so.c_nnz = staged;
     so.row_nnz = row_nnz;
-    if ((st = run_numeric(h, op, n, dt, so, pl, s, nullptr, 0))) return st;
-    // 5. rows that did not fit
+    if ((st = run_bins(h, op, n, dt, so, pl, bp, s, use_arena ? &ar : nullptr))) return st;
+    // 4. rows that did not fit
     {
         LaunchTimer lt(h, s, "overflow_list", -1, 256, n, 0, 0, 0);
         launch_overflow_list(row_nnz, n, list, (int *)(ctr + 1), ovf, s);
+        if (use_arena) launch_mark_rows(arena_rows, nd, row_nnz, ovf, s);
     }
     if (cudaMemcpyAsync(h->host, ctr + 1, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
@@ -429,7 +476,7 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
         if ((st = plan_buffers(h, n, true, s, ps))) return st;
         if ((st = run_symbolic(h, op, n, ps, row_nnz, s, list, novf))) return st;
     }
-    // 6. exact row pointer of C, then its arrays
+    // 5. exact row pointer of C, then its arrays
     {
         LaunchTimer lt(h, s, "scan_rowptr", -1, 512, n, 0, 0, 0, 3);
         launch_scan_rowptr(row_nnz, n, C->row_ptr, ctr + 2, scan, s);
@@ -448,6 +495,10 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
             LaunchTimer lt(h, s, "compact_rows", -1, 256, n, 0, 0, cnnz);
             launch_compact_rows(dt, n, stage_rp, row_nnz, ovf, stage_ci, stage_val, C->row_ptr, C->col_idx, C->val,
                                 cnnz, h->sms, s);
+        }
+        if (use_arena) {
+            LaunchTimer lt(h, s, "compact_arena", -1, 256, nd, 0, 0, cnnz);
+            launch_arena_compact(dt, arena_rows, nd, nw, ar, ovf, C->row_ptr, C->col_idx, C->val, h->sms, s);
         }
         if (novf > 0) {
             Plan pn;

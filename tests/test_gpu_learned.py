@@ -133,3 +133,27 @@ def test_learned_rectangular_and_empty_rows(handle, trained):
         Ch = C.to_host()
         owner.free()
         assert_matches_oracle(Ch, A, B)
+
+
+@pytest.mark.parametrize("margin", [0.15, -0.9, 3.0])
+@pytest.mark.parametrize("dense_blocks", [2, 4])
+def test_learned_dense_rows_in_arena(handle, trained, margin, dense_blocks):
+    """Dense rows of the learned path: column-window items write into the arena
+    (several windows per row); an arena too small for them (margin -0.9) sends
+    the rows to the exact fallback."""
+    from paper_2105_14156_gb300 import smash
+    from tests.helpers import random_csr
+    model, _, _ = trained
+    A = random_csr(300, 200, 0.1, 81, values="f64")
+    B = random_csr(200, 30000, 0.01, 82, values="f64")
+    defaults = handle.params.as_dict()
+    handle.set_params(dense_ratio=1 << 20, dense_blocks=dense_blocks)
+    try:
+        C, stats, owner = handle.spgemm_learned(smash.to_device(A), smash.to_device(B), model, margin=margin)
+        Ch = C.to_host()
+        owner.free()
+    finally:
+        handle.set_params(**defaults)
+    assert_matches_oracle(Ch, A, B)
+    if margin < 0:
+        assert stats["overflow_rows"] > 0
