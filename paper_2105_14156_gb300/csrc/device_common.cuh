@@ -416,19 +416,33 @@ __device__ __forceinline__ void group_products(const Operands<V> &op, int64_t ab
                     av_u[u] = V(0);
                     bv[u] = V(0);
                     if (q < hi) {
-                        const int c = c0 + lane;
-                        const int e = c < nf ? sc.incl[c] - q : INT_MAX;
-                        const int ci = c0 + step_entry(e);
                         act[u] = q + lane < hi;
-                        if (act[u]) {
-                            const int64_t idx = sc.start[ci] + q + lane;
-                            jv[u] = __ldg(op.b_ci + idx);
-                            if constexpr (NUM) {
-                                bv[u] = __ldg(op.b_val + idx);
-                                av_u[u] = sc.av[ci];
+                        const int e0 = sc.incl[c0] - q;   // same for all lanes
+                        if (e0 >= 32) {
+                            // the whole step lies in entry c0 (long rows of B)
+                            if (act[u]) {
+                                const int64_t idx = sc.start[c0] + q + lane;
+                                jv[u] = __ldg(op.b_ci + idx);
+                                if constexpr (NUM) {
+                                    bv[u] = __ldg(op.b_val + idx);
+                                    av_u[u] = sc.av[c0];
+                                }
                             }
+                            if (e0 == 32) ++c0;
+                        } else {
+                            const int c = c0 + lane;
+                            const int e = c < nf ? sc.incl[c] - q : INT_MAX;
+                            const int ci = c0 + step_entry(e);
+                            if (act[u]) {
+                                const int64_t idx = sc.start[ci] + q + lane;
+                                jv[u] = __ldg(op.b_ci + idx);
+                                if constexpr (NUM) {
+                                    bv[u] = __ldg(op.b_val + idx);
+                                    av_u[u] = sc.av[ci];
+                                }
+                            }
+                            c0 += __popc(__ballot_sync(kFull, e <= 32));
                         }
-                        c0 += __popc(__ballot_sync(kFull, e <= 32));
                     }
                 }
 #pragma unroll
