@@ -338,8 +338,9 @@ int window_plan(smash_handle *h, const RawOperands &op, int dt, int cpc, int nw,
     if ((st = ensure(h, h->split, 256 + window_plan_bytes(op, nw, vsz), s))) return st;
     (void)before;
     {
-        LaunchTimer lt(h, s, "dense_plan", -1, 256, op.b_rows, 0, 0, op.b_nnz, nw > 1 ? 2 : 0);
-        launch_window_plan(dt, op, nw, cpc, (char *)h->split.ptr + 256, sl, h->sms, s);
+        LaunchTimer lt(h, s, "dense_plan", -1, 256, op.b_rows, 0, 0, op.b_nnz, 0);
+        lt.add_kernels(launch_window_plan(dt, op, nw, cpc, (char *)h->split.ptr + 256, sl, h->sms, s,
+                                          (int *)((char *)h->host + 1536)));
     }
     pc.valid = true;
     pc.b_rp = op.b_rp;

@@ -227,6 +227,10 @@ struct LaunchTimer {
         e0 = take_event(h);
         cudaEventRecord(e0, s);
     }
+    // kernels known only once launched
+    void add_kernels(int k) {
+        if (h->timing && slot >= 0) h->totals[slot].kernels += k;
+    }
     ~LaunchTimer() {
         if (!h->timing || slot < 0) return;
         cudaEvent_t e1 = take_event(h);

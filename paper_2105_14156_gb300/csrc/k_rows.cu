@@ -216,37 +216,51 @@ __global__ void __launch_bounds__(256) k_rowinfo(RawOperands op, const int64_t *
     st.flush(bb);
 }
 
-// The long rows: one warp per row.
+// The long rows: one block per row (the longest rows of R-MAT hold tens of
+// thousands of entries; a block spreads them over 256 threads).
 template <bool LEARN>
 __global__ void __launch_bounds__(256) k_rowinfo_long(RawOperands op, const int64_t *c_rp, int64_t c_nnz,
                                                       BinRule rule, BinBuffers bb, long long *bound_out, int *nnz_out,
                                                       int *err, const int *long_list,
                                                       const unsigned long long *long_count, LearnArgs la) {
     __shared__ RowStats st;
+    __shared__ long long s_f[8], s_mx[8];
     st.init();
     __syncthreads();
     const int lane = lane_id();
+    const int wp = threadIdx.x >> 5;
     const int64_t n = (int64_t)*long_count;
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < n; q += warps) {
+    for (int64_t q = blockIdx.x; q < n; q += gridDim.x) {
         const int64_t i = long_list[q];
         const int64_t ab = __ldg(op.a_rp + i), ae = __ldg(op.a_rp + i + 1);   // checked by k_rowinfo
         long long f = 0, mx = 0;
 #pragma unroll 4
-        for (int64_t e = ab + lane; e < ae; e += 32) {
+        for (int64_t e = ab + threadIdx.x; e < ae; e += 256) {
             const long long l = b_row_len(op, __ldg(op.a_ci + e), err);
             f += l;
             mx = l > mx ? l : mx;
         }
         f = warp_sum(f);
         mx = warp_max(mx);
-        if constexpr (LEARN) {
-            if (lane == 0) la.gather[i] = RowGather{f, (int)(ae - ab), (int)(mx < INT_MAX ? mx : INT_MAX)};
-        } else {
-            long long size = 0;
-            if (lane == 0) size = row_size(i, f, op, c_rp, c_nnz, bound_out, err);
-            bin_rows(lane == 0, i, ae - ab, f, size, rule, bb, c_rp ? nullptr : nnz_out, st);
+        if (lane == 0) {
+            s_f[wp] = f;
+            s_mx[wp] = mx;
         }
+        __syncthreads();
+        if (wp == 0) {
+            f = lane < 8 ? s_f[lane] : 0;
+            mx = lane < 8 ? s_mx[lane] : 0;
+            f = warp_sum(f);
+            mx = warp_max(mx);
+            if constexpr (LEARN) {
+                if (lane == 0) la.gather[i] = RowGather{f, (int)(ae - ab), (int)(mx < INT_MAX ? mx : INT_MAX)};
+            } else {
+                long long size = 0;
+                if (lane == 0) size = row_size(i, f, op, c_rp, c_nnz, bound_out, err);
+                bin_rows(lane == 0, i, ae - ab, f, size, rule, bb, c_rp ? nullptr : nnz_out, st);
+            }
+        }
+        __syncthreads();
     }
     __syncthreads();
     st.flush(bb);
@@ -395,10 +409,10 @@ static void rowinfo(const RawOperands &op, const int64_t *c_rp, int64_t c_nnz, c
     unsigned long long *lc = (unsigned long long *)(bb.stats + 2);
     k_rowinfo<LEARN><<<rowinfo_grid(n, sms), 256, 0, s>>>(op, c_rp, c_nnz, rule, bb, bound_out, nnz_out, err,
                                                              row_list, n, bb.rows, lc, la);
-    // at most min(n, nnz(A) / (kLongRow + 1)) long rows, 8 per block
+    // at most min(n, nnz(A) / (kLongRow + 1)) long rows, one per block
     int64_t most = op.a_nnz / (kLongRow + 1) + 1;
     if (most > n) most = n;
-    const int64_t blocks = (most + 7) / 8;
+    const int64_t blocks = most;
     const int64_t cap = (int64_t)sms * 8;
     k_rowinfo_long<LEARN><<<(int)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap), 256, 0, s>>>(
         op, c_rp, c_nnz, rule, bb, bound_out, nnz_out, err, bb.rows, lc, la);

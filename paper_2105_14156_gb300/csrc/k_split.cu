@@ -4,10 +4,12 @@
 // cpc consecutive columns, window w = [w*cpc, (w+1)*cpc), and each (row,
 // window) pair is an independent work item of the numeric dense kernel, whose
 // accumulator is the window only. So that an item enumerates only the
-// products that land in its window, the entries of each row of B are
-// regrouped by window (stable within a window; a no-op reordering when the
-// row is sorted) and woff[k][0..nw] records where each window's entries
-// start, relative to the row's start.
+// products that land in its window, woff[k][0..nw] records where each
+// window's entries start in row k of B, relative to the row's start. When
+// every row of B is sorted by column the windows are contiguous already and
+// their bounds come from binary searches (B itself is the sliced copy);
+// otherwise the entries of each row are regrouped by window into a copy
+// (stable within a window).
 #include "device_common.cuh"
 #include "kernels.h"
 
@@ -103,10 +105,55 @@ __global__ void __launch_bounds__(kSplitNT) k_split_scatter(const int64_t *b_rp,
     }
 }
 
+// Any row of B with a column smaller than its predecessor sets *unsorted.
+__global__ void __launch_bounds__(256) k_check_sorted(const int64_t *b_rp, const int32_t *b_ci, int64_t b_rows,
+                                                      int64_t b_nnz, int *unsorted) {
+    const int lane = lane_id();
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    bool bad = false;
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < b_rows; k += warps) {
+        int64_t s, t;
+        b_row_ok(b_rp, k, b_nnz, s, t);
+        for (int64_t e = s + lane; e + 1 < t; e += 32) bad |= __ldg(b_ci + e) > __ldg(b_ci + e + 1);
+    }
+    if (__any_sync(kFull, bad) && lane == 0) atomicOr(unsorted, 1);
+}
+
+// Sorted rows: woff[k][w] = first entry of row k with column >= w*cpc
+// (binary search); window 0 starts at the row's start and the last window
+// ends at its end, so that out-of-range columns stay enumerated (and are
+// reported). One thread per (row, window bound).
+__global__ void __launch_bounds__(256) k_split_bsearch(const int64_t *b_rp, const int32_t *b_ci, int64_t b_rows,
+                                                       int64_t b_nnz, int cpc, int nw, int32_t *woff) {
+    const int64_t total = b_rows * (int64_t)(nw + 1);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += stride) {
+        const int64_t k = x / (nw + 1);
+        const int w = (int)(x - k * (nw + 1));
+        int64_t s, t;
+        b_row_ok(b_rp, k, b_nnz, s, t);
+        int64_t pos;
+        if (w == 0) pos = s;
+        else if (w == nw) pos = t;
+        else {
+            const int key = w * cpc;
+            int64_t lo = s, hi = t;   // first entry >= key
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (__ldg(b_ci + mid) < key) lo = mid + 1;
+                else hi = mid;
+            }
+            pos = lo;
+        }
+        woff[x] = (int32_t)(pos - s);
+    }
+}
+
 size_t window_plan_bytes(const RawOperands &op, int nw, size_t vsz) {
     size_t b = 0;
     auto add = [&](size_t n) { b = ((b + 255) & ~size_t(255)) + n; };
     if (nw > 1) {
+        add(sizeof(int));                       // unsorted flag
         add(4 * (size_t)op.b_rows * (nw + 1));  // woff
         add(4 * (size_t)op.b_nnz);              // ci
         add(vsz * (size_t)op.b_nnz);            // val
@@ -114,14 +161,14 @@ size_t window_plan_bytes(const RawOperands &op, int nw, size_t vsz) {
     return b + 256;
 }
 
-void launch_window_plan(int dtype, const RawOperands &op, int nw, int cpc, void *ws, BSlices &sl, int sms,
-                        cudaStream_t s) {
+int launch_window_plan(int dtype, const RawOperands &op, int nw, int cpc, void *ws, BSlices &sl, int sms,
+                       cudaStream_t s, int *host_word) {
     sl.nslices = nw;
     sl.cpc = cpc;
     sl.woff = nullptr;
     sl.ci = nullptr;
     sl.val = nullptr;
-    if (nw <= 1 || op.b_rows <= 0) return;
+    if (nw <= 1 || op.b_rows <= 0) return 0;
     const size_t vsz = dtype ? 8 : 4;
     char *p = (char *)ws;
     size_t off = 0;
@@ -131,12 +178,28 @@ void launch_window_plan(int dtype, const RawOperands &op, int nw, int cpc, void 
         off += n;
         return r;
     };
+    int *unsorted = (int *)take(sizeof(int));
     int32_t *woff = (int32_t *)take(4 * (size_t)op.b_rows * (nw + 1));
     int32_t *sci = (int32_t *)take(4 * (size_t)op.b_nnz);
     void *sval = take(vsz * (size_t)op.b_nnz);
     const int64_t cap_blocks = (int64_t)sms * 8;
     const int64_t blocks = (op.b_rows + kSplitWarps - 1) / kSplitWarps;
     const int grid = (int)(blocks < cap_blocks ? blocks : cap_blocks);
+    // sorted rows of B need no copy
+    cudaMemsetAsync(unsorted, 0, sizeof(int), s);
+    k_check_sorted<<<grid, kSplitNT, 0, s>>>(op.b_rp, op.b_ci, op.b_rows, op.b_nnz, unsorted);
+    cudaMemcpyAsync(host_word, unsorted, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    sl.woff = woff;
+    if (*host_word == 0) {
+        const int64_t pairs = op.b_rows * (int64_t)(nw + 1);
+        const int64_t bb = (pairs + 255) / 256;
+        k_split_bsearch<<<(int)(bb < cap_blocks ? bb : cap_blocks), 256, 0, s>>>(op.b_rp, op.b_ci, op.b_rows,
+                                                                                 op.b_nnz, cpc, nw, woff);
+        sl.ci = op.b_ci;
+        sl.val = op.b_val;
+        return 2;
+    }
     const size_t smem = (size_t)kSplitWarps * nw * sizeof(int);
     if (smem > 48 * 1024) {
         cudaFuncSetAttribute(k_split_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -150,9 +213,9 @@ void launch_window_plan(int dtype, const RawOperands &op, int nw, int cpc, void 
     else
         k_split_scatter<float><<<grid, kSplitNT, smem, s>>>(op.b_rp, op.b_ci, (const float *)op.b_val, op.b_rows,
                                                              op.b_nnz, cpc, nw, woff, sci, (float *)sval);
-    sl.woff = woff;
     sl.ci = sci;
     sl.val = sval;
+    return 3;
 }
 
 }  // namespace smash

@@ -163,8 +163,10 @@ struct BSlices {
     const void *val = nullptr;
 };
 size_t window_plan_bytes(const RawOperands &op, int nw, size_t vsz);
-void launch_window_plan(int dtype, const RawOperands &op, int nw, int cpc, void *ws, BSlices &sl, int sms,
-                        cudaStream_t s);
+// host_word: pinned host int (the sortedness of B is read back). Returns the
+// number of kernels launched.
+int launch_window_plan(int dtype, const RawOperands &op, int nw, int cpc, void *ws, BSlices &sl, int sms,
+                       cudaStream_t s, int *host_word);
 // Widest column window (a multiple of kSubCols, at most kMaxWinCols) of the
 // numeric dense kernel at `blocks_per_sm` resident blocks per SM; 0: none.
 constexpr int kMaxWinCols = 65536;
