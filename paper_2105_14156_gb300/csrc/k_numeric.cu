@@ -31,23 +31,25 @@ template <typename V, int GS, int NT>
 __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows, int count, int *token,
                                                  int tbits, HashCfg hc, int bsh, int bm_words, int bitmap_ratio,
                                                  NumOutT<V> out, int *err) {
-    // bsh >= 0: bucket-rank write-out (its T/4 counters and T/2 grouped keys
-    // follow each group's table); bsh < 0: bitonic.
+    // bsh >= 0: bucket-rank write-out (its T/4 counters and the T/2 grouped
+    // pairs follow each group's table); bsh < 0: bitonic.
     using G = Group<GS, NT>;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_row[G::kGroups];
     const int T = 1 << tbits;
-    const size_t grp_bytes = (size_t)T * (4 + sizeof(V)) + (bsh >= 0 ? bucket_bytes(T) : 0);
+    const size_t grp_bytes = (size_t)T * (4 + sizeof(V)) + (bsh >= 0 ? bucket_bytes<V>(T) : 0);
     unsigned char *gb = smem + (size_t)G::gid() * grp_bytes;
     int *keys = (int *)gb;
     V *vals = (V *)(gb + (size_t)T * 4);
-    int *bc = (int *)(gb + (size_t)T * (4 + sizeof(V)));   // T/4 bucket counters
-    int *gk = bc + (T >> 2);                               // T/2 grouped keys
+    V *gv = (V *)(gb + (size_t)T * (4 + sizeof(V)));       // T/2 grouped values
+    int *bc = (int *)(gv + (T >> 1));                       // T/4 bucket counters
+    int *gk = bc + (T >> 2);                                // T/2 grouped columns
     unsigned char *scr = smem + (size_t)G::kGroups * grp_bytes + (size_t)G::gid() * num_scratch_bytes<V, GS>();
     const ProdScratch<V> sc = carve_prod_scratch<V, GS>(scr);
     unsigned *bm = (unsigned *)(smem + (size_t)G::kGroups * (grp_bytes + num_scratch_bytes<V, GS>()));
     int *pre = (int *)(bm + bm_words);
     const int t = G::tid();
+    bool clean = false;   // the table is EMPTY / 0 (left so by the bucket write-out)
     for (;;) {
         int r;
         if constexpr (GS == 32) {
@@ -65,9 +67,11 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
         int n_exp;
         const bool ok = out_range(out, i, c0, n_exp, err);
         const bool use_bm = (GS == NT) && bm_words > 0 && (long long)bm_words <= (long long)bitmap_ratio * n_exp;
-        for (int s = t; s < T; s += GS) {
-            keys[s] = kEmpty;
-            vals[s] = V(0);
+        if (!clean) {
+            for (int s = t; s < T; s += GS) {
+                keys[s] = kEmpty;
+                vals[s] = V(0);
+            }
         }
         if (bsh >= 0)
             for (int s = t; s < (T >> 2); s += GS) bc[s] = 0;
@@ -83,7 +87,10 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
             const int h = hash_find_or_insert<false>(keys, tbits, hc, j, ins);
             if (h >= 0) {
                 atomicAdd(vals + h, v);
-                cnt += ins ? 1 : 0;
+                if (ins) {
+                    ++cnt;
+                    if (bsh >= 0) atomicAdd(bc + (j >> bsh), 1);   // bucket counts for the write-out
+                }
             } else if (out.row_nnz) {
                 ovf = 1;
             } else {
@@ -110,12 +117,18 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
         } else if (t == 0 && tot != n_exp) {
             raise_err(err, kErrCountMismatch);
         }
+        clean = false;
         if (!over) {
-            if (GS == 32 && tot <= 32) writeout_warp_rank<V>(keys, vals, T, tot, n_exp, out, c0);
-            else if (use_bm) writeout_bitmap<V, GS, NT>(keys, vals, T, bm, pre, bm_words, n_exp, out, c0, sc.red);
-            else if (bsh >= 0 && tot <= (T >> 1))
-                writeout_bucket<V, GS, NT>(keys, vals, tbits, hc, bc, gk, bsh, tot, n_exp, out, c0, sc.red);
-            else writeout_bitonic<V, GS, NT>(keys, vals, T, n_exp, out, c0, sc.red);
+            if (GS == 32 && tot <= 32) {
+                writeout_warp_rank<V>(keys, vals, T, tot, n_exp, out, c0);
+            } else if (use_bm) {
+                writeout_bitmap<V, GS, NT>(keys, vals, T, bm, pre, bm_words, n_exp, out, c0, sc.red);
+            } else if (bsh >= 0 && tot <= (T >> 1)) {
+                writeout_bucket<V, GS, NT>(keys, vals, T, bc, gk, gv, bsh, tot, n_exp, out, c0, sc.red);
+                clean = true;
+            } else {
+                writeout_bitonic<V, GS, NT>(keys, vals, T, n_exp, out, c0, sc.red);
+            }
         }
         G::sync();
     }
@@ -521,7 +534,7 @@ static size_t num_hash_smem(int tbits, int gs, int bm_words, bool buckets = fals
         default: scr = num_scratch_bytes<V, 1024>(); break;
     }
     const int T = 1 << tbits;
-    return (size_t)groups * ((size_t)(4 + sizeof(V)) * T + (buckets ? bucket_bytes(T) : 0)) +
+    return (size_t)groups * ((size_t)(4 + sizeof(V)) * T + (buckets ? bucket_bytes<V>(T) : 0)) +
            (size_t)groups * scr + (size_t)bm_words * 8;
 }
 

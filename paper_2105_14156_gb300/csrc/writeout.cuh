@@ -121,27 +121,23 @@ __device__ __forceinline__ void writeout_bitonic(int *keys, V *vals, int T, int 
 // ----- write-out: bucket rank ------------------------------------------------
 // Counting sort by the high bits of the column, then a rank inside each
 // (small) bucket: NB = T/4 buckets, bucket(j) = j >> sh (monotone in j).
-// bc[NB]: per-bucket counters (zero on entry), gk[T/2]: the keys grouped by
-// bucket. A key's final position is its bucket's start plus the number of
-// smaller keys in its bucket; its value is found again by probing the table.
-// Needs tot <= T/2 (the row's distinct columns).
+// bc[NB]: per-bucket counts, made while the row was hashed (one increment per
+// inserted column); gk[T/2], gv[T/2]: the row's (column, value) pairs grouped
+// by bucket. The pass that groups them also returns the table's occupied
+// slots to EMPTY / 0, so the next row needs no clearing. A pair's position is
+// its bucket's start plus the number of smaller columns in its bucket. Needs
+// tot <= T/2 (the row's distinct columns).
+template <typename V>
 __host__ __device__ constexpr size_t bucket_bytes(int T) {
-    return (size_t)T * 3;   // bc: T/4 ints, gk: T/2 ints
+    return (size_t)T * 3 + (size_t)(T / 2) * sizeof(V);   // bc: T/4 ints, gk: T/2 ints, gv: T/2 values
 }
 
 template <typename V, int GS, int NT>
-__device__ __forceinline__ void writeout_bucket(const int *keys, const V *vals, int tbits, HashCfg hc, int *bc,
-                                                int *gk, int sh, int tot, int n_exp, const NumOutT<V> &out,
-                                                int64_t c0, int *red) {
+__device__ __forceinline__ void writeout_bucket(int *keys, V *vals, int T, int *bc, int *gk, V *gv, int sh, int tot,
+                                                int n_exp, const NumOutT<V> &out, int64_t c0, int *red) {
     using G = Group<GS, NT>;
     const int t = G::tid();
-    const int T = 1 << tbits;
     const int NB = T >> 2;
-    for (int s = t; s < T; s += GS) {
-        const int k = keys[s];
-        if (k != kEmpty) atomicAdd(bc + (k >> sh), 1);
-    }
-    G::sync();
     {
         const int per = (NB + GS - 1) / GS;
         const int b0 = min(t * per, NB), b1 = min(b0 + per, NB);
@@ -158,11 +154,16 @@ __device__ __forceinline__ void writeout_bucket(const int *keys, const V *vals, 
     G::sync();
     for (int s = t; s < T; s += GS) {
         const int k = keys[s];
-        if (k != kEmpty) gk[atomicAdd(bc + (k >> sh), 1)] = k;
+        if (k != kEmpty) {
+            const int p = atomicAdd(bc + (k >> sh), 1);
+            gk[p] = k;
+            gv[p] = vals[s];
+            keys[s] = kEmpty;
+            vals[s] = V(0);
+        }
     }
     G::sync();
     // bc[b] is now the end of bucket b
-    const uint32_t mask = (uint32_t)T - 1u;
     for (int q = t; q < tot; q += GS) {
         const int k = gk[q];
         const int b = k >> sh;
@@ -170,12 +171,10 @@ __device__ __forceinline__ void writeout_bucket(const int *keys, const V *vals, 
         const int s0 = b ? bc[b - 1] : 0;
         int r = 0;
         for (int x = s0; x < e; ++x) r += gk[x] < k ? 1 : 0;
-        uint32_t h = hash_slot(k, tbits, hc) & mask;
-        for (uint32_t n = 0; n <= mask && keys[h] != k; ++n) h = (h + 1u) & mask;
         const int pos = s0 + r;
         if (pos < n_exp) {
             out.c_ci[c0 + pos] = k;
-            out.c_val[c0 + pos] = vals[h];
+            out.c_val[c0 + pos] = gv[q];
         }
     }
 }
