@@ -73,6 +73,20 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def smem_atomic_peak(vb: int):
+    """Measured shared-memory atomic add rate (Gop/s, random slots, whole GPU)
+    for the value type, from the committed probe summary."""
+    path = os.path.join(ROOT, "profiles", "smem_atomics_gb300.md")
+    key = "| f64 add, local, spread |" if vb == 8 else "| f32 add, local, spread |"
+    try:
+        for line in open(path):
+            if line.startswith(key):
+                return float(line.split("|")[2])
+    except OSError:
+        pass
+    return None
+
+
 def recorded_traffic(kernel: str, workload: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
     taken on the current kernel sources (else None)."""
@@ -311,6 +325,13 @@ def main():
                 "kernel": "%s (bin %d)" % (dom["name"], dom["bin"]),
                 "share_of_step": dom["ms"] / args.steps / ms,
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src}
+    # the dominant kernels merge one product per shared-memory atomic add: the
+    # measured atomic rate is their compute ceiling
+    apeak = smem_atomic_peak(vb)
+    if apeak:
+        arate = dom["products"] / (dom["ms"] / 1e3) / 1e9
+        roofline["smem_atomic"] = {"achieved": arate, "peak": apeak, "unit": "Gop/s", "frac": arate / apeak,
+                                   "peak_source": "measured (profiles/smem_atomics_gb300.md, random slots)"}
 
     # end to end through the public API with host buffers
     pinned = {}
