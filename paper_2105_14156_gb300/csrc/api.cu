@@ -318,7 +318,7 @@ int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const
 
 bool dense_windows(const smash_handle *h, const RawOperands &op, int dt, long long products, int &cpc, int &nw) {
     cpc = num_window_cols(dt, dense_blocks_of(h, dt));
-    if (cpc <= 0) return false;
+    if (cpc <= 0 || op.b_nnz >= INT_MAX) return false;   // window bounds are int32 positions in B
     nw = (int)((op.ncols + cpc - 1) / cpc);
     const double vsz = dt ? 8.0 : 4.0;
     const double plan = nw > 1 ? 4.0 * (double)op.b_rows * (nw + 1) + 2.0 * (4 + vsz) * (double)op.b_nnz : 0.0;

@@ -188,7 +188,8 @@ struct Operands {
     int32_t ncols;
     // Optional column slicing of B: when b_woff != nullptr, each row k of B is
     // stored grouped by column window, and only window `slice` is enumerated:
-    // entries [b_rp[k] + b_woff[k*(nslices+1) + slice], ... + slice+1).
+    // entries [b_woff[k*(nslices+1) + slice], b_woff[k*(nslices+1) + slice+1])
+    // (absolute positions in b_ci / b_val).
     const int32_t *b_woff = nullptr;
     int32_t nslices = 0;
     int32_t slice = 0;
@@ -214,17 +215,23 @@ template <typename V>
 __device__ __forceinline__ void b_row_of(const Operands<V> &op, int k, int &len, int64_t &bs, int *err) {
     len = 0;
     bs = 0;
+    if (op.b_woff) {
+        // sliced B: absolute bounds of row k's entries in this window
+        if ((unsigned)k < (unsigned)op.b_rows) {
+            const int32_t *w = op.b_woff + (size_t)k * (op.nslices + 1) + op.slice;
+            bs = w[0];
+            len = w[1] - w[0];
+        } else {
+            raise_err(err, kErrBadIndex);
+        }
+        return;
+    }
     if ((unsigned)k < (unsigned)op.b_rows) {
         int64_t s = __ldg(op.b_rp + k), t = __ldg(op.b_rp + k + 1);
         if (s >= 0 && t >= s && t <= op.b_nnz) {
             if (t - s < kMaxBRow) {
                 bs = s;
                 len = (int)(t - s);
-                if (op.b_woff) {
-                    const int32_t *w = op.b_woff + (size_t)k * (op.nslices + 1) + op.slice;
-                    bs = s + w[0];
-                    len = w[1] - w[0];
-                }
             } else {
                 raise_err(err, kErrBRowTooLong);
             }

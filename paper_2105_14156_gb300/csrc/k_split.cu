@@ -5,7 +5,8 @@
 // window) pair is an independent work item of the numeric dense kernel, whose
 // accumulator is the window only. So that an item enumerates only the
 // products that land in its window, woff[k][0..nw] records where each
-// window's entries start in row k of B, relative to the row's start. When
+// window's entries start in row k of B (absolute positions; B has fewer than
+// 2^31 entries when windows are used). When
 // every row of B is sorted by column the windows are contiguous already and
 // their bounds come from binary searches (B itself is the sliced copy);
 // otherwise the entries of each row are regrouped by window into a copy
@@ -59,10 +60,10 @@ __global__ void __launch_bounds__(kSplitNT) k_split_count(const int64_t *b_rp, c
             const int q = q0 + lane;
             const int c = q < nw ? cnt[q] : 0;
             const int incl = warp_incl_scan(c);
-            if (q < nw) woff[k * (nw + 1) + q] = run + incl - c;
+            if (q < nw) woff[k * (nw + 1) + q] = (int32_t)(s + run + incl - c);
             run += __shfl_sync(kFull, incl, 31);
         }
-        if (lane == 0) woff[k * (nw + 1) + nw] = run;
+        if (lane == 0) woff[k * (nw + 1) + nw] = (int32_t)(s + run);
         __syncwarp();
     }
 }
@@ -96,8 +97,8 @@ __global__ void __launch_bounds__(kSplitNT) k_split_scatter(const int64_t *b_rp,
             __syncwarp();
             if (valid) {
                 const int pos = base + __popc(peers & lanemask_lt());
-                out_ci[s + pos] = j;
-                out_val[s + pos] = v;
+                out_ci[pos] = j;
+                out_val[pos] = v;
                 if ((peers & lanemask_lt()) == 0) cur[q] = base + __popc(peers);
             }
             __syncwarp();
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(256) k_split_bsearch(const int64_t *b_rp, cons
             }
             pos = lo;
         }
-        woff[x] = (int32_t)(pos - s);
+        woff[x] = (int32_t)pos;
     }
 }
 
