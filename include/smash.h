@@ -266,9 +266,16 @@ int smash_mlp_train(smash_handle *h, smash_model *m, const float *feats, const f
 int smash_mlp_gradient(smash_handle *h, smash_model *m, const float *feats, const float *targets, int64_t n,
                        float *grad, float *loss, void *stream);
 
-/* Predictions y (device float[n]) with the bfloat16 inference weights. */
+/* Predictions y (device float[n]) with the bfloat16 inference weights,
+ * fp32 activations and accumulation (CUDA cores). */
 int smash_mlp_predict(smash_handle *h, const smash_model *m, const float *feats, int64_t n, float *y,
                       void *stream);
+
+/* The same predictions as computed inside spgemm_learned: layer 2 (64x64) on
+ * the tensor cores (bf16 operands, the layer-1 activations rounded to bf16,
+ * fp32 accumulation), 32 rows per warp. */
+int smash_mlp_predict_tc(smash_handle *h, const smash_model *m, const float *feats, int64_t n, float *y,
+                         void *stream);
 
 /*
  * C = A*B with learned sizing. Each row gets a capacity

@@ -61,6 +61,26 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const float *feats, const lon
     }
 }
 
+// Inference with layer 2 on the tensor cores: one warp per 32 rows.
+__global__ void __launch_bounds__(256) k_mlp_infer_tc(const float *feats, int64_t nrows, const __nv_bfloat16 *wb,
+                                                      const float *norm, float *y_out) {
+    extern __shared__ __align__(16) float s_mlp[];
+    load_mlp_tc(s_mlp, wb, norm);
+    __syncthreads();
+    const int lane = lane_id();
+    uint32_t *h1t = (uint32_t *)(s_mlp + kSmH1) + (threadIdx.x >> 5) * kH1Words;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < nrows;
+         base += warps * 32) {
+        const int64_t r = base + lane;
+        float f[kFeat];
+#pragma unroll
+        for (int c = 0; c < kFeat; ++c) f[c] = r < nrows ? feats[(size_t)r * kFeat + c] : 0.f;
+        const float y = mlp_forward_warp(s_mlp, f, h1t);
+        if (r < nrows) y_out[r] = y;
+    }
+}
+
 // Training: loss and gradient of a minibatch, TILE samples per block.
 // Sample s of minibatch step uses data index perm(base + s) with
 // perm(q) = (a*q + c) mod n, a coprime with n (a fresh c per epoch).
@@ -256,6 +276,21 @@ void launch_mlp_infer(const float *feats, const long long *bound, const int *row
     k_mlp_infer<<<(int)(blocks < cap ? blocks : cap), 256, 0, s>>>(feats, bound, row_list, nrows,
                                                                      (const __nv_bfloat16 *)wb, norm, margin, y_out,
                                                                      cap_out);
+}
+
+void launch_mlp_infer_tc(const float *feats, int64_t n, const void *wb, const float *norm, float *y, int sms,
+                         cudaStream_t s) {
+    if (n <= 0) return;
+    static bool attr = false;
+    const size_t smem = (size_t)mlp_tc_words(256 / 32) * 4;
+    if (!attr) {
+        cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    const int64_t blocks = (n + 255) / 256;
+    const int64_t cap = (int64_t)sms * 4;
+    k_mlp_infer_tc<<<(int)(blocks < cap ? blocks : cap), 256, smem, s>>>(feats, n, (const __nv_bfloat16 *)wb,
+                                                                          norm, y);
 }
 
 static size_t grad_smem() {

@@ -84,6 +84,9 @@ void launch_features(const RawOperands &op, const int *row_list, int64_t nrows, 
 void launch_mlp_infer(const float *feats, const long long *bound, const int *row_list, int64_t nrows,
                       const void *wb, const float *norm, float margin, float *y_out, int *cap_out, int sms,
                       cudaStream_t s);
+// Tensor-core forward (mlp_forward_warp) of n rows of raw features.
+void launch_mlp_infer_tc(const float *feats, int64_t n, const void *wb, const float *norm, float *y, int sms,
+                         cudaStream_t s);
 void launch_mlp_grad(const float *feats, const float *targets, int64_t n, int64_t first, int64_t count,
                      unsigned long long mul, const unsigned long long *shift, const float *params, const float *norm,
                      float *grad, float *loss_acc, int sms, cudaStream_t s);

@@ -230,6 +230,14 @@ int smash_mlp_predict(smash_handle *h, const smash_model *m, const float *feats,
     return last_cuda_status();
 }
 
+int smash_mlp_predict_tc(smash_handle *h, const smash_model *m, const float *feats, int64_t n, float *y,
+                         void *stream) {
+    if (!h || !m || !feats || !y || n < 0) return SMASH_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    launch_mlp_infer_tc(feats, n, m->wb, m->norm, y, h->sms, (cudaStream_t)stream);
+    return last_cuda_status();
+}
+
 int smash_mlp_train(smash_handle *h, smash_model *m, const float *feats, const float *targets, int64_t n,
                     const smash_train_cfg *cfg_in, float *final_loss, void *stream) {
     if (!h || !m || !feats || !targets || n <= 0 || n >= (1ll << 31)) return SMASH_ERR_INVALID_ARG;

@@ -27,7 +27,7 @@ EXPORTS = [
     "smash_status_string", "smash_set_timing", "smash_get_timings",
     "smash_train_cfg_default", "smash_model_create", "smash_model_destroy", "smash_model_get", "smash_model_set",
     "smash_model_save", "smash_model_load", "smash_row_features", "smash_mlp_train", "smash_mlp_gradient",
-    "smash_mlp_predict", "spgemm_learned", "smash_free_csr", "spgemm_symbolic_noalloc",
+    "smash_mlp_predict", "smash_mlp_predict_tc", "spgemm_learned", "smash_free_csr", "spgemm_symbolic_noalloc",
     "spgemm_batched", "smash_batched_set_table_bits", "smash_batched_get_table_bits", "smash_batched_autotune",
 ]
 
@@ -152,6 +152,7 @@ def load_library(path: str = LIB_PATH):
                                         ctypes.POINTER(ctypes.c_float), P]
         lib.smash_mlp_gradient.argtypes = [P, P, P, P, ctypes.c_int64, P, ctypes.POINTER(ctypes.c_float), P]
         lib.smash_mlp_predict.argtypes = [P, P, P, ctypes.c_int64, P, P]
+        lib.smash_mlp_predict_tc.argtypes = [P, P, P, ctypes.c_int64, P, P]
         lib.spgemm_learned.argtypes = [P, ctypes.POINTER(CsrStruct), ctypes.POINTER(CsrStruct), ctypes.c_int, P,
                                        ctypes.c_float, ctypes.POINTER(CsrStruct), ctypes.POINTER(LearnedStats), P]
         lib.smash_free_csr.argtypes = [P, ctypes.POINTER(CsrStruct)]
@@ -387,11 +388,14 @@ class Handle:
                                            ctypes.byref(loss), _stream_ptr(stream)), "smash_mlp_gradient")
         return g, float(loss.value)
 
-    def mlp_predict(self, model: "Model", feats, stream=None):
+    def mlp_predict(self, model: "Model", feats, stream=None, tensor_cores: bool = False):
+        """Predictions of the model for raw features (device float32 [n, 6]);
+        tensor_cores: the forward pass spgemm_learned uses (bf16 layer 2)."""
         import torch
         y = torch.empty(feats.shape[0], dtype=torch.float32, device=feats.device)
-        _check(self.lib.smash_mlp_predict(self.h, model.m, feats.contiguous().data_ptr(), feats.shape[0],
-                                          y.data_ptr(), _stream_ptr(stream)), "smash_mlp_predict")
+        fn = self.lib.smash_mlp_predict_tc if tensor_cores else self.lib.smash_mlp_predict
+        _check(fn(self.h, model.m, feats.contiguous().data_ptr(), feats.shape[0], y.data_ptr(),
+                  _stream_ptr(stream)), "smash_mlp_predict")
         return y
 
     def spgemm_learned(self, A: DeviceCsr, B: DeviceCsr, model: "Model", margin: float = 0.15, stream=None):

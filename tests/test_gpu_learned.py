@@ -76,6 +76,35 @@ def test_predict_matches_oracle_with_bf16_weights(handle):
     model.close()
 
 
+def test_tensor_core_predict_within_bf16_activation_bound(handle):
+    """The forward pass of the learned path (layer 2 on the tensor cores, the
+    layer-1 activations rounded to bf16, fp32 accumulation) against the float64
+    oracle with the same bf16 weights. Rounding h1 to bf16 changes each h1_v by
+    at most 2^-9 |h1_v|, so per row |y - y*| <= 2^-9 sum_u |w3_u| sum_v
+    |W2_uv| |h1_v| (relu is 1-Lipschitz), plus fp32 accumulation error."""
+    import torch
+    from oracle.mlp import unpack
+    from paper_2105_14156_gb300 import smash
+    rng = np.random.default_rng(5)
+    model = smash.Model(handle, seed=10)
+    p = rng.normal(0, 0.2, smash.MLP_PARAMS).astype(np.float32)
+    norm = np.concatenate([rng.normal(0, 1, 6), rng.uniform(0.5, 2, 6)]).astype(np.float32)
+    model.set(p, norm)
+    n = 1000   # 31 full warps of 32 rows and a ragged one
+    feats = rng.normal(0, 2, (n, 6)).astype(np.float32)
+    y = handle.mlp_predict(model, torch.from_numpy(feats).cuda(), tensor_cores=True).cpu().numpy()
+    pb = bf16_round(p).astype(np.float64)
+    x = mlp_oracle.normalise(feats, norm[:6].astype(np.float64), norm[6:].astype(np.float64))
+    ref, (_, _, h1, _, _) = mlp_oracle.forward(pb, x)
+    w = unpack(pb)
+    bound = 2.0 ** -9 * (np.abs(h1) @ np.abs(w["W2"]).T) @ np.abs(w["w3"])
+    err = np.abs(y - ref)
+    assert np.all(err <= 1.01 * bound + 1e-4 * np.maximum(1.0, np.abs(ref))), np.max(err - bound)
+    # and the bound is not vacuous: the two forward passes differ
+    assert np.max(err) > 0
+    model.close()
+
+
 def test_save_load_roundtrip(handle, tmp_path):
     from paper_2105_14156_gb300 import smash
     m1 = smash.Model(handle, seed=11)
