@@ -29,21 +29,21 @@ namespace smash {
 // ----- shared-memory hash rows -----------------------------------------------
 template <typename V, int GS, int NT>
 __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows, int count, int *token,
-                                                 int tbits, HashCfg hc, int bsh, int bm_words, int bitmap_ratio,
-                                                 NumOutT<V> out, int *err) {
-    // bsh >= 0: bucket-rank write-out (its T/4 counters and the T/2 grouped
-    // pairs follow each group's table); bsh < 0: bitonic.
+                                                 int tbits, HashCfg hc, int bsh, int bcap, int bm_words,
+                                                 int bitmap_ratio, NumOutT<V> out, int *err) {
+    // bsh >= 0: bucket-rank write-out (its T/4 counters and room for bcap
+    // grouped pairs follow each group's table); bsh < 0: bitonic.
     using G = Group<GS, NT>;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_row[G::kGroups];
     const int T = 1 << tbits;
-    const size_t grp_bytes = (size_t)T * (4 + sizeof(V)) + (bsh >= 0 ? bucket_bytes<V>(T) : 0);
+    const size_t grp_bytes = (size_t)T * (4 + sizeof(V)) + (bsh >= 0 ? bucket_bytes<V>(T, bcap) : 0);
     unsigned char *gb = smem + (size_t)G::gid() * grp_bytes;
     int *keys = (int *)gb;
     V *vals = (V *)(gb + (size_t)T * 4);
-    V *gv = (V *)(gb + (size_t)T * (4 + sizeof(V)));       // T/2 grouped values
-    int *bc = (int *)(gv + (T >> 1));                       // T/4 bucket counters
-    int *gk = bc + (T >> 2);                                // T/2 grouped columns
+    V *gv = (V *)(gb + (size_t)T * (4 + sizeof(V)));       // bcap grouped values
+    int *bc = (int *)(gv + bcap);                           // T/4 bucket counters
+    int *gk = bc + (T >> 2);                                // bcap grouped columns
     unsigned char *scr = smem + (size_t)G::kGroups * grp_bytes + (size_t)G::gid() * num_scratch_bytes<V, GS>();
     const ProdScratch<V> sc = carve_prod_scratch<V, GS>(scr);
     unsigned *bm = (unsigned *)(smem + (size_t)G::kGroups * (grp_bytes + num_scratch_bytes<V, GS>()));
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
                 writeout_warp_rank<V>(keys, vals, T, tot, n_exp, out, c0);
             } else if (use_bm) {
                 writeout_bitmap<V, GS, NT>(keys, vals, T, bm, pre, bm_words, n_exp, out, c0, sc.red);
-            } else if (bsh >= 0 && tot <= (T >> 1)) {
+            } else if (bsh >= 0 && tot <= bcap) {
                 writeout_bucket<V, GS, NT>(keys, vals, T, bc, gk, gv, bsh, tot, n_exp, out, c0, sc.red);
                 clean = true;
             } else {
@@ -521,7 +521,7 @@ static int threads_per_row(int tbits, int shift) {
 static int block_threads(int gs) { return gs < 64 ? 256 : gs; }
 
 template <typename V>
-static size_t num_hash_smem(int tbits, int gs, int bm_words, bool buckets = false) {
+static size_t num_hash_smem(int tbits, int gs, int bm_words, int bcap = 0) {
     const int nt = block_threads(gs);
     const int groups = nt / gs;
     size_t scr = 0;
@@ -534,7 +534,7 @@ static size_t num_hash_smem(int tbits, int gs, int bm_words, bool buckets = fals
         default: scr = num_scratch_bytes<V, 1024>(); break;
     }
     const int T = 1 << tbits;
-    return (size_t)groups * ((size_t)(4 + sizeof(V)) * T + (buckets ? bucket_bytes<V>(T) : 0)) +
+    return (size_t)groups * ((size_t)(4 + sizeof(V)) * T + (bcap > 0 ? bucket_bytes<V>(T, bcap) : 0)) +
            (size_t)groups * scr + (size_t)bm_words * 8;
 }
 
@@ -556,49 +556,55 @@ static int resident_grid(K kernel, int nt, size_t smem, int sms, long long want_
 
 template <typename V, int GS>
 static void num_hash_go(const Operands<V> &op, const int *rows, int count, int *token, const HashLaunch &hl,
-                        int bitmap_ratio, const NumOutT<V> &out, int *err, cudaStream_t s) {
+                        float inv_load, int bitmap_ratio, const NumOutT<V> &out, int *err, cudaStream_t s) {
     // one group per block from 64 threads up (block barriers, no named ones)
     constexpr int NT = GS < 64 ? 256 : GS;
     constexpr int groups = NT / GS;
+    const int T = 1 << hl.tbits;
+    const size_t lim = (size_t)max_smem_per_block();
     int bm_words = 0;
     if (GS == NT && bitmap_ratio > 0) {
         const int words = (op.ncols + 31) / 32;
-        if (num_hash_smem<V>(hl.tbits, GS, words, true) <= (size_t)max_smem_per_block()) bm_words = words;
+        if (num_hash_smem<V>(hl.tbits, GS, words, T / 2) <= lim) bm_words = words;
     }
-    // bucket-rank write-out when its arrays fit next to the tables
-    const bool buckets = num_hash_smem<V>(hl.tbits, GS, bm_words, true) <= (size_t)max_smem_per_block();
-    const size_t smem = num_hash_smem<V>(hl.tbits, GS, bm_words, buckets);
+    // bucket-rank write-out when its arrays fit next to the tables: room for
+    // the rows' distinct columns, T/2 at loads up to 0.5, else 3T/4 (loads up
+    // to 0.75) when that fits
+    int bcap = inv_load >= 2.f ? T / 2 : T - T / 4;
+    if (num_hash_smem<V>(hl.tbits, GS, bm_words, bcap) > lim) bcap = T / 2;
+    if (num_hash_smem<V>(hl.tbits, GS, bm_words, bcap) > lim) bcap = 0;
+    const bool buckets = bcap > 0;
+    const size_t smem = num_hash_smem<V>(hl.tbits, GS, bm_words, bcap);
     auto kern = k_num_hash<V, GS, NT>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int grid = resident_grid(kern, NT, smem, hl.sms, (count + groups - 1) / groups);
     const HashCfg hc{hl.hash_kind, hl.colbits};
     // buckets: T/4 of them over the column range, by the high bits
     const int bsh = !buckets ? -1 : hl.colbits > hl.tbits - 2 ? hl.colbits - (hl.tbits - 2) : 0;
-    kern<<<grid, NT, smem, s>>>(op, rows, count, token, hl.tbits, hc, bsh, bm_words, bitmap_ratio, out, err);
+    kern<<<grid, NT, smem, s>>>(op, rows, count, token, hl.tbits, hc, bsh, bcap, bm_words, bitmap_ratio, out, err);
 }
 
 template <typename V>
 static void num_hash_typed(const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
-                           int bitmap_ratio, const NumOut &o, int *err, cudaStream_t s) {
+                           float inv_load, int bitmap_ratio, const NumOut &o, int *err, cudaStream_t s) {
     const Operands<V> op = num_operands<V>(r);
     const NumOutT<V> out = num_out<V>(o);
     switch (threads_per_row(hl.tbits, hl.group_shift)) {
-        case 32: num_hash_go<V, 32>(op, rows, count, token, hl, bitmap_ratio, out, err, s); break;
-        case 64: num_hash_go<V, 64>(op, rows, count, token, hl, bitmap_ratio, out, err, s); break;
-        case 128: num_hash_go<V, 128>(op, rows, count, token, hl, bitmap_ratio, out, err, s); break;
-        case 256: num_hash_go<V, 256>(op, rows, count, token, hl, bitmap_ratio, out, err, s); break;
-        case 512: num_hash_go<V, 512>(op, rows, count, token, hl, bitmap_ratio, out, err, s); break;
-        default: num_hash_go<V, 1024>(op, rows, count, token, hl, bitmap_ratio, out, err, s); break;
+        case 32: num_hash_go<V, 32>(op, rows, count, token, hl, inv_load, bitmap_ratio, out, err, s); break;
+        case 64: num_hash_go<V, 64>(op, rows, count, token, hl, inv_load, bitmap_ratio, out, err, s); break;
+        case 128: num_hash_go<V, 128>(op, rows, count, token, hl, inv_load, bitmap_ratio, out, err, s); break;
+        case 256: num_hash_go<V, 256>(op, rows, count, token, hl, inv_load, bitmap_ratio, out, err, s); break;
+        case 512: num_hash_go<V, 512>(op, rows, count, token, hl, inv_load, bitmap_ratio, out, err, s); break;
+        default: num_hash_go<V, 1024>(op, rows, count, token, hl, inv_load, bitmap_ratio, out, err, s); break;
     }
 }
 
 void launch_num_hash(int dtype, const RawOperands &r, const int *rows, int count, int *token,
                      const HashLaunch &hl, float inv_load, int bitmap_ratio, const NumOut &out, int *err,
                      cudaStream_t s) {
-    (void)inv_load;
     if (count <= 0) return;
-    if (dtype) num_hash_typed<double>(r, rows, count, token, hl, bitmap_ratio, out, err, s);
-    else num_hash_typed<float>(r, rows, count, token, hl, bitmap_ratio, out, err, s);
+    if (dtype) num_hash_typed<double>(r, rows, count, token, hl, inv_load, bitmap_ratio, out, err, s);
+    else num_hash_typed<float>(r, rows, count, token, hl, inv_load, bitmap_ratio, out, err, s);
 }
 
 int dense_bitmap_max_cols() {

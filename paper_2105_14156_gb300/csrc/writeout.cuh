@@ -122,14 +122,15 @@ __device__ __forceinline__ void writeout_bitonic(int *keys, V *vals, int T, int 
 // Counting sort by the high bits of the column, then a rank inside each
 // (small) bucket: NB = T/4 buckets, bucket(j) = j >> sh (monotone in j).
 // bc[NB]: per-bucket counts, made while the row was hashed (one increment per
-// inserted column); gk[T/2], gv[T/2]: the row's (column, value) pairs grouped
-// by bucket. The pass that groups them also returns the table's occupied
-// slots to EMPTY / 0, so the next row needs no clearing. A pair's position is
-// its bucket's start plus the number of smaller columns in its bucket. Needs
-// tot <= T/2 (the row's distinct columns).
+// inserted column); gk[cap], gv[cap]: the row's (column, value) pairs
+// grouped by bucket, cap = 3T/4 or T/2 (what shared memory allows). The pass
+// that groups them also returns the table's occupied slots to EMPTY / 0, so
+// the next row needs no clearing. A pair's position is its bucket's start plus
+// the number of smaller columns in its bucket. Needs tot <= cap.
 template <typename V>
-__host__ __device__ constexpr size_t bucket_bytes(int T) {
-    return (size_t)T * 3 + (size_t)(T / 2) * sizeof(V);   // bc: T/4 ints, gk: T/2 ints, gv: T/2 values
+__host__ __device__ constexpr size_t bucket_bytes(int T, int cap) {
+    // bc: T/4 ints, gv: cap values, gk: cap ints
+    return (size_t)(T >> 2) * 4 + (size_t)cap * (sizeof(V) + 4);
 }
 
 template <typename V, int GS, int NT>
