@@ -60,6 +60,7 @@ size_t batched_smem(int dtype, int tw_bits);
 int batched_dense_max(int dtype, int tw_bits);
 void launch_batch_rowinfo(const BatchArgs &p, int sms, cudaStream_t s);
 int batched_grid(int dtype, int tw_bits, int sms);
-int launch_batched(int dtype, const BatchArgs &p, int grid, cudaStream_t s);
+// p_dev: the arguments in device memory (read by every block at start).
+int launch_batched(int dtype, const BatchArgs *p_dev, int tw_bits, int grid, cudaStream_t s);
 
 }  // namespace smash

@@ -20,8 +20,11 @@ struct BatchState {
     size_t pinned_bytes = 0;
     int tw_bits = 10;
     cudaStream_t cs = nullptr;       // private stream for graph recording
-    cudaGraph_t graph = nullptr;     // last recorded launch (kept until the next call)
+    cudaGraph_t graph = nullptr;     // the recorded launch, replayed while its key holds
     cudaGraphExec_t exec = nullptr;
+    // what the recorded launch depends on: argument buffer, grid, type, table size
+    const void *key_args = nullptr;
+    int key_grid = 0, key_dt = -1, key_bits = 0;
 };
 std::map<smash_handle *, BatchState> g_batch;
 
@@ -34,27 +37,41 @@ void drop_graph(BatchState &b) {
     b.graph = nullptr;
 }
 
-// Record the persistent launch (with the reset of its work tokens and barrier
-// words) as a CUDA graph and launch it on s; fall back to a direct launch if
-// recording is not possible.
-int run_batched_graph(BatchState &b, int dt, const BatchArgs &p, int grid, cudaStream_t s) {
-    drop_graph(b);
+// The persistent launch (with the reset of its work tokens and barrier words)
+// is recorded once as a CUDA graph and replayed on s; its arguments are
+// copied to p_dev before each replay (p_host: pinned). It is recorded again
+// when the argument buffer, grid, type or table size changes; a direct launch
+// is the fallback if recording is not possible.
+int run_batched_graph(BatchState &b, int dt, const BatchArgs *p_host, BatchArgs *p_dev, int grid, cudaStream_t s) {
+    if (cudaMemcpyAsync(p_dev, p_host, sizeof(BatchArgs), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return SMASH_ERR_CUDA;
+    const bool same = b.exec && b.key_args == p_dev && b.key_grid == grid && b.key_dt == dt &&
+                      b.key_bits == p_host->tw_bits;
     bool ok = true;
-    if (!b.cs && cudaStreamCreateWithFlags(&b.cs, cudaStreamNonBlocking) != cudaSuccess) ok = false;
-    if (ok && cudaStreamBeginCapture(b.cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) ok = false;
-    if (ok) {
-        const bool m = cudaMemsetAsync(p.counters + 2, 0, sizeof(int) * 6, b.cs) == cudaSuccess;
-        const int e = launch_batched(dt, p, grid, b.cs);
-        const bool endok = cudaStreamEndCapture(b.cs, &b.graph) == cudaSuccess;
-        ok = m && e == 0 && endok && b.graph;
+    if (!same) {
+        drop_graph(b);
+        if (!b.cs && cudaStreamCreateWithFlags(&b.cs, cudaStreamNonBlocking) != cudaSuccess) ok = false;
+        if (ok && cudaStreamBeginCapture(b.cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) ok = false;
+        if (ok) {
+            const bool m = cudaMemsetAsync(p_host->counters + 2, 0, sizeof(int) * 6, b.cs) == cudaSuccess;
+            const int e = launch_batched(dt, p_dev, p_host->tw_bits, grid, b.cs);
+            const bool endok = cudaStreamEndCapture(b.cs, &b.graph) == cudaSuccess;
+            ok = m && e == 0 && endok && b.graph;
+        }
+        if (ok) ok = cudaGraphInstantiate(&b.exec, b.graph, 0) == cudaSuccess;
+        if (ok) {
+            b.key_args = p_dev;
+            b.key_grid = grid;
+            b.key_dt = dt;
+            b.key_bits = p_host->tw_bits;
+        }
     }
-    if (ok) ok = cudaGraphInstantiate(&b.exec, b.graph, 0) == cudaSuccess;
     if (ok) ok = cudaGraphLaunch(b.exec, s) == cudaSuccess;
     if (ok) return SMASH_OK;
     cudaGetLastError();
     drop_graph(b);
-    if (cudaMemsetAsync(p.counters + 2, 0, sizeof(int) * 6, s) != cudaSuccess) return SMASH_ERR_CUDA;
-    if (launch_batched(dt, p, grid, s) != 0) {
+    if (cudaMemsetAsync(p_host->counters + 2, 0, sizeof(int) * 6, s) != cudaSuccess) return SMASH_ERR_CUDA;
+    if (launch_batched(dt, p_dev, p_host->tw_bits, grid, s) != 0) {
         cudaGetLastError();
         return SMASH_ERR_CUDA;
     }
@@ -160,6 +177,7 @@ int spgemm_batched(smash_handle *h, int count, const smash_csr *A, const smash_c
     carve_size<unsigned long long>(need, 4);
     carve_size<int64_t>(need, count + 1);
     carve_size<int64_t>(need, count);
+    carve_size<BatchArgs>(need, 1);
     if ((st = ensure(h, bs.dev, need, s))) return st;
     Carver c(bs.dev.ptr);
     Layout L;
@@ -175,8 +193,9 @@ int spgemm_batched(smash_handle *h, int count, const smash_csr *A, const smash_c
     L.sums = c.take<unsigned long long>(4);
     L.base = c.take<int64_t>(count + 1);
     L.totals = c.take<int64_t>(count);
+    BatchArgs *args_dev = c.take<BatchArgs>(1);
     // descriptors (pinned host -> device)
-    const size_t hbytes = sizeof(BatchMat) * count + 2 * sizeof(int64_t) * (count + 1);
+    const size_t hbytes = sizeof(BatchMat) * count + 2 * sizeof(int64_t) * (count + 1) + sizeof(BatchArgs) + 64;
     if ((st = ensure_pinned(bs, hbytes + 4096))) return st;
     cudaStreamSynchronize(s);   // the pinned staging may still feed a previous copy
     BatchMat *hm = (BatchMat *)bs.pinned;
@@ -306,7 +325,10 @@ int spgemm_batched(smash_handle *h, int count, const smash_csr *A, const smash_c
     if (grid < 1) grid = 1;
     {
         LaunchTimer lt(h, s, "batched_persistent", -1, 256, nrows, 0, (long long)sum_f, 0);
-        if ((st = run_batched_graph(bs, dt, p, grid, s))) return st;
+        // the arguments through pinned memory, after the descriptors
+        BatchArgs *p_pin = (BatchArgs *)(((uintptr_t)(hts + count + 1) + 63) & ~(uintptr_t)63);
+        *p_pin = p;
+        if ((st = run_batched_graph(bs, dt, p_pin, args_dev, grid, s))) return st;
     }
     // base offsets and totals
     std::vector<int64_t> base(count + 1), totals(count);

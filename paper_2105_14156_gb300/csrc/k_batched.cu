@@ -324,9 +324,15 @@ __device__ bool run_items(const BatchArgs &p, int *token, const BatchSmem<V> &sm
 }
 
 template <typename V>
-__global__ void __launch_bounds__(kBNT) k_batched(BatchArgs p) {
+__global__ void __launch_bounds__(kBNT) k_batched(const BatchArgs *pp) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_w[32];
+    // the arguments live in device memory (a recorded launch is replayed with
+    // new arguments copied there)
+    __shared__ BatchArgs s_p;
+    if (threadIdx.x == 0) s_p = *pp;
+    __syncthreads();
+    const BatchArgs &p = s_p;
     BatchSmem<V> sm;
     sm.tab = smem;
     const size_t tab_bytes = ((size_t)kBW << p.tw_bits) * (4 + sizeof(V));
@@ -429,8 +435,8 @@ int batched_grid(int dtype, int tw_bits, int sms) {
     return per * sms;
 }
 
-int launch_batched(int dtype, const BatchArgs &p, int grid, cudaStream_t s) {
-    const size_t smem = batched_smem(dtype, p.tw_bits);
+int launch_batched(int dtype, const BatchArgs *p_dev, int tw_bits, int grid, cudaStream_t s) {
+    const size_t smem = batched_smem(dtype, tw_bits);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid, 1, 1);
     cfg.blockDim = dim3(kBNT, 1, 1);
@@ -442,8 +448,8 @@ int launch_batched(int dtype, const BatchArgs &p, int grid, cudaStream_t s) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaError_t e;
-    if (dtype) e = cudaLaunchKernelEx(&cfg, k_batched<double>, p);
-    else e = cudaLaunchKernelEx(&cfg, k_batched<float>, p);
+    if (dtype) e = cudaLaunchKernelEx(&cfg, k_batched<double>, p_dev);
+    else e = cudaLaunchKernelEx(&cfg, k_batched<float>, p_dev);
     return e == cudaSuccess ? 0 : (int)e;
 }
 

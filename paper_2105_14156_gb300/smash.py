@@ -425,33 +425,62 @@ def _pair_structs(pairs):
     return SA, SB
 
 
+class BatchedInputs:
+    """The descriptors of a list of (A, B) device pairs, built once and reused
+    by every batched call on them (the arrays must stay alive and unchanged)."""
+
+    def __init__(self, pairs):
+        self.pairs = list(pairs)
+        self.n = len(self.pairs)
+        self.SA, self.SB = _pair_structs(self.pairs)
+        self.dt = _dtype_code(self.pairs[0][0].val) if self.n else 0
+        self.vdt = self.pairs[0][0].val.dtype if self.n else None
+
+
+class BatchedResult:
+    """The products of a batched call, C_m as zero-copy views made on access."""
+
+    def __init__(self, structs, vdt):
+        self.SC = structs
+        self.vdt = vdt
+
+    def __len__(self):
+        return len(self.SC)
+
+    def __getitem__(self, m):
+        import torch
+        if m < 0:
+            m += len(self.SC)
+        c = self.SC[m]
+        return DeviceCsr(int(c.rows), int(c.cols), _view(c.row_ptr, int(c.rows) + 1, torch.int64),
+                         _view(c.col_idx, int(c.nnz), torch.int32), _view(c.val, int(c.nnz), self.vdt))
+
+    def __iter__(self):
+        for m in range(len(self.SC)):
+            yield self[m]
+
+
 def _batched(self, pairs, stream=None):
-    """C_m = A_m * B_m for all pairs in one persistent launch. Returns
-    (list of C as zero-copy views, stats, owner); owner.free() releases them."""
-    import torch
-    n = len(pairs)
+    """C_m = A_m * B_m for all pairs (a list of (A, B), or BatchedInputs) in
+    one persistent launch. Returns (the products, stats, owner): the products
+    index as C_m views; owner.free() releases their memory."""
+    inp = pairs if isinstance(pairs, BatchedInputs) else BatchedInputs(pairs)
+    n = inp.n
     if n == 0:
-        return [], BatchedStats().as_dict(), None
-    dt = _dtype_code(pairs[0][0].val)
-    SA, SB = _pair_structs(pairs)
+        return BatchedResult([], None), BatchedStats().as_dict(), None
     SC = (CsrStruct * n)()
     st = BatchedStats()
-    _check(self.lib.spgemm_batched(self.h, n, SA, SB, dt, SC, ctypes.byref(st), _stream_ptr(stream)),
+    _check(self.lib.spgemm_batched(self.h, n, inp.SA, inp.SB, inp.dt, SC, ctypes.byref(st), _stream_ptr(stream)),
            "spgemm_batched")
-    vdt = pairs[0][0].val.dtype
-    Cs = [DeviceCsr(int(c.rows), int(c.cols), _view(c.row_ptr, int(c.rows) + 1, torch.int64),
-                    _view(c.col_idx, int(c.nnz), torch.int32), _view(c.val, int(c.nnz), vdt)) for c in SC]
-    return Cs, st.as_dict(), LibraryCsr(self, SC[0])
+    return BatchedResult(SC, inp.vdt), st.as_dict(), LibraryCsr(self, SC[0])
 
 
 def _batched_autotune(self, pairs, stream=None):
-    n = len(pairs)
-    dt = _dtype_code(pairs[0][0].val)
-    SA, SB = _pair_structs(pairs)
+    inp = pairs if isinstance(pairs, BatchedInputs) else BatchedInputs(pairs)
     bits = ctypes.c_int(0)
     ms = ctypes.c_float(0)
-    _check(self.lib.smash_batched_autotune(self.h, n, SA, SB, dt, ctypes.byref(bits), ctypes.byref(ms),
-                                           _stream_ptr(stream)), "smash_batched_autotune")
+    _check(self.lib.smash_batched_autotune(self.h, inp.n, inp.SA, inp.SB, inp.dt, ctypes.byref(bits),
+                                           ctypes.byref(ms), _stream_ptr(stream)), "smash_batched_autotune")
     return int(bits.value), float(ms.value)
 
 
