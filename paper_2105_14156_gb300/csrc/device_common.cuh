@@ -159,6 +159,44 @@ struct Group {
 };
 
 // ---------------------------------------------------------------------------
+// Rows of a bin handed out to groups by an atomic counter, one row ahead: the
+// claim of a group's next row is issued when its current row starts, so the
+// atomic's latency is hidden behind the row's work. A warp keeps the claim in
+// lane 0's register; larger groups pass it through s_row[2][kGroups]
+// alternately (the row's closing group barrier orders the write of one slot
+// after the reads of it). Every iteration of the caller's row loop must end
+// with a group barrier when GS > 32.
+template <typename G>
+struct RowClaim {
+    int *token;
+    int (*s_row)[G::kGroups];
+    int nx = 0;    // GS = 32: the claimed next row (lane 0)
+    int par = 0;   // GS > 32: slot holding the claimed next row
+
+    __device__ __forceinline__ RowClaim(int *tok, int (*s)[G::kGroups]) : token(tok), s_row(s) {
+        if (G::tid() == 0) nx = atomicAdd(token, 1);
+        if constexpr (G::kWarps > 1) {
+            if (G::tid() == 0) s_row[0][G::gid()] = nx;
+            G::sync();
+        }
+    }
+
+    // The group's row for this iteration (>= count: no more rows); claims the next.
+    __device__ __forceinline__ int next(int count) {
+        int r;
+        if constexpr (G::kWarps == 1) {
+            r = __shfl_sync(kFull, nx, 0);
+            if (G::tid() == 0 && r < count) nx = atomicAdd(token, 1);
+        } else {
+            r = s_row[par][G::gid()];
+            par ^= 1;
+            if (G::tid() == 0 && r < count) s_row[par][G::gid()] = atomicAdd(token, 1);
+        }
+        return r;
+    }
+};
+
+// ---------------------------------------------------------------------------
 // Hash slot of column j in a table of 2^tbits slots.
 struct HashCfg {
     int kind;     // 0 low bits, 1 multiplicative, 2 high bits
@@ -354,8 +392,8 @@ __device__ __forceinline__ int step_entry(int e) {
     return __popc(ends & ((2u << lane_id()) - 1u));
 }
 
-// Every product of A entries [ab, ae), enumerated by a group of GS >= 64
-// threads: batches of GS A entries are staged in shared memory (entries with
+// Every product of A entries [ab, ae), enumerated by a group of GS threads
+// (a warp or more): batches of GS A entries are staged in shared memory (entries with
 // an empty row of B dropped), the batch's products are split into one
 // contiguous range per warp, and each warp walks its range 32 products at a
 // time, kProdUnroll steps per round. The window of 32 staged entries that
@@ -463,14 +501,6 @@ __device__ __forceinline__ void group_products(const Operands<V> &op, int64_t ab
         }
         G::sync();
     }
-}
-
-// Dispatch: warp or group enumeration.
-template <typename V, bool NUM, int GS, int NT, typename F>
-__device__ __forceinline__ void row_products(const Operands<V> &op, int64_t ab, int64_t ae,
-                                             const ProdScratch<V> &sc, int *err, F &&f) {
-    if constexpr (GS == 32) warp_products<V, NUM>(op, ab, ae, err, f);
-    else group_products<V, NUM, GS, NT>(op, ab, ae, sc, err, f);
 }
 
 // ---------------------------------------------------------------------------

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
     // grouped pairs follow each group's table); bsh < 0: bitonic.
     using G = Group<GS, NT>;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_row[G::kGroups];
+    __shared__ int s_row[2][G::kGroups];
     const int T = 1 << tbits;
     const size_t grp_bytes = (size_t)T * (4 + sizeof(V)) + (bsh >= 0 ? bucket_bytes<V>(T, bcap) : 0);
     unsigned char *gb = smem + (size_t)G::gid() * grp_bytes;
@@ -50,17 +50,9 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
     int *pre = (int *)(bm + bm_words);
     const int t = G::tid();
     bool clean = false;   // the table is EMPTY / 0 (left so by the bucket write-out)
+    RowClaim<G> claim(token, s_row);
     for (;;) {
-        int r;
-        if constexpr (GS == 32) {
-            r = 0;
-            if (t == 0) r = atomicAdd(token, 1);
-            r = __shfl_sync(kFull, r, 0);
-        } else {
-            if (t == 0) s_row[G::gid()] = atomicAdd(token, 1);
-            G::sync();
-            r = s_row[G::gid()];
-        }
+        const int r = claim.next(count);
         if (r >= count) break;
         const int i = rows[r];
         int64_t c0;
@@ -81,12 +73,11 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
         int64_t ab = 0, ae = 0;
         if (ok) a_row_range(op, i, ab, ae, err);
         int cnt = 0, ovf = 0;
-        row_products<V, true, GS, NT>(op, ab, ae, sc, err, [&](int j, V a, V bkj) {
-            const V v = a * bkj;
+        group_products<V, true, GS, NT>(op, ab, ae, sc, err, [&](int j, V a, V bkj) {
             bool ins;
             const int h = hash_find_or_insert<false>(keys, tbits, hc, j, ins);
             if (h >= 0) {
-                atomicAdd(vals + h, v);
+                atomicAdd(vals + h, a * bkj);
                 if (ins) {
                     ++cnt;
                     if (bsh >= 0) atomicAdd(bc + (j >> bsh), 1);   // bucket counts for the write-out
@@ -397,7 +388,7 @@ __global__ void __launch_bounds__(NT) k_num_spill(Operands<V> op, const int *row
         int64_t ab = 0, ae = 0;
         if (ok) a_row_range(op, i, ab, ae, err);
         int cnt = 0, ovf = 0;
-        row_products<V, true, NT, NT>(op, ab, ae, sc, err, [&](int j, V a, V bkj) {
+        group_products<V, true, NT, NT>(op, ab, ae, sc, err, [&](int j, V a, V bkj) {
             const V v = a * bkj;
             bool ins;
             const int h = hash_find_or_insert<true>(keys, tb, hc, j, ins);

@@ -22,23 +22,16 @@ __global__ void __launch_bounds__(NT) k_sym_hash(Operands<float> op, const int *
                                                  int tbits, HashCfg hc, int *nnz_out, int *err) {
     using G = Group<GS, NT>;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_row[G::kGroups];
+    __shared__ int s_row[2][G::kGroups];
     const int T = 1 << tbits;
     int *keys = (int *)smem + (size_t)G::gid() * T;
+    // group scratch (GS > 32 only: warp rows enumerate from registers)
     unsigned char *scr = smem + (size_t)G::kGroups * T * 4 + (size_t)G::gid() * prod_scratch_bytes<float, GS>();
     const ProdScratch<float> sc = carve_prod_scratch<float, GS>(scr);
     const int t = G::tid();
+    RowClaim<G> claim(token, s_row);
     for (;;) {
-        int r;
-        if constexpr (GS == 32) {
-            r = 0;
-            if (t == 0) r = atomicAdd(token, 1);
-            r = __shfl_sync(kFull, r, 0);
-        } else {
-            if (t == 0) s_row[G::gid()] = atomicAdd(token, 1);
-            G::sync();
-            r = s_row[G::gid()];
-        }
+        const int r = claim.next(count);
         if (r >= count) break;
         const int i = rows[r];
         for (int s = t; s < T; s += GS) keys[s] = kEmpty;
@@ -46,11 +39,15 @@ __global__ void __launch_bounds__(NT) k_sym_hash(Operands<float> op, const int *
         int64_t ab, ae;
         a_row_range(op, i, ab, ae, err);
         int cnt = 0;
-        row_products<float, false, GS, NT>(op, ab, ae, sc, err, [&](int j, float, float) {
+        // warp rows: the register-staged enumerator (measured faster here than
+        // the shared-memory one, which the numeric warp rows use)
+        auto ins_key = [&](int j, float, float) {
             bool ins;
             if (hash_find_or_insert<false>(keys, tbits, hc, j, ins) < 0) raise_err(err, kErrTableFull);
             cnt += ins ? 1 : 0;
-        });
+        };
+        if constexpr (GS == 32) warp_products<float, false>(op, ab, ae, err, ins_key);
+        else group_products<float, false, GS, NT>(op, ab, ae, sc, err, ins_key);
         int tot;
         if constexpr (GS == 32) tot = warp_sum(cnt);
         else tot = G::template sum<int>(cnt, sc.red);
@@ -107,7 +104,7 @@ __global__ void __launch_bounds__(NT) k_sym_dense(Operands<float> op, const int 
         __syncthreads();
         int64_t ab, ae;
         a_row_range(op, i, ab, ae, err);
-        row_products<float, false, NT, NT>(op, ab, ae, sc, err, [&](int j, float, float) {
+        group_products<float, false, NT, NT>(op, ab, ae, sc, err, [&](int j, float, float) {
             const unsigned bit = 1u << (j & 31);
             unsigned *w = bm + (j >> 5);
             if (!(*(volatile unsigned *)w & bit)) atomicOr(w, bit);
@@ -164,7 +161,7 @@ __global__ void __launch_bounds__(NT) k_sym_spill(Operands<float> op, const int 
         int64_t ab, ae;
         a_row_range(op, i, ab, ae, err);
         int cnt = 0;
-        row_products<float, false, NT, NT>(op, ab, ae, sc, err, [&](int j, float, float) {
+        group_products<float, false, NT, NT>(op, ab, ae, sc, err, [&](int j, float, float) {
             bool ins;
             if (hash_find_or_insert<true>(keys, tb, hc, j, ins) < 0) raise_err(err, kErrTableFull);
             cnt += ins ? 1 : 0;

@@ -153,14 +153,22 @@ __device__ __forceinline__ void writeout_bucket(int *keys, V *vals, int T, int *
         }
     }
     G::sync();
-    for (int s = t; s < T; s += GS) {
-        const int k = keys[s];
-        if (k != kEmpty) {
-            const int p = atomicAdd(bc + (k >> sh), 1);
-            gk[p] = k;
-            gv[p] = vals[s];
-            keys[s] = kEmpty;
-            vals[s] = V(0);
+    // four slots per thread per round, so that their atomics overlap
+    for (int s0 = t; s0 < T; s0 += 4 * GS) {
+        int k[4], p[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) k[u] = s0 + u * GS < T ? keys[s0 + u * GS] : kEmpty;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p[u] = k[u] != kEmpty ? atomicAdd(bc + (k[u] >> sh), 1) : 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (k[u] != kEmpty) {
+                const int s = s0 + u * GS;
+                gk[p[u]] = k[u];
+                gv[p[u]] = vals[s];
+                keys[s] = kEmpty;
+                vals[s] = V(0);
+            }
         }
     }
     G::sync();
