@@ -478,10 +478,13 @@ void launch_overflow_list(const int *row_nnz, int64_t n, int *list, int *count, 
 }
 
 // Copy each staged row that fitted to its place in C. Work is split by output
-// position: a warp owns a chunk of kCompactChunk consecutive entries of C,
-// finds the first row reaching into it by binary search on C's row pointer
-// and walks the rows of the chunk, copying each overlap with all lanes
-// (coalesced reads and writes, equal work per warp whatever the row lengths).
+// position: a warp owns a chunk of kCompactChunk consecutive entries of C. It
+// finds the first row reaching into the chunk by a 32-way search on C's row
+// pointer (each round the lanes test 32 evenly spaced rows, so four rounds
+// cover a million rows), loads the row pointers, staging offsets and
+// overflow flags of the next 32 rows in one coalesced round trip, and walks
+// those rows copying each overlap with all lanes, four loads per lane issued
+// before their stores (equal work per warp whatever the row lengths).
 constexpr int64_t kCompactChunk = 2048;
 
 template <typename V>
@@ -495,27 +498,62 @@ __global__ void __launch_bounds__(256) k_compact_rows(int64_t n, int64_t c_nnz, 
     for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < nchunks; ch += warps) {
         const int64_t p0 = ch * kCompactChunk;
         const int64_t p1 = p0 + kCompactChunk < c_nnz ? p0 + kCompactChunk : c_nnz;
-        int64_t lo = 0, hi = n;   // last row r with c_rp[r] <= p0 (c_rp[n] = c_nnz > p0)
+        // last row r with c_rp[r] <= p0, in [lo, hi) (c_rp[0] = 0 <= p0, c_rp[n] = c_nnz > p0)
+        int64_t lo = 0, hi = n;
         while (hi - lo > 1) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (__ldg(c_rp + mid) <= p0) lo = mid;
-            else hi = mid;
+            const int64_t step = (hi - lo + 31) / 32;
+            const int64_t x = lo + lane * step;
+            const bool le = x < hi && __ldg(c_rp + x) <= p0;
+            const int cnt = __popc(__ballot_sync(kFull, le));   // rows lo, lo+step, ... that start at or before p0
+            const int64_t nlo = lo + (int64_t)(cnt - 1) * step;
+            const int64_t nhi = nlo + step < hi ? nlo + step : hi;
+            lo = nlo;
+            hi = nhi;
         }
         int64_t p = p0;
-        for (int64_t r = lo; p < p1 && r < n; ++r) {
-            const int64_t rb = __ldg(c_rp + r), re = __ldg(c_rp + r + 1);
-            const int64_t a = p > rb ? p : rb;
-            const int64_t b = p1 < re ? p1 : re;
-            if (b > a && !ovf[r]) {
-                const int64_t src = __ldg(stage_rp + r) + (a - rb);
-                const int64_t m = b - a;
-#pragma unroll 4
-                for (int64_t k = lane; k < m; k += 32) {
-                    cci[a + k] = __ldg(sci + src + k);
-                    cval[a + k] = __ldg(sval + src + k);
-                }
+        for (int64_t r0 = lo; p < p1 && r0 < n; r0 += 32) {
+            // rows r0 .. r0+31: lane l holds row r0+l's bounds, staging offset and flag
+            const int64_t rl = r0 + lane;
+            int64_t rb = c_nnz, re = c_nnz, sb = 0;
+            bool skip = true;
+            if (rl < n) {
+                rb = __ldg(c_rp + rl);
+                re = __ldg(c_rp + rl + 1);
+                sb = __ldg(stage_rp + rl);
+                skip = ovf[rl] != 0;
             }
-            if (re > p) p = re;
+            for (int j = 0; j < 32 && p < p1; ++j) {
+                const int64_t b0 = __shfl_sync(kFull, rb, j), e0 = __shfl_sync(kFull, re, j);
+                const int64_t s0 = __shfl_sync(kFull, sb, j);
+                const bool sk = __shfl_sync(kFull, skip ? 1 : 0, j) != 0;
+                const int64_t a = p > b0 ? p : b0;
+                const int64_t b = p1 < e0 ? p1 : e0;
+                if (b > a && !sk) {
+                    const int64_t src = s0 + (a - b0);
+                    const int m = (int)(b - a);
+                    for (int k0 = 0; k0 < m; k0 += 128) {
+                        int32_t ci[4];
+                        V va[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int k = k0 + 32 * u + lane;
+                            if (k < m) {
+                                ci[u] = __ldg(sci + src + k);
+                                va[u] = __ldg(sval + src + k);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int k = k0 + 32 * u + lane;
+                            if (k < m) {
+                                cci[a + k] = ci[u];
+                                cval[a + k] = va[u];
+                            }
+                        }
+                    }
+                }
+                if (e0 > p) p = e0;
+            }
         }
     }
 }

@@ -173,6 +173,23 @@ def test_dense_rows_windows(handle, ncols, dense_blocks, dtype):
     assert_matches_oracle(C, A, B)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_dense_windows_zero_values_and_cancellations(handle, dtype):
+    """Window columns whose products are all zero (+0.0 or -0.0) or cancel
+    exactly keep their entries: the structure comes from which columns were
+    hit, never from the values."""
+    A = random_csr(96, 64, 0.3, 55, values=dtype)
+    B = random_csr(64, 20000, 0.04, 56, values=dtype)
+    pick = np.array([1.0, -1.0, 0.0, -0.0])
+    for M, seed in ((A, 57), (B, 58)):
+        idx = np.random.default_rng(seed).integers(0, 4, M.val.size)
+        M.val[:] = pick[idx].astype(M.val.dtype)
+    C = run(handle, A, B, dense_ratio=1 << 20, dense_blocks=2)
+    assert_matches_oracle(C, A, B)
+    # every C entry whose products are all zero is still present
+    assert np.sum(C.val == 0) > 0
+
+
 def test_dense_rows_without_windows(handle):
     """Dense rows whose few products do not pay for slicing a tall B by column
     window take the global-memory hash instead."""
