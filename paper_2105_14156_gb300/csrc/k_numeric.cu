@@ -349,6 +349,8 @@ __device__ __forceinline__ void block_minmax(int &mn, int &mx, int *s_mm) {
     __syncthreads();
 }
 
+constexpr int kSpillUnroll = 8;
+
 template <typename V, int NT>
 __global__ void __launch_bounds__(NT) k_num_spill(Operands<V> op, const int *rows, int count, int *token,
                                                   HashCfg hc, float inv_load, int spill_tbits, int *keys_all,
@@ -412,12 +414,19 @@ __global__ void __launch_bounds__(NT) k_num_spill(Operands<V> op, const int *row
         } else if (t == 0 && tot != n_exp) {
             raise_err(err, kErrCountMismatch);
         }
+        // the table lives in global memory: every scan below keeps kSpillUnroll
+        // loads in flight per thread
         int mn = INT_MAX, mx = INT_MIN;
-        for (int s = t; s < T; s += NT) {
-            const int k = __ldcg(keys + s);
-            if (k != kEmpty) {
-                mn = min(mn, k);
-                mx = max(mx, k);
+        for (int s0 = t; s0 < T; s0 += kSpillUnroll * NT) {
+            int k[kSpillUnroll];
+#pragma unroll
+            for (int u = 0; u < kSpillUnroll; ++u) k[u] = s0 + u * NT < T ? __ldcg(keys + s0 + u * NT) : kEmpty;
+#pragma unroll
+            for (int u = 0; u < kSpillUnroll; ++u) {
+                if (k[u] != kEmpty) {
+                    mn = min(mn, k[u]);
+                    mx = max(mx, k[u]);
+                }
             }
         }
         block_minmax<NT>(mn, mx, s_mm);
@@ -426,25 +435,41 @@ __global__ void __launch_bounds__(NT) k_num_spill(Operands<V> op, const int *row
             for (long long w0 = ((long long)mn / WIN) * WIN; w0 <= (long long)mx; w0 += WIN) {
                 for (int w = t; w < win_words; w += NT) bm[w] = 0u;
                 __syncthreads();
-                for (int s = t; s < T; s += NT) {
-                    const long long k = __ldcg(keys + s);
-                    if (k != kEmpty && k >= w0 && k < w0 + WIN) {
-                        const int d = (int)(k - w0);
-                        atomicOr(bm + (d >> 5), 1u << (d & 31));
+                for (int s0 = t; s0 < T; s0 += kSpillUnroll * NT) {
+                    int k[kSpillUnroll];
+#pragma unroll
+                    for (int u = 0; u < kSpillUnroll; ++u)
+                        k[u] = s0 + u * NT < T ? __ldcg(keys + s0 + u * NT) : kEmpty;
+#pragma unroll
+                    for (int u = 0; u < kSpillUnroll; ++u) {
+                        if (k[u] != kEmpty && k[u] >= w0 && k[u] < w0 + WIN) {
+                            const int d = (int)(k[u] - w0);
+                            atomicOr(bm + (d >> 5), 1u << (d & 31));
+                        }
                     }
                 }
                 __syncthreads();
                 const int wt = bitmap_prefix<NT, NT>(bm, pre, win_words, sc.red);
                 __syncthreads();
-                for (int s = t; s < T; s += NT) {
-                    const long long k = __ldcg(keys + s);
-                    if (k != kEmpty && k >= w0 && k < w0 + WIN) {
-                        const int d = (int)(k - w0);
-                        const long long pos =
-                            done + pre[d >> 5] + __popc(bm[d >> 5] & ((1u << (d & 31)) - 1u));
-                        if (pos < n_exp) {
-                            out.c_ci[c0 + pos] = (int)k;
-                            out.c_val[c0 + pos] = __ldcg(vals + s);
+                for (int s0 = t; s0 < T; s0 += kSpillUnroll * NT) {
+                    int k[kSpillUnroll];
+                    V v[kSpillUnroll];
+#pragma unroll
+                    for (int u = 0; u < kSpillUnroll; ++u) {
+                        const int s = s0 + u * NT;
+                        k[u] = s < T ? __ldcg(keys + s) : kEmpty;
+                        v[u] = s < T ? __ldcg(vals + s) : V(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kSpillUnroll; ++u) {
+                        if (k[u] != kEmpty && k[u] >= w0 && k[u] < w0 + WIN) {
+                            const int d = (int)(k[u] - w0);
+                            const long long pos =
+                                done + pre[d >> 5] + __popc(bm[d >> 5] & ((1u << (d & 31)) - 1u));
+                            if (pos < n_exp) {
+                                out.c_ci[c0 + pos] = k[u];
+                                out.c_val[c0 + pos] = v[u];
+                            }
                         }
                     }
                 }
@@ -701,10 +726,25 @@ __global__ void __launch_bounds__(256) k_arena_compact(const int *rows, int coun
         const V *__restrict__ sv = (const V *)ar.val + src;
         int32_t *__restrict__ dci = c_ci + dst;
         V *__restrict__ dv = c_val + dst;
-#pragma unroll 4
-        for (int k = lane; k < n; k += 32) {
-            dci[k] = __ldg(sci + k);
-            dv[k] = __ldg(sv + k);
+        for (int k0 = 0; k0 < n; k0 += 32 * 8) {
+            int32_t ci[8];
+            V va[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = k0 + 32 * u + lane;
+                if (k < n) {
+                    ci[u] = __ldg(sci + k);
+                    va[u] = __ldg(sv + k);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = k0 + 32 * u + lane;
+                if (k < n) {
+                    dci[k] = ci[u];
+                    dv[k] = va[u];
+                }
+            }
         }
     }
 }
