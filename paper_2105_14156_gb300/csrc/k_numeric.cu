@@ -587,8 +587,14 @@ static void num_hash_go(const Operands<V> &op, const int *rows, int count, int *
     // the rows' distinct columns, T/2 at loads up to 0.5, else 3T/4 (loads up
     // to 0.75) when that fits
     int bcap = inv_load >= 2.f ? T / 2 : T - T / 4;
-    if (num_hash_smem<V>(hl.tbits, GS, bm_words, bcap) > lim) bcap = T / 2;
-    if (num_hash_smem<V>(hl.tbits, GS, bm_words, bcap) > lim) bcap = 0;
+    // every row of the bin has more than (T/2)/inv_load columns (else it would
+    // sit in a smaller bin): when that already makes the bitmap write-out
+    // their choice, the bucket arrays would only take shared memory (and
+    // resident groups) away
+    const long long n_min = (long long)((T / 2) / inv_load) + 1;
+    if (bm_words > 0 && (long long)bm_words <= (long long)bitmap_ratio * n_min) bcap = 0;
+    if (bcap > 0 && num_hash_smem<V>(hl.tbits, GS, bm_words, bcap) > lim) bcap = T / 2;
+    if (bcap > 0 && num_hash_smem<V>(hl.tbits, GS, bm_words, bcap) > lim) bcap = 0;
     const bool buckets = bcap > 0;
     const size_t smem = num_hash_smem<V>(hl.tbits, GS, bm_words, bcap);
     auto kern = k_num_hash<V, GS, NT>;
