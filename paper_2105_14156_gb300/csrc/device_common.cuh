@@ -125,7 +125,10 @@ struct Group {
 
     // Exclusive scan of v over the group; *total receives the sum.
     // scratch: kWarps ints private to the group (unused for GS = 32).
-    template <typename T>
+    // kFree = false leaves out the closing barrier that lets the scratch be
+    // written again: for callers that pass another group barrier before
+    // their next scan.
+    template <typename T, bool kFree = true>
     __device__ __forceinline__ static T excl_scan(T v, T *scratch, T *total) {
         T incl;
         if constexpr (sizeof(T) == 8) incl = (T)warp_incl_scan64((long long)v);
@@ -145,7 +148,7 @@ struct Group {
                 tot += x;
             }
             *total = tot;
-            sync();
+            if constexpr (kFree) sync();
             return off + incl - v;
         }
     }
@@ -423,7 +426,9 @@ __device__ __forceinline__ void group_products(const Operands<V> &op, int64_t ab
         // one scan of (entry has products, product count): count in the high half
         const long long packed = ((long long)(len > 0 ? 1 : 0) << 32) | (long long)len;
         long long tot64;
-        const long long ex = G::template excl_scan<long long>(packed, (long long *)sc.red64, &tot64);
+        // the scan's scratch is written again only in the next batch's scan,
+        // after the staging barrier below
+        const long long ex = G::template excl_scan<long long, false>(packed, (long long *)sc.red64, &tot64);
         const int cidx = (int)(ex >> 32);
         const int excl = (int)(ex & 0xffffffffll);
         const int nf = (int)(tot64 >> 32);
@@ -499,8 +504,10 @@ __device__ __forceinline__ void group_products(const Operands<V> &op, int64_t ab
                 }
             }
         }
-        G::sync();
+        // no barrier here: the next batch stages its entries only after the
+        // first barrier of its scan, which every warp reaches after its walk
     }
+    G::sync();
 }
 
 // ---------------------------------------------------------------------------

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(NT) k_num_window(Operands<V> op, const int *ro
     constexpr int kWarps = NT / 32;
     constexpr int kMaxChunks = kMaxWinCols / 1024;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ long long s_item, s_aoff;
+    __shared__ long long s_item[2], s_aoff;
     __shared__ int s_off, s_cnt;
     __shared__ int s_chunk[kMaxChunks + 1];
     const int words = cpc >> 5;
@@ -170,20 +170,29 @@ __global__ void __launch_bounds__(NT) k_num_window(Operands<V> op, const int *ro
     for (int j = t; j < cpc; j += NT) acc[j] = V(0);
     for (int w = t; w < words; w += NT) bm[w] = 0u;
     const int64_t items = (int64_t)count * nw;
+    // items are claimed one ahead (the claim's latency hides behind the
+    // current item); s_item[par] holds the claimed next item, written before
+    // the item's closing barrier and read after it
+    int par = 0;
+    if (t == 0) s_item[0] = (long long)atomicAdd(token, 1ull);
+    __syncthreads();
     for (;;) {
-        if (t == 0) s_item = (long long)atomicAdd(token, 1ull);
-        __syncthreads();
-        const int64_t item = s_item;
+        const int64_t item = s_item[par];
+        par ^= 1;
         if (item >= items) break;
+        if (t == 0) s_item[par] = (long long)atomicAdd(token, 1ull);
         const int r = (int)(item / nw);
         const int w = (int)(item - (int64_t)r * nw);
         const int i = rows[r];
         // capacity mode: skip a row that overflowed. In arena mode other blocks
         // update row_nnz[i] meanwhile: one thread reads it for the whole block.
-        if (t == 0) s_off = (out.row_nnz && out.row_nnz[i] < 0) ? 1 : 0;
-        __syncthreads();
-        bool skip = s_off != 0;
-        __syncthreads();
+        bool skip = false;
+        if (out.row_nnz) {
+            if (t == 0) s_off = out.row_nnz[i] < 0 ? 1 : 0;
+            __syncthreads();
+            skip = s_off != 0;
+            __syncthreads();
+        }
         int slot = -1;
         int64_t c0 = 0;
         int n_exp = 0;

@@ -77,16 +77,15 @@ __global__ void __launch_bounds__(NT) k_sym_dense(Operands<float> op, const int 
     using G = Group<NT, NT>;
     constexpr int kWarps = NT / 32;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_row;
+    __shared__ int s_row[2][1];
     unsigned *bm = (unsigned *)smem;
     const ProdScratch<float> sc = carve_prod_scratch<float, NT>(smem + (size_t)words * 4);
     const int t = threadIdx.x;
     const int lane = lane_id();
     const int wp = t >> 5;
+    RowClaim<G> claim(token, s_row);
     for (;;) {
-        if (t == 0) s_row = atomicAdd(token, 1);
-        __syncthreads();
-        const int r = s_row;
+        const int r = claim.next(count);
         if (r >= count) break;
         const int i = rows[r];
         int64_t slot = -1;
