@@ -41,6 +41,13 @@ constexpr int kBinEmpty = 0;
 constexpr int kBinDense = 13;
 constexpr int kBinSpill = 14;
 constexpr int kNumBins = 15;
+// The smallest bins run one thread per row (k_tiny.cu) and hold rows of at
+// most kTinyFlopPerSlot * 2^tbits products: tables up to 2^kTinySymTBits
+// slots in the symbolic phase, 2^kTinyNumTBits in the numeric one (the
+// sizes where that beat a warp per row, measured).
+constexpr int kTinySymTBits = 6;
+constexpr int kTinyNumTBits = 5;
+constexpr int kTinyFlopPerSlot = 2;
 __host__ __device__ constexpr int bin_of_tbits(int tbits) { return 1 + tbits - kMinTBits; }
 __host__ __device__ constexpr int tbits_of_bin(int bin) { return bin - 1 + kMinTBits; }
 

@@ -442,6 +442,7 @@ inline BinRule sym_rule(const smash_handle *h, int64_t ncols) {
     r.dense_ok = (h->params.sym_dense_ratio > 0 && ncols <= dense_bitmap_max_cols()) ? 1 : 0;
     r.dense_min = r.dense_ok ? (ncols + h->params.sym_dense_ratio - 1) / h->params.sym_dense_ratio : (1ll << 62);
     if (r.dense_min < 1) r.dense_min = 1;
+    r.tiny_tbits = kTinySymTBits;
     return r;
 }
 
@@ -467,6 +468,7 @@ inline BinRule num_rule(const smash_handle *h, int64_t ncols, int dtype) {
         --mt;
     }
     r.max_tbits = mt;
+    r.tiny_tbits = kTinyNumTBits;
     return r;
 }
 

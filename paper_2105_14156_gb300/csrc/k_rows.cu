@@ -14,10 +14,15 @@
 
 namespace smash {
 
-__device__ __forceinline__ int bin_for(long long size, const BinRule &r) {
+__device__ __forceinline__ int bin_for(long long size, long long f, const BinRule &r) {
     if (size <= 0) return kBinEmpty;
     if (r.dense_ok && size >= r.dense_min) return kBinDense;
-    const int tb = table_bits(size, r.inv_load);
+    int tb = table_bits(size, r.inv_load);
+    // the thread-per-row bins (k_tiny.cu) take rows of at most
+    // kTinyFlopPerSlot * T products; a row with more goes to the first bin
+    // above them
+    if (tb <= r.tiny_tbits && f > ((long long)kTinyFlopPerSlot << tb) && r.tiny_tbits + 1 <= r.max_tbits)
+        tb = r.tiny_tbits + 1;
     if (tb <= r.max_tbits) return bin_of_tbits(tb);
     return r.dense_ok ? kBinDense : kBinSpill;
 }
@@ -82,7 +87,7 @@ __device__ __forceinline__ void bin_rows(bool valid, int64_t i, int64_t len, lon
     const int lane = lane_id();
     int b = kBinEmpty;
     if (valid) {
-        b = bin_for(size, rule);
+        b = bin_for(size, f, rule);
         bb.bin[i] = (uint8_t)b;
         if (nnz_out && b == kBinEmpty) nnz_out[i] = 0;
     }

@@ -12,6 +12,7 @@ struct BinRule {
     int max_tbits;      // largest shared-memory table (log2 slots)
     int dense_ok;       // dense accumulator allowed (column bitmap fits shared memory)
     int64_t dense_min;  // size >= dense_min goes dense (when dense_ok)
+    int tiny_tbits;     // bins of tables up to 2^tiny_tbits slots run one thread per row
 };
 
 // Raw device view of a CSR operand pair (values as void*).
@@ -156,6 +157,13 @@ struct NumOut {
 void launch_num_hash(int dtype, const RawOperands &op, const int *rows, int count, int *token,
                      const HashLaunch &hl, float inv_load, int bitmap_ratio, const NumOut &out, int *err,
                      cudaStream_t s);
+// Thread-per-row bins (tbits <= BinRule::tiny_tbits, k_tiny.cu): list length of a bin, and
+// the symbolic count / numeric merge of its rows.
+int tiny_list_len(int tbits, float max_load);
+void launch_sym_tiny(const RawOperands &op, const int *rows, int count, int tbits, float max_load, int sms,
+                     int *nnz_out, int *err, cudaStream_t s);
+void launch_num_tiny(int dtype, const RawOperands &op, const int *rows, int count, int tbits, float max_load,
+                     int sms, const NumOut &out, int *err, cudaStream_t s);
 // Column windows of the dense rows (k_split.cu): slices of B regrouped by
 // window of cpc columns; woff[B.rows][nslices+1] (nslices > 1 only).
 struct BSlices {

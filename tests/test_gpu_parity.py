@@ -190,6 +190,30 @@ def test_dense_windows_zero_values_and_cancellations(handle, dtype):
     assert np.sum(C.val == 0) > 0
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("max_load", [0.5, 0.7])
+def test_tiny_rows_thread_per_row(handle, dtype, max_load):
+    """Rows of a few products (bins of at most 128 slots) merged one thread per
+    row: unsorted rows of B with duplicate columns, empty rows, and rows whose
+    many products collapse onto few columns (binned one bin up)."""
+    A = random_csr(3000, 2000, 0.002, 81, values=dtype)
+    B = random_csr(2000, 5000, 0.001, 82, values=dtype, sort_cols=False, dup_frac=0.2)
+    C = run(handle, A, B, max_load=max_load)
+    assert_matches_oracle(C, A, B)
+    # few columns of B: every row's bound is at most 8 columns, its products many
+    A2 = random_csr(400, 300, 0.2, 83, values=dtype)
+    B2 = random_csr(300, 8, 0.5, 84, values=dtype)
+    C2 = run(handle, A2, B2, max_load=max_load)
+    assert_matches_oracle(C2, A2, B2)
+
+
+def test_tiny_rows_integer_values_exact(handle):
+    """Small-integer float32 data: the thread-per-row merge is exact."""
+    A = rmat(12, 2, GRAPH500_ABCD, seed=85, values="int4")
+    C = run(handle, A, A)
+    assert_matches_oracle(C, A, A, exact=True)
+
+
 def test_dense_rows_without_windows(handle):
     """Dense rows whose few products do not pay for slicing a tall B by column
     window take the global-memory hash instead."""
