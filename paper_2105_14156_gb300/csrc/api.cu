@@ -286,7 +286,7 @@ int run_symbolic(smash_handle *h, const RawOperands &op, int64_t n, Plan &pl, in
             LaunchTimer lt(h, s, "sym_spill", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
             launch_sym_spill(op, rows, counts[b], tok, hl, rule.inv_load, pl.bound, tb, (int *)h->tables.ptr,
                              nnz_out, err, s);
-        } else if (tbits_of_bin(b) <= rule.tiny_tbits) {
+        } else if (tbits_of_bin(b) <= rule.tiny_tbits && counts[b] >= tiny_min_rows(h)) {
             LaunchTimer lt(h, s, "sym_tiny", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);
             launch_sym_tiny(op, rows, counts[b], tbits_of_bin(b), h->params.max_load, h->sms, nnz_out, err, s);
         } else {
@@ -426,7 +426,7 @@ int run_bins(smash_handle *h, const RawOperands &op, int64_t n, int dt, const Nu
             if ((st = ensure(h, h->tables, need, s))) return st;
             LaunchTimer lt(h, s, "num_spill", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
             launch_num_spill(dt, op, rows, counts[b], tok, hl, rule.inv_load, tb, h->tables.ptr, out, err, s);
-        } else if (tbits_of_bin(b) <= rule.tiny_tbits) {
+        } else if (tbits_of_bin(b) <= rule.tiny_tbits && counts[b] >= tiny_min_rows(h)) {
             LaunchTimer lt(h, s, "num_tiny", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);
             launch_num_tiny(dt, op, rows, counts[b], tbits_of_bin(b), h->params.max_load, h->sms, out, err, s);
         } else {

@@ -432,6 +432,11 @@ inline int dense_blocks_of(const smash_handle *h, int dtype) {
     return b > 0 ? b : (dtype ? 2 : 4);
 }
 
+// A thread-per-row bin pays only with enough rows to fill the GPU (its rows'
+// dependent loads are hidden by other rows, not by other lanes of a row):
+// fewer rows than one 128-thread block per SM take the warp-per-row hash.
+inline int tiny_min_rows(const smash_handle *h) { return h->sms * 128; }
+
 inline BinRule sym_rule(const smash_handle *h, int64_t ncols) {
     BinRule r;
     r.inv_load = 1.0f / h->params.max_load;

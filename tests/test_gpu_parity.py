@@ -196,8 +196,9 @@ def test_tiny_rows_thread_per_row(handle, dtype, max_load):
     """Rows of a few products (bins of at most 128 slots) merged one thread per
     row: unsorted rows of B with duplicate columns, empty rows, and rows whose
     many products collapse onto few columns (binned one bin up)."""
-    A = random_csr(3000, 2000, 0.002, 81, values=dtype)
-    B = random_csr(2000, 5000, 0.001, 82, values=dtype, sort_cols=False, dup_frac=0.2)
+    # enough rows (more than one 128-thread block per SM) for the thread-per-row path
+    A = random_csr(60000, 20000, 0.00015, 81, values=dtype)
+    B = random_csr(20000, 50000, 0.00006, 82, values=dtype, sort_cols=False, dup_frac=0.2)
     C = run(handle, A, B, max_load=max_load)
     assert_matches_oracle(C, A, B)
     # few columns of B: every row's bound is at most 8 columns, its products many
