@@ -164,6 +164,24 @@ def test_learned_rectangular_and_empty_rows(handle, trained):
         assert_matches_oracle(Ch, A, B)
 
 
+@pytest.mark.parametrize("margin", [0.15, -0.6, 3.0])
+@pytest.mark.parametrize("values", ["f32", "f64"])
+def test_learned_many_tiny_rows(handle, trained, margin, values):
+    """Enough rows of a few products for the thread-per-row bins in capacity
+    mode: rows that fit their predicted room are written there, the others
+    (forced by the negative margin) overflow to the exact fallback."""
+    from paper_2105_14156_gb300 import smash
+    from tests.helpers import random_csr
+    model, _, _ = trained
+    A = random_csr(60000, 20000, 0.00015, 91, values=values)
+    B = random_csr(20000, 50000, 0.00006, 92, values=values, sort_cols=False, dup_frac=0.2)
+    C, stats, owner = handle.spgemm_learned(smash.to_device(A), smash.to_device(B), model, margin=margin)
+    Ch = C.to_host()
+    owner.free()
+    assert_matches_oracle(Ch, A, B)
+    assert stats["c_nnz"] == Ch.col_idx.size
+
+
 @pytest.mark.parametrize("margin", [0.15, -0.9, 3.0])
 @pytest.mark.parametrize("dense_blocks", [2, 4])
 def test_learned_dense_rows_in_arena(handle, trained, margin, dense_blocks):
