@@ -5,10 +5,11 @@
 // with more products are binned one bin up, see bin_for). For such rows a
 // hash table per warp costs hundreds of instructions of set-up, clearing and
 // write-out per row while the row has a few dozen products. Here each thread
-// merges its row's products (Gustavson's row-by-row expansion, Algorithm
-// SpGEMM) into a column-sorted list in shared memory by insertion: the list
-// is the row's accumulator and, being sorted, also its write-back order
-// (Write-back Phase), so no separate sort is needed. Entry e of thread t's
+// merges its row's products (the row-wise product of the SMASH HASHING
+// algorithm, with a sorted list in place of its table) into a column-sorted
+// list in shared memory by insertion: the list is the row's accumulator and,
+// being sorted, also its write-back order (SMASH WRITEBACK), so no separate
+// sort is needed. Entry e of thread t's
 // list sits at e * NT + t: consecutive threads use consecutive banks.
 //
 // Every index read from the inputs is checked (error word, never a fault); a
