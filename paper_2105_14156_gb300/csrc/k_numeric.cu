@@ -37,16 +37,19 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_row[2][G::kGroups];
     const int T = 1 << tbits;
-    const size_t grp_bytes = (size_t)T * (4 + sizeof(V)) + (bsh >= 0 ? bucket_bytes<V>(T, bcap) : 0);
+    if (bsh < 0) bcap = 0;
+    // group layout (hash_group_bytes): keys, values, bucket counters, then the
+    // product staging, whose room the write-out's grouped pairs reuse
+    const size_t grp_bytes = hash_group_bytes<V, GS>(T, bcap);
     unsigned char *gb = smem + (size_t)G::gid() * grp_bytes;
     int *keys = (int *)gb;
     V *vals = (V *)(gb + (size_t)T * 4);
-    V *gv = (V *)(gb + (size_t)T * (4 + sizeof(V)));       // bcap grouped values
-    int *bc = (int *)(gv + bcap);                           // T/4 bucket counters
-    int *gk = bc + (T >> 2);                                // bcap grouped columns
-    unsigned char *scr = smem + (size_t)G::kGroups * grp_bytes + (size_t)G::gid() * num_scratch_bytes<V, GS>();
-    const ProdScratch<V> sc = carve_prod_scratch<V, GS>(scr);
-    unsigned *bm = (unsigned *)(smem + (size_t)G::kGroups * (grp_bytes + num_scratch_bytes<V, GS>()));
+    int *bc = (int *)(gb + (size_t)T * (4 + sizeof(V)));    // T/4 bucket counters
+    unsigned char *uni = (unsigned char *)(bc + (bcap > 0 ? (T >> 2) : 0));
+    V *gv = (V *)uni;                                       // bcap grouped values
+    int *gk = (int *)(uni + (size_t)bcap * sizeof(V));      // bcap grouped columns
+    const ProdScratch<V> sc = carve_prod_scratch<V, GS>(uni);
+    unsigned *bm = (unsigned *)(smem + (size_t)G::kGroups * grp_bytes);
     int *pre = (int *)(bm + bm_words);
     const int t = G::tid();
     bool clean = false;   // the table is EMPTY / 0 (left so by the bucket write-out)
@@ -549,18 +552,17 @@ template <typename V>
 static size_t num_hash_smem(int tbits, int gs, int bm_words, int bcap = 0) {
     const int nt = block_threads(gs);
     const int groups = nt / gs;
-    size_t scr = 0;
-    switch (gs) {
-        case 32: scr = num_scratch_bytes<V, 32>(); break;
-        case 64: scr = num_scratch_bytes<V, 64>(); break;
-        case 128: scr = num_scratch_bytes<V, 128>(); break;
-        case 256: scr = num_scratch_bytes<V, 256>(); break;
-        case 512: scr = num_scratch_bytes<V, 512>(); break;
-        default: scr = num_scratch_bytes<V, 1024>(); break;
-    }
     const int T = 1 << tbits;
-    return (size_t)groups * ((size_t)(4 + sizeof(V)) * T + (bcap > 0 ? bucket_bytes<V>(T, bcap) : 0)) +
-           (size_t)groups * scr + (size_t)bm_words * 8;
+    size_t grp = 0;
+    switch (gs) {
+        case 32: grp = hash_group_bytes<V, 32>(T, bcap); break;
+        case 64: grp = hash_group_bytes<V, 64>(T, bcap); break;
+        case 128: grp = hash_group_bytes<V, 128>(T, bcap); break;
+        case 256: grp = hash_group_bytes<V, 256>(T, bcap); break;
+        case 512: grp = hash_group_bytes<V, 512>(T, bcap); break;
+        default: grp = hash_group_bytes<V, 1024>(T, bcap); break;
+    }
+    return (size_t)groups * grp + (size_t)bm_words * 8;
 }
 
 bool num_hash_bitmap_fits(int dtype, int tbits, int ncols) {

@@ -127,12 +127,6 @@ __device__ __forceinline__ void writeout_bitonic(int *keys, V *vals, int T, int 
 // that groups them also returns the table's occupied slots to EMPTY / 0, so
 // the next row needs no clearing. A pair's position is its bucket's start plus
 // the number of smaller columns in its bucket. Needs tot <= cap.
-template <typename V>
-__host__ __device__ constexpr size_t bucket_bytes(int T, int cap) {
-    // bc: T/4 ints, gv: cap values, gk: cap ints
-    return (size_t)(T >> 2) * 4 + (size_t)cap * (sizeof(V) + 4);
-}
-
 template <typename V, int GS, int NT>
 __device__ __forceinline__ void writeout_bucket(int *keys, V *vals, int T, int *bc, int *gk, V *gv, int sh, int tot,
                                                 int n_exp, const NumOutT<V> &out, int64_t c0, int *red) {
@@ -238,6 +232,18 @@ __device__ __forceinline__ void writeout_bitmap(const int *keys, const V *vals, 
 template <typename V, int GS>
 __host__ __device__ constexpr size_t num_scratch_bytes() {
     return (prod_scratch_bytes<V, GS>() + 15) & ~size_t(15);
+}
+
+// Shared memory of one group of the shared-memory hash kernel: keys[T],
+// vals[T], with buckets (bcap > 0) the counters bc[T/4], then one region
+// used first by the product staging (while the row's products are merged)
+// and then by the write-out's grouped pairs gv[bcap], gk[bcap].
+template <typename V, int GS>
+__host__ __device__ constexpr size_t hash_group_bytes(int T, int bcap) {
+    const size_t pairs = (size_t)bcap * (sizeof(V) + 4);
+    const size_t scr = num_scratch_bytes<V, GS>();
+    const size_t uni = ((pairs > scr ? pairs : scr) + 15) & ~size_t(15);
+    return (size_t)T * (4 + sizeof(V)) + (bcap > 0 ? (size_t)(T >> 2) * 4 : 0) + uni;
 }
 
 }  // namespace smash
