@@ -233,7 +233,8 @@ def timed(fn, steps, flush, stream):
 
 
 def kernel_bytes(t, vb, nnz_b, total_products):
-    """Algorithmic bytes of one timed launch group (measurement)."""
+    """Algorithmic bytes of one timed launch group: A, B and C each moved once,
+    B's bytes shared out over the launch groups by their products."""
     rows, a_nnz, prods, c_nnz = t["rows"], t["a_nnz"], t["products"], t["c_nnz"]
     share = prods / total_products if total_products else 0.0
     if t["name"].startswith("sym_") or t["name"] == "num_dense_count":

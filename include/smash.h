@@ -84,7 +84,11 @@ typedef struct {
     int32_t sym_dense_blocks; /* symbolic dense rows: resident blocks per SM of the bitmap kernel (1, 2, 4
                                  or 8; fewer when their bitmaps do not fit); 0 (default): the most resident
                                  threads, then the most blocks */
-    int32_t reserved[5];
+    int32_t warp_rows;       /* rows served by one warp (tables of at most 32 << group_shift slots):
+                                1 (default): products enumerated from registers, compare-and-swap-first
+                                probing, write-out driven by the list of claimed slots;
+                                0: the shared-memory staged enumeration of the thread-group kernels */
+    int32_t reserved[4];
 } smash_params;
 
 /* Per-call statistics (the last symbolic or numeric call of the handle). */
@@ -253,6 +257,15 @@ int smash_model_load(smash_model *m, const char *path);
 /* Features of every row of C = A*B (device float[A.rows * 6], row-major). */
 int smash_row_features(smash_handle *h, const smash_csr *A, const smash_csr *B, float *feats, void *stream);
 
+/* Training samples of the row-size model from C = A*B, made by the method
+ * itself: the exact symbolic phase counts nnz(C_i) of every row; every row
+ * with at least one product gives one sample, in row order: its six features
+ * (feats, device float[A.rows * 6] of room) and the target log1p(nnz(C_i))
+ * (targets, device float[A.rows] of room). *count (host) receives the number
+ * of samples written. Synchronises the stream. */
+int smash_training_rows(smash_handle *h, const smash_csr *A, const smash_csr *B, float *feats, float *targets,
+                        int64_t *count, void *stream);
+
 /* Train on n samples: feats device float[n*6] (raw features as produced by
  * smash_row_features), targets device float[n] (log1p of the exact row
  * counts). The normalisation is set from the data's mean and standard
@@ -285,6 +298,8 @@ int smash_mlp_predict_tc(smash_handle *h, const smash_model *m, const float *fea
  * numeric); finally C is assembled. C->row_ptr, C->col_idx and C->val are
  * allocated through the handle's allocator and owned by the caller (release
  * them with the same allocator); C->rows, cols and nnz are set.
+ * m == NULL: the same one-pass pipeline without the network, every row sized
+ * by its bound min(flop_i, cols(B)) (margin ignored; no row can overflow).
  * margin > -1 (a negative margin forces under-prediction: a test hook).
  * stats may be NULL. Synchronises the stream.
  */

@@ -10,6 +10,9 @@ with gcc and marshals numpy arrays through ctypes.
 Functions and the passage each follows:
   row_flops  -- per-row product count of Gustavson's first pass
                 ("Window Distribution Phase": count the FMAs of each row).
+  row_nnz    -- nnz(C_i) of the selected rows: the number of distinct columns
+                j with at least one product a_ik*b_kj (Eq. row_wise), the
+                structure half of spgemm without the values.
   spgemm     -- C = A*B by Eq. inner_product / Eq. row_wise; structure = every
                 (i, j) hit by a product; values exact-then-rounded; the scale
                 s_ij = sum |a_ik||b_kj| for tolerance checks.
@@ -86,6 +89,20 @@ def row_flops(A, B) -> np.ndarray:
     out = np.zeros(A.rows, dtype=np.int64)
     lib.oracle_row_flops(A.rows, _p(a_rp), _p(a_ci), _p(b_rp), _p(out))
     return out
+
+
+def row_nnz(A, B, rows=None) -> np.ndarray:
+    """nnz(C_i) for all rows (rows=None) or for the listed rows of A, in order."""
+    if A.cols != B.rows:
+        raise ValueError("shape mismatch: A.cols != B.rows")
+    lib = _load()
+    a_rp, a_ci, b_rp, b_ci = _arrays(A, B)
+    sel = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    nsel = A.rows if sel is None else sel.size
+    nnz = np.zeros(nsel, dtype=np.int64)
+    if lib.oracle_count(nsel, _p(sel), B.cols, _p(a_rp), _p(a_ci), _p(b_rp), _p(b_ci), _p(nnz)) < 0:
+        raise MemoryError("oracle_count")
+    return nnz
 
 
 def spgemm(A, B, rows=None, exact_int: bool = False) -> OracleResult:

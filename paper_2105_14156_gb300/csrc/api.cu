@@ -21,6 +21,7 @@ int smash_default_params(smash_params *p) {
     p->sym_dense_ratio = 64;
     p->dense_blocks = 0;
     p->sym_dense_blocks = 0;
+    p->warp_rows = 1;
     return SMASH_OK;
 }
 
@@ -89,11 +90,11 @@ int smash_destroy(smash_handle *h) {
         release(h, h->wslot);
         release(h, h->wcnt);
         release(h, h->stage);
-    release(h, h->arena);
         release(h, h->arena);
         release(h, h->learn);
         batched_release(h);
         release(h, h->err);
+        destroy_streams(h);
         if (h->host) cudaFreeHost(h->host);
     }
     delete h;
@@ -256,43 +257,61 @@ int run_symbolic(smash_handle *h, const RawOperands &op, int64_t n, Plan &pl, in
     int counts[16], offsets[17];
     long long maxsize[16], stats[4], sums[48];
     if ((st = fetch_bins(h, pl, s, counts, offsets, maxsize, stats, sums))) return st;
-    for (int b = 1; b < kNumBins; ++b) {
+    // buffers of the dense and spill bins, before the launches fork
+    const int nsub = (int)((op.ncols + kSubCols - 1) / kSubCols);
+    int spill_tb = 0;
+    if (counts[kBinDense]) {
+        if ((st = ensure(h, h->wslot, sizeof(int) * (size_t)n, s))) return st;
+        if ((st = ensure(h, h->wcnt, sizeof(uint16_t) * (size_t)counts[kBinDense] * nsub, s))) return st;
+        if (cudaMemsetAsync(h->wslot.ptr, 0xff, sizeof(int) * (size_t)n, s) != cudaSuccess) return SMASH_ERR_CUDA;
+    }
+    if (counts[kBinSpill]) {
+        spill_tb = table_bits(maxsize[kBinSpill], rule.inv_load);
+        const HashLaunch hl = hash_launch(h, spill_tb, op.ncols);
+        if ((st = ensure(h, h->tables, ((size_t)sym_spill_grid(hl) << spill_tb) * sizeof(int), s))) return st;
+    }
+    int order[kNumBins];
+    const int nb = bin_order(sums, order);
+    Fork fk(h, s);
+    int q = 0;
+    for (int x = 0; x < nb; ++x) {
+        const int b = order[x];
         if (!counts[b]) continue;
+        cudaStream_t bs = fk.get(q++);
         const int *rows = pl.bb.rows + offsets[b];
         int *tok = pl.bb.tokens + b;
         if (b == kBinDense) {
             // the bitmap pass also counts each row's columns per block of
             // kSubCols columns, for the numeric dense kernel
-            const int nsub = (int)((op.ncols + kSubCols - 1) / kSubCols);
-            if ((st = ensure(h, h->wslot, sizeof(int) * (size_t)n, s))) return st;
-            if ((st = ensure(h, h->wcnt, sizeof(uint16_t) * (size_t)counts[b] * nsub, s))) return st;
-            if (cudaMemsetAsync(h->wslot.ptr, 0xff, sizeof(int) * (size_t)n, s) != cudaSuccess) return SMASH_ERR_CUDA;
             WinCount wc;
             wc.wslot = (int *)h->wslot.ptr;
             wc.wcnt = (uint16_t *)h->wcnt.ptr;
             wc.nsub = nsub;
             {
                 const HashLaunch hl = hash_launch(h, 0, op.ncols);
-                LaunchTimer lt(h, s, "sym_dense", b, sym_dense_threads(hl, op.ncols), counts[b], sums[b], sums[16 + b],
+                LaunchTimer lt(h, bs, "sym_dense", b, sym_dense_threads(hl, op.ncols), counts[b], sums[b], sums[16 + b],
                                sums[32 + b]);
-                launch_sym_dense(op, rows, counts[b], tok, hl, wc, nnz_out, NumCheck{}, err, s);
+                launch_sym_dense(op, rows, counts[b], tok, hl, wc, nnz_out, NumCheck{}, err, bs);
             }
             wcache_set(h, op, nsub, counts[b]);
         } else if (b == kBinSpill) {
-            const int tb = table_bits(maxsize[b], rule.inv_load);
-            const HashLaunch hl = hash_launch(h, tb, op.ncols);
-            const size_t need = ((size_t)sym_spill_grid(hl) << tb) * sizeof(int);
-            if ((st = ensure(h, h->tables, need, s))) return st;
-            LaunchTimer lt(h, s, "sym_spill", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
-            launch_sym_spill(op, rows, counts[b], tok, hl, rule.inv_load, pl.bound, tb, (int *)h->tables.ptr,
-                             nnz_out, err, s);
+            const HashLaunch hl = hash_launch(h, spill_tb, op.ncols);
+            LaunchTimer lt(h, bs, "sym_spill", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
+            launch_sym_spill(op, rows, counts[b], tok, hl, rule.inv_load, pl.bound, spill_tb, (int *)h->tables.ptr,
+                             nnz_out, err, bs);
         } else if (tbits_of_bin(b) <= rule.tiny_tbits && counts[b] >= tiny_min_rows(h)) {
-            LaunchTimer lt(h, s, "sym_tiny", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);
-            launch_sym_tiny(op, rows, counts[b], tbits_of_bin(b), h->params.max_load, h->sms, nnz_out, err, s);
+            LaunchTimer lt(h, bs, "sym_tiny", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);
+            launch_sym_tiny(op, rows, counts[b], tbits_of_bin(b), h->params.max_load, h->sms, nnz_out, err, bs);
         } else {
             const HashLaunch hl = hash_launch(h, tbits_of_bin(b), op.ncols);
-            LaunchTimer lt(h, s, "sym_hash", b, group_threads(hl), counts[b], sums[b], sums[16 + b], sums[32 + b]);
-            launch_sym_hash(op, rows, counts[b], tok, hl, nnz_out, err, s);
+            if (use_warp_rows(h, hl, -1)) {
+                LaunchTimer lt(h, bs, "sym_warp", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);
+                launch_sym_warp(op, rows, counts[b], tok, hl, nnz_out, err, bs);
+            } else {
+                LaunchTimer lt(h, bs, "sym_hash", b, group_threads(hl), counts[b], sums[b], sums[16 + b],
+                               sums[32 + b]);
+                launch_sym_hash(op, rows, counts[b], tok, hl, nnz_out, err, bs);
+            }
         }
         if ((st = last_cuda_status())) return st;
     }
@@ -369,70 +388,102 @@ int run_bins(smash_handle *h, const RawOperands &op, int64_t n, int dt, const Nu
     const long long *maxsize = bp.maxsize;
     const long long *sums = bp.sums;
     const size_t vsz = dt ? 8 : 4;
-    for (int b = 1; b < kNumBins; ++b) {
+    // Dense rows take column windows when their products pay for slicing B
+    // (a pass over B's rows and entries); otherwise the global hash. Their
+    // counts and the slices of B are prepared on s before the bins fork.
+    const int bd = kBinDense;
+    int cpc = 0, nw = 0;
+    const bool windows = counts[bd] && dense_windows(h, op, dt, sums[16 + bd], cpc, nw);
+    HashLaunch hld = hash_launch(h, 0, op.ncols);
+    hld.dense_blocks = dense_blocks_of(h, dt);
+    WinCount wc;
+    BSlices sl;
+    if (windows) {
+        if (!arena) {
+            // 1. per-block column counts of the dense rows: from the symbolic
+            //    phase of the same operands, else counted here (and sizes checked)
+            const int nsub = (int)((op.ncols + kSubCols - 1) / kSubCols);
+            if (!wcache_matches(h, op) || h->wcache.nsub != nsub) {
+                if ((st = ensure(h, h->wslot, sizeof(int) * (size_t)n, s))) return st;
+                if (cudaMemsetAsync(h->wslot.ptr, 0xff, sizeof(int) * (size_t)n, s) != cudaSuccess)
+                    return SMASH_ERR_CUDA;
+                wcache_set(h, op, nsub, 0);
+            }
+            const int64_t base = h->wcache.slots;
+            if ((st = ensure_keep(h, h->wcnt, sizeof(uint16_t) * (size_t)(base + counts[bd]) * nsub,
+                                  sizeof(uint16_t) * (size_t)base * nsub, s)))
+                return st;
+            wc.wslot = (int *)h->wslot.ptr;
+            wc.wcnt = (uint16_t *)h->wcnt.ptr;
+            wc.nsub = nsub;
+            wc.slot_base = base;
+            wc.skip_slotted = 1;
+            NumCheck nc;
+            nc.c_rp = out.c_rp;
+            nc.c_nnz = out.c_nnz;
+            nc.row_nnz = out.row_nnz;
+            {
+                LaunchTimer lt(h, s, "num_dense_count", bd, sym_dense_threads(hld, op.ncols), counts[bd], sums[bd],
+                               sums[16 + bd], sums[32 + bd]);
+                launch_sym_dense(op, pl.bb.rows + offsets[bd], counts[bd], pl.bb.tokens + bd, hld, wc, nullptr, nc,
+                                 err, s);
+            }
+            h->wcache.slots = base + counts[bd];
+        }
+        // 2. column windows: slices of B
+        if ((st = window_plan(h, op, dt, cpc, nw, s, sl))) return st;
+    }
+    // global-memory tables of the spill bin (and of dense rows without windows)
+    int spill_tb = 0;
+    for (int b : {(int)kBinSpill, (int)kBinDense}) {
+        if (!counts[b] || (b == kBinDense && windows)) continue;
+        const int tb = table_bits(maxsize[b], rule.inv_load);
+        spill_tb = tb > spill_tb ? tb : spill_tb;
+    }
+    if (spill_tb) {
+        const HashLaunch hl = hash_launch(h, spill_tb, op.ncols);
+        if ((st = ensure(h, h->tables, ((size_t)num_spill_grid(dt, hl) << spill_tb) * (4 + vsz), s))) return st;
+    }
+    // both spill launches (when there are two) share the tables: one stream
+    cudaStream_t spill_stream = nullptr;
+    int order[kNumBins];
+    const int nb = bin_order(sums, order);
+    Fork fk(h, s);
+    int q = 0;
+    for (int x = 0; x < nb; ++x) {
+        const int b = order[x];
         if (!counts[b]) continue;
         const int *rows = pl.bb.rows + offsets[b];
         int *tok = pl.bb.tokens + b;
-        // Dense rows take column windows when their products pay for slicing
-        // B (a pass over B's rows and entries); otherwise the global hash.
-        int cpc = 0, nw = 0;
-        const bool windows = b == kBinDense && dense_windows(h, op, dt, sums[16 + b], cpc, nw);
         if (b == kBinDense && windows) {
-            HashLaunch hl = hash_launch(h, 0, op.ncols);
-            hl.dense_blocks = dense_blocks_of(h, dt);
-            WinCount wc;
-            if (!arena) {
-                // 1. per-block column counts of the dense rows: from the symbolic
-                //    phase of the same operands, else counted here (and sizes checked)
-                const int nsub = (int)((op.ncols + kSubCols - 1) / kSubCols);
-                if (!wcache_matches(h, op) || h->wcache.nsub != nsub) {
-                    if ((st = ensure(h, h->wslot, sizeof(int) * (size_t)n, s))) return st;
-                    if (cudaMemsetAsync(h->wslot.ptr, 0xff, sizeof(int) * (size_t)n, s) != cudaSuccess)
-                        return SMASH_ERR_CUDA;
-                    wcache_set(h, op, nsub, 0);
-                }
-                const int64_t base = h->wcache.slots;
-                if ((st = ensure_keep(h, h->wcnt, sizeof(uint16_t) * (size_t)(base + counts[b]) * nsub,
-                                      sizeof(uint16_t) * (size_t)base * nsub, s)))
-                    return st;
-                wc.wslot = (int *)h->wslot.ptr;
-                wc.wcnt = (uint16_t *)h->wcnt.ptr;
-                wc.nsub = nsub;
-                wc.slot_base = base;
-                wc.skip_slotted = 1;
-                NumCheck nc;
-                nc.c_rp = out.c_rp;
-                nc.c_nnz = out.c_nnz;
-                nc.row_nnz = out.row_nnz;
-                {
-                    LaunchTimer lt(h, s, "num_dense_count", b, sym_dense_threads(hl, op.ncols), counts[b], sums[b],
-                                   sums[16 + b], sums[32 + b]);
-                    launch_sym_dense(op, rows, counts[b], tok, hl, wc, nullptr, nc, err, s);
-                }
-                h->wcache.slots = base + counts[b];
-            }
-            // 2. column windows: slices of B
-            BSlices sl;
-            if ((st = window_plan(h, op, dt, cpc, nw, s, sl))) return st;
-            // 3. (row, window) items
-            LaunchTimer lt(h, s, "num_dense_window", b, 1024 / hl.dense_blocks, counts[b], sums[b], sums[16 + b],
+            cudaStream_t bs = fk.get(q++);
+            // (row, window) items
+            LaunchTimer lt(h, bs, "num_dense_window", b, 1024 / hld.dense_blocks, counts[b], sums[b], sums[16 + b],
                            sums[32 + b]);
-            launch_num_window(dt, op, rows, counts[b], (unsigned long long *)h->split.ptr, hl, sl, wc,
-                              arena ? *arena : WinArena{}, out, err, s);
+            launch_num_window(dt, op, rows, counts[b], (unsigned long long *)h->split.ptr, hld, sl, wc,
+                              arena ? *arena : WinArena{}, out, err, bs);
         } else if (b == kBinSpill || b == kBinDense) {
-            const int tb = table_bits(maxsize[b], rule.inv_load);
-            const HashLaunch hl = hash_launch(h, tb, op.ncols);
-            const size_t need = ((size_t)num_spill_grid(dt, hl) << tb) * (4 + vsz);
-            if ((st = ensure(h, h->tables, need, s))) return st;
-            LaunchTimer lt(h, s, "num_spill", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
-            launch_num_spill(dt, op, rows, counts[b], tok, hl, rule.inv_load, tb, h->tables.ptr, out, err, s);
+            if (!spill_stream) spill_stream = fk.get(q++);
+            cudaStream_t bs = spill_stream;
+            const HashLaunch hl = hash_launch(h, spill_tb, op.ncols);
+            LaunchTimer lt(h, bs, "num_spill", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
+            launch_num_spill(dt, op, rows, counts[b], tok, hl, rule.inv_load, spill_tb, h->tables.ptr, out, err, bs);
         } else if (tbits_of_bin(b) <= rule.tiny_tbits && counts[b] >= tiny_min_rows(h)) {
-            LaunchTimer lt(h, s, "num_tiny", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);
-            launch_num_tiny(dt, op, rows, counts[b], tbits_of_bin(b), h->params.max_load, h->sms, out, err, s);
+            cudaStream_t bs = fk.get(q++);
+            LaunchTimer lt(h, bs, "num_tiny", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);
+            launch_num_tiny(dt, op, rows, counts[b], tbits_of_bin(b), h->params.max_load, h->sms, out, err, bs);
         } else {
+            cudaStream_t bs = fk.get(q++);
             const HashLaunch hl = hash_launch(h, tbits_of_bin(b), op.ncols);
-            LaunchTimer lt(h, s, "num_hash", b, group_threads(hl), counts[b], sums[b], sums[16 + b], sums[32 + b]);
-            launch_num_hash(dt, op, rows, counts[b], tok, hl, rule.inv_load, h->params.bitmap_ratio, out, err, s);
+            if (use_warp_rows(h, hl, dt)) {
+                LaunchTimer lt(h, bs, "num_warp", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);
+                launch_num_warp(dt, op, rows, counts[b], tok, hl, rule.inv_load, out, err, bs);
+            } else {
+                LaunchTimer lt(h, bs, "num_hash", b, group_threads(hl), counts[b], sums[b], sums[16 + b],
+                               sums[32 + b]);
+                launch_num_hash(dt, op, rows, counts[b], tok, hl, rule.inv_load, h->params.bitmap_ratio, out, err,
+                                bs);
+            }
         }
         if ((st = last_cuda_status())) return st;
     }

@@ -77,6 +77,13 @@ struct smash_handle {
     smash::DevBuf err;        // kNumErr ints (+ scratch words)
     long long *host = nullptr;  // pinned host staging
     smash_stats stats{};
+    // Streams that run the bins of one phase side by side (created on first
+    // use): a bin's kernel starts on SMs that the kernels before it release,
+    // so the tails of the large bins and the small bins overlap.
+    static constexpr int kAux = 3;
+    cudaStream_t aux[kAux] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kAux] = {nullptr, nullptr, nullptr};
 };
 
 namespace smash {
@@ -294,6 +301,7 @@ inline int check_params(const smash_params *p) {
     if (p->sym_dense_blocks != 0 && p->sym_dense_blocks != 1 && p->sym_dense_blocks != 2 &&
         p->sym_dense_blocks != 4 && p->sym_dense_blocks != 8)
         return SMASH_ERR_INVALID_ARG;
+    if (p->warp_rows != 0 && p->warp_rows != 1) return SMASH_ERR_INVALID_ARG;
     return SMASH_OK;
 }
 
@@ -421,6 +429,63 @@ inline int read_flags(smash_handle *h, cudaStream_t s, bool clear) {
     return st;
 }
 
+// Fork of the caller's stream s into s and the handle's auxiliary streams for
+// the launches of one phase, joined back into s when the Fork goes out of
+// scope. Buffers that more than one of the forked launches use must be
+// allocated before the fork.
+struct Fork {
+    smash_handle *h;
+    cudaStream_t s;
+    int n = 1;   // streams in use: s and n - 1 auxiliary ones
+    Fork(smash_handle *hh, cudaStream_t ss) : h(hh), s(ss) {
+        bool ok = true;
+        if (!h->fork_ev) ok = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; ok && k < smash_handle::kAux; ++k) {
+            if (!h->aux[k]) ok = cudaStreamCreateWithFlags(&h->aux[k], cudaStreamNonBlocking) == cudaSuccess;
+            if (ok && !h->join_ev[k]) ok = cudaEventCreateWithFlags(&h->join_ev[k], cudaEventDisableTiming) == cudaSuccess;
+        }
+        if (!ok) {
+            cudaGetLastError();
+            return;   // everything on s
+        }
+        if (cudaEventRecord(h->fork_ev, s) != cudaSuccess) return;
+        for (int k = 0; k < smash_handle::kAux; ++k) cudaStreamWaitEvent(h->aux[k], h->fork_ev, 0);
+        n = 1 + smash_handle::kAux;
+    }
+    cudaStream_t get(int k) const { return (k % n) == 0 ? s : h->aux[(k % n) - 1]; }
+    ~Fork() {
+        for (int k = 0; k + 1 < n; ++k) {
+            cudaEventRecord(h->join_ev[k], h->aux[k]);
+            cudaStreamWaitEvent(s, h->join_ev[k], 0);
+        }
+    }
+};
+
+inline void destroy_streams(smash_handle *h) {
+    for (int k = 0; k < smash_handle::kAux; ++k) {
+        if (h->aux[k]) cudaStreamDestroy(h->aux[k]);
+        if (h->join_ev[k]) cudaEventDestroy(h->join_ev[k]);
+        h->aux[k] = nullptr;
+        h->join_ev[k] = nullptr;
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    h->fork_ev = nullptr;
+}
+
+// Order in which the bins of a phase are launched: most products first, so
+// that the largest kernels start first and the small ones fill their tails.
+inline int bin_order(const long long *sums, int *order) {
+    int n = 0;
+    for (int b = 1; b < kNumBins; ++b) order[n++] = b;
+    for (int x = 1; x < n; ++x)
+        for (int y = x; y > 0 && sums[16 + order[y]] > sums[16 + order[y - 1]]; --y) {
+            const int t = order[y];
+            order[y] = order[y - 1];
+            order[y - 1] = t;
+        }
+    return n;
+}
+
 inline int last_cuda_status() {
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SMASH_OK : SMASH_ERR_CUDA;
@@ -480,6 +545,15 @@ inline BinRule num_rule(const smash_handle *h, int64_t ncols, int dtype) {
 inline int group_threads(const HashLaunch &hl) {
     int t = 1 << (hl.tbits > hl.group_shift ? hl.tbits - hl.group_shift : 0);
     return t < 32 ? 32 : (t > 1024 ? 1024 : t);
+}
+
+// Whether a bin of tables of 2^hl.tbits slots runs the register-enumerating
+// warp-row kernel (k_warp.cu): one warp per row, and its shared memory fits.
+// dtype < 0: the symbolic phase.
+inline bool use_warp_rows(const smash_handle *h, const HashLaunch &hl, int dtype) {
+    if (!h->params.warp_rows || group_threads(hl) != 32) return false;
+    const size_t need = dtype < 0 ? sym_warp_smem(hl.tbits) : num_warp_smem(dtype, hl.tbits, 1.0f / h->params.max_load);
+    return need <= (size_t)max_smem_per_block();
 }
 
 inline HashLaunch hash_launch(const smash_handle *h, int tbits, int64_t ncols) {

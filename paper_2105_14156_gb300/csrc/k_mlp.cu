@@ -259,6 +259,35 @@ __global__ void __launch_bounds__(256) k_feat_stats(const float *feats, int64_t 
 }
 
 // ---------------------------------------------------------------------------
+// Training samples: rows with at least one product (bound > 0), in row
+// order; the target of a row is log1p of its exact count.
+__global__ void k_keep_rows(int64_t n, const long long *bound, int *keep) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) keep[i] = bound[i] > 0 ? 1 : 0;
+}
+
+__global__ void k_training_rows(int64_t n, const int *nnz, const int *keep, const int64_t *pos, const float *ftmp,
+                                float *feats, float *targets) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && keep[i]) {
+        const int64_t p = pos[i];
+#pragma unroll
+        for (int c = 0; c < kFeat; ++c) feats[p * kFeat + c] = ftmp[i * kFeat + c];
+        targets[p] = log1pf((float)nnz[i]);
+    }
+}
+
+void launch_training_rows(int64_t n, const int *nnz, const long long *bound, const float *ftmp, int *keep,
+                          int64_t *pos, long long *total, void *scan, float *feats, float *targets, int sms,
+                          cudaStream_t s) {
+    (void)sms;
+    if (n <= 0) return;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    k_keep_rows<<<blocks, 256, 0, s>>>(n, bound, keep);
+    launch_scan_rowptr(keep, n, pos, total, scan, s);
+    k_training_rows<<<blocks, 256, 0, s>>>(n, nnz, keep, pos, ftmp, feats, targets);
+}
+
 void launch_features(const RawOperands &op, const int *row_list, int64_t nrows, float *feats, long long *bound,
                      int *err, int sms, cudaStream_t s) {
     if (nrows <= 0) return;

@@ -141,7 +141,9 @@ __global__ void __launch_bounds__(256) k_learned_bin(RawOperands op, BinRule rul
     __shared__ RowStats st;
     extern __shared__ __align__(16) float s_mlp[];   // the predictor's weights (mlp.cuh)
     st.init();
-    load_mlp_tc(s_mlp, (const __nv_bfloat16 *)la.wb, la.norm);
+    // without weights every row is sized by its bound min(flop_i, cols(B))
+    const bool model = la.wb != nullptr;
+    if (model) load_mlp_tc(s_mlp, (const __nv_bfloat16 *)la.wb, la.norm);
     __syncthreads();
     const int lane = lane_id();
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -151,13 +153,16 @@ __global__ void __launch_bounds__(256) k_learned_bin(RawOperands op, BinRule rul
         const bool valid = i < nrows;
         RowGather rg{0, 0, 0};
         if (valid) rg = la.gather[i];
-        float x[kFeat];
-        row_features(rg.na, rg.f, rg.mx, op.ncols, x);
-        const float y = mlp_forward_warp(s_mlp, x, (uint32_t *)(s_mlp + kSmH1) + (threadIdx.x >> 5) * kH1Words);
+        float y = 0.f;
+        if (model) {
+            float x[kFeat];
+            row_features(rg.na, rg.f, rg.mx, op.ncols, x);
+            y = mlp_forward_warp(s_mlp, x, (uint32_t *)(s_mlp + kSmH1) + (threadIdx.x >> 5) * kH1Words);
+        }
         long long size = 0;
         if (valid) {
             const long long ub = rg.f < (long long)op.ncols ? rg.f : (long long)op.ncols;
-            size = cap_of(y, la.margin, ub);
+            size = model ? cap_of(y, la.margin, ub) : ub;
             la.cap[i] = (int)size;
         }
         bin_rows(valid, i, rg.na, rg.f, size, rule, bb, nullptr, st);

@@ -96,6 +96,11 @@ void launch_adam(float *params, float *grad, float *m, float *v, void *wb, float
 void launch_epoch_shift(unsigned long long *epoch, unsigned long long *shift, unsigned long long seed,
                         unsigned long long n, cudaStream_t s);
 void launch_feat_stats(const float *feats, int64_t n, double *acc, int sms, cudaStream_t s);
+// Training samples (k_mlp.cu): the rows with bound > 0, in order: features
+// from ftmp and target log1p(nnz[i]); *total receives their number.
+void launch_training_rows(int64_t n, const int *nnz, const long long *bound, const float *ftmp, int *keep,
+                          int64_t *pos, long long *total, void *scan, float *feats, float *targets, int sms,
+                          cudaStream_t s);
 void launch_to_bf16(const float *src, void *dst, int n, cudaStream_t s);
 void launch_bin_scatter(int64_t n, BinBuffers bb, cudaStream_t s);
 size_t scan_scratch_bytes(int64_t n);
@@ -157,6 +162,15 @@ struct NumOut {
 void launch_num_hash(int dtype, const RawOperands &op, const int *rows, int count, int *token,
                      const HashLaunch &hl, float inv_load, int bitmap_ratio, const NumOut &out, int *err,
                      cudaStream_t s);
+// Warp rows (k_warp.cu): one warp per row, products enumerated from
+// registers, compare-and-swap-first probing, list-driven write-out. The
+// *_smem functions give the dynamic shared memory of one block.
+size_t sym_warp_smem(int tbits);
+size_t num_warp_smem(int dtype, int tbits, float inv_load);
+void launch_sym_warp(const RawOperands &op, const int *rows, int count, int *token, const HashLaunch &hl,
+                     int *nnz_out, int *err, cudaStream_t s);
+void launch_num_warp(int dtype, const RawOperands &op, const int *rows, int count, int *token,
+                     const HashLaunch &hl, float inv_load, const NumOut &out, int *err, cudaStream_t s);
 // Thread-per-row bins (tbits <= BinRule::tiny_tbits, k_tiny.cu): list length of a bin, and
 // the symbolic count / numeric merge of its rows.
 int tiny_list_len(int tbits, float max_load);

@@ -204,6 +204,56 @@ int smash_row_features(smash_handle *h, const smash_csr *A, const smash_csr *B, 
     return last_cuda_status();
 }
 
+int smash_training_rows(smash_handle *h, const smash_csr *A, const smash_csr *B, float *feats, float *targets,
+                        int64_t *count, void *stream) {
+    if (!h || !feats || !targets || !count) return SMASH_ERR_INVALID_ARG;
+    int st = check_csr(A, false);
+    if (st) return st;
+    if ((st = check_csr(B, false))) return st;
+    if (A->cols != B->rows) return SMASH_ERR_SHAPE_MISMATCH;
+    DeviceGuard g(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = A->rows;
+    *count = 0;
+    if (n == 0) return SMASH_OK;
+    const RawOperands op = raw_ops(A, B);
+    // 1. exact nnz(C_i) of every row (the symbolic phase)
+    Plan pl;
+    if ((st = plan_buffers(h, n, true, s, pl))) return st;
+    if (A->nnz > 0 && B->nnz > 0) {
+        if ((st = run_symbolic(h, op, n, pl, pl.nnz, s, nullptr, 0))) return st;
+    } else if (cudaMemsetAsync(pl.nnz, 0, sizeof(int) * (size_t)n, s) != cudaSuccess) {
+        return SMASH_ERR_CUDA;
+    }
+    // 2. features and bounds of every row; 3. rows with products, in order
+    size_t need = 0;
+    carve_size<float>(need, (size_t)n * 6);
+    carve_size<long long>(need, (size_t)n);
+    carve_size<int>(need, (size_t)n);
+    carve_size<int64_t>(need, (size_t)n + 1);
+    carve_size<long long>(need, 1);
+    carve_size<char>(need, scan_scratch_bytes(n));
+    if ((st = ensure(h, h->learn, need, s))) return st;
+    Carver c(h->learn.ptr);
+    float *ftmp = c.take<float>((size_t)n * 6);
+    long long *bound = c.take<long long>((size_t)n);
+    int *keep = c.take<int>((size_t)n);
+    int64_t *pos = c.take<int64_t>((size_t)n + 1);
+    long long *total = c.take<long long>(1);
+    void *scan = c.take<char>(scan_scratch_bytes(n));
+    {
+        LaunchTimer lt(h, s, "training_rows", -1, 256, n, A->nnz, 0, 0, 5);
+        launch_features(op, nullptr, n, ftmp, bound, (int *)h->err.ptr, h->sms, s);
+        launch_training_rows(n, pl.nnz, bound, ftmp, keep, pos, total, scan, feats, targets, h->sms, s);
+    }
+    if ((st = last_cuda_status())) return st;
+    if (cudaMemcpyAsync(h->host, total, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return SMASH_ERR_CUDA;
+    st = read_flags(h, s, true);
+    *count = h->host[0];
+    return st;
+}
+
 int smash_mlp_gradient(smash_handle *h, smash_model *m, const float *feats, const float *targets, int64_t n,
                        float *grad, float *loss, void *stream) {
     if (!h || !m || !feats || !targets || !grad || n <= 0) return SMASH_ERR_INVALID_ARG;
@@ -329,7 +379,7 @@ int smash_free_csr(smash_handle *h, smash_csr *C) {
 
 int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smash_dtype dtype,
                    const smash_model *m, float margin, smash_csr *C, smash_learned_stats *stats, void *stream) {
-    if (!h || !m || !C || !(margin > -1.f)) return SMASH_ERR_INVALID_ARG;
+    if (!h || !C || !(margin > -1.f)) return SMASH_ERR_INVALID_ARG;
     if (dtype != SMASH_F32 && dtype != SMASH_F64) return SMASH_ERR_UNSUPPORTED;
     int st = check_csr(A, true);
     if (st) return st;
@@ -390,8 +440,8 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
     if ((st = plan_buffers(h, n, false, s, pl))) return st;
     {
         LearnArgs la;
-        la.wb = m->wb;
-        la.norm = m->norm;
+        la.wb = m ? m->wb : nullptr;     // no model: every row sized by its bound
+        la.norm = m ? m->norm : nullptr;
         la.margin = margin;
         la.cap = cap;
         la.gather = gather;

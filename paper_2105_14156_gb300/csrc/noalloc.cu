@@ -13,6 +13,8 @@
 // distinct columns of its rows with compare-and-swap inserts, and writes the
 // count of row i to c_row_ptr[i+1]; one block then turns those counts into the
 // exclusive prefix sum in place.
+#include <atomic>
+
 #include "internal.h"
 
 using namespace smash;
@@ -31,8 +33,10 @@ constexpr size_t kNaWords = (size_t)kNaErrWords + ((size_t)kNaBlocks << kNaTable
 static __device__ __align__(256) int g_noalloc_scratch[kNaWords];
 
 // Device address of the scratch per device, looked up once (host code may
-// not use the array's name as an address).
-int *g_scratch_addr[256];
+// not use the array's name as an address). Atomic entries: two host threads
+// that make their first call on a device at the same time both look the
+// address up and store the same value, without a data race.
+std::atomic<int *> g_scratch_addr[256];
 
 __global__ void __launch_bounds__(kNaThreads) k_na_count(Operands<float> op, int64_t n, HashCfg hc,
                                                          int64_t *c_rp, int *scratch) {
@@ -113,16 +117,17 @@ int spgemm_symbolic_noalloc(const smash_csr *A, const smash_csr *B, int64_t *c_r
     if (B->cols > kNaMaxCols) return SMASH_ERR_UNSUPPORTED;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return SMASH_ERR_CUDA;
-    if (!g_scratch_addr[dev]) {
+    int *scratch = g_scratch_addr[dev].load(std::memory_order_relaxed);
+    if (!scratch) {
         // one-time set-up on this device (the device is current)
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
             return SMASH_ERR_CUDA;
         }
-        g_scratch_addr[dev] = (int *)p;
+        scratch = (int *)p;
+        g_scratch_addr[dev].store(scratch, std::memory_order_relaxed);
     }
-    int *scratch = g_scratch_addr[dev];
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = A->rows;
     if (cudaMemsetAsync(c_row_ptr, 0, sizeof(int64_t) * (size_t)(n + 1), s) != cudaSuccess ||

@@ -30,18 +30,16 @@ def training_matrices(seeds, workers: int = 0):
 
 
 def training_set(handle, mats, device="cuda"):
-    """(features [n,6] float32, targets [n] float32) on the device for C = M*M."""
+    """(features [n,6] float32, targets [n] float32) on the device for C = M*M:
+    the library's smash_training_rows per matrix, concatenated."""
     import torch
     from . import smash
     feats, targets = [], []
     for M in mats:
         dM = smash.to_device(M, device, dtype=np.float32)
-        c_rp, _ = handle.symbolic(dM, dM)
-        f = handle.features(dM, dM)
-        nnz = (c_rp[1:] - c_rp[:-1]).to(torch.float32)
-        keep = torch.expm1(f[:, 1]) > 0.5          # rows with at least one product
-        feats.append(f[keep])
-        targets.append(torch.log1p(nnz[keep]))
+        f, t = handle.training_rows(dM, dM)
+        feats.append(f)
+        targets.append(t)
     return torch.cat(feats), torch.cat(targets)
 
 

@@ -29,6 +29,7 @@ EXPORTS = [
     "smash_model_save", "smash_model_load", "smash_row_features", "smash_mlp_train", "smash_mlp_gradient",
     "smash_mlp_predict", "smash_mlp_predict_tc", "spgemm_learned", "smash_free_csr", "spgemm_symbolic_noalloc",
     "spgemm_batched", "smash_batched_set_table_bits", "smash_batched_get_table_bits", "smash_batched_autotune",
+    "smash_training_rows",
 ]
 
 
@@ -87,7 +88,7 @@ class Params(ctypes.Structure):
                 ("dense_ratio", ctypes.c_int32), ("bitmap_ratio", ctypes.c_int32),
                 ("spill_blocks_per_sm", ctypes.c_int32), ("sym_dense_ratio", ctypes.c_int32),
                 ("dense_blocks", ctypes.c_int32), ("sym_dense_blocks", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("warp_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -148,6 +149,8 @@ def load_library(path: str = LIB_PATH):
         lib.smash_model_save.argtypes = [P, ctypes.c_char_p]
         lib.smash_model_load.argtypes = [P, ctypes.c_char_p]
         lib.smash_row_features.argtypes = [P, ctypes.POINTER(CsrStruct), ctypes.POINTER(CsrStruct), P, P]
+        lib.smash_training_rows.argtypes = [P, ctypes.POINTER(CsrStruct), ctypes.POINTER(CsrStruct), P, P,
+                                            ctypes.POINTER(ctypes.c_int64), P]
         lib.smash_mlp_train.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.POINTER(TrainCfg),
                                         ctypes.POINTER(ctypes.c_float), P]
         lib.smash_mlp_gradient.argtypes = [P, P, P, P, ctypes.c_int64, P, ctypes.POINTER(ctypes.c_float), P]
@@ -367,6 +370,18 @@ class Handle:
                                            _stream_ptr(stream)), "smash_row_features")
         return f
 
+    def training_rows(self, A: DeviceCsr, B: DeviceCsr, stream=None):
+        """Training samples of C = A*B made by the library: (features [n, 6],
+        targets log1p(nnz(C_i)) [n]) of the rows with at least one product."""
+        import torch
+        f = torch.empty((A.rows, 6), dtype=torch.float32, device=A.row_ptr.device)
+        t = torch.empty(A.rows, dtype=torch.float32, device=A.row_ptr.device)
+        n = ctypes.c_int64(0)
+        sa, sb = A.struct(), B.struct()
+        _check(self.lib.smash_training_rows(self.h, ctypes.byref(sa), ctypes.byref(sb), f.data_ptr(), t.data_ptr(),
+                                            ctypes.byref(n), _stream_ptr(stream)), "smash_training_rows")
+        return f[: n.value], t[: n.value]
+
     def mlp_train(self, model: "Model", feats, targets, stream=None, **cfg) -> float:
         c = TrainCfg()
         _check(self.lib.smash_train_cfg_default(ctypes.byref(c)), "smash_train_cfg_default")
@@ -398,15 +413,18 @@ class Handle:
                   _stream_ptr(stream)), "smash_mlp_predict")
         return y
 
-    def spgemm_learned(self, A: DeviceCsr, B: DeviceCsr, model: "Model", margin: float = 0.15, stream=None):
-        """C = A*B sized by the model. Returns (C as zero-copy views, stats, owner);
-        call owner.free() (or let it be collected) to release C's arrays."""
+    def spgemm_learned(self, A: DeviceCsr, B: DeviceCsr, model: "Model | None", margin: float = 0.15, stream=None):
+        """C = A*B sized by the model (model None: every row sized by its bound
+        min(flop_i, cols), the same one-pass pipeline without the network).
+        Returns (C as zero-copy views, stats, owner); call owner.free() (or let
+        it be collected) to release C's arrays."""
         import torch
         dt = _dtype_code(A.val)
         sa, sb = A.struct(), B.struct()
         sc = CsrStruct()
         st = LearnedStats()
-        _check(self.lib.spgemm_learned(self.h, ctypes.byref(sa), ctypes.byref(sb), dt, model.m, margin,
+        _check(self.lib.spgemm_learned(self.h, ctypes.byref(sa), ctypes.byref(sb), dt,
+                                       model.m if model is not None else None, margin,
                                        ctypes.byref(sc), ctypes.byref(st), _stream_ptr(stream)), "spgemm_learned")
         owner = LibraryCsr(self, sc)
         vdt = A.val.dtype

