@@ -88,7 +88,10 @@ typedef struct {
                                 1 (default): products enumerated from registers, compare-and-swap-first
                                 probing, write-out driven by the list of claimed slots;
                                 0: the shared-memory staged enumeration of the thread-group kernels */
-    int32_t reserved[4];
+    int32_t bulk_copy;       /* warp rows: 1 stages each sorted row in shared memory and streams it to C
+                                with bulk (TMA engine) copies, Version 3's copy-out; 0 (default): each lane
+                                stores its entries (measured faster for rows of a few hundred entries) */
+    int32_t reserved[3];
 } smash_params;
 
 /* Per-call statistics (the last symbolic or numeric call of the handle). */
@@ -140,7 +143,11 @@ int smash_set_params(smash_handle *h, const smash_params *params);
 int smash_get_params(const smash_handle *h, smash_params *params);
 
 /* Route the handle's scratch allocations through (alloc, free, ctx). Frees
- * the current scratch first (synchronising the device). */
+ * the current scratch first (synchronising the device). alloc == NULL restores
+ * cudaMalloc / cudaFree. If the new allocator cannot provide the handle's
+ * error words, the handle goes back to cudaMalloc / cudaFree and the call
+ * returns SMASH_ERR_ALLOC. A call whose allocation fails returns
+ * SMASH_ERR_ALLOC and leaves nothing allocated for the caller. */
 int smash_set_allocator(smash_handle *h, smash_alloc_fn alloc, smash_free_fn free_fn, void *ctx);
 
 /*
@@ -342,9 +349,26 @@ int spgemm_batched(smash_handle *h, int count, const smash_csr *A, const smash_c
 int smash_batched_set_table_bits(smash_handle *h, int bits);
 int smash_batched_get_table_bits(smash_handle *h, int *bits);
 
+/* Which rows of a batch one warp serves (tables up to 2^(bits - warp_less)
+ * slots, 32 threads per row) and which the whole block serves (up to
+ * 2^(bits + block_more) slots, 256 threads per row); larger rows take the
+ * regular per-product path. warp_less in [0, 3] (default 0), block_more in
+ * [0, 3] (default 3). The autotuner sets them with the table size. */
+int smash_batched_set_row_cutoffs(smash_handle *h, int warp_less, int block_more);
+int smash_batched_get_row_cutoffs(smash_handle *h, int *warp_less, int *block_more);
+
+/* Bounded waits of the batched kernel: each of its grid barriers polls at
+ * most wait_spins times (about 256 ns apart; 0 restores the default of about
+ * one second), then records a time-out and the kernel returns, so that the
+ * call ends with SMASH_ERR_TIMEOUT and the context stays usable.
+ * missing_arrivals (0 or 1) is a test hook: 1 makes every barrier wait for
+ * one arrival more than the grid has, so that the waits run out. */
+int smash_batched_set_wait(smash_handle *h, int64_t wait_spins, int missing_arrivals);
+
 /* Autotuner: times spgemm_batched on the given batch for each table size that
- * fits (2^8 .. 2^11 slots), keeps the fastest in the handle and reports it
- * (*best_ms: mean of two timed runs after one warm-up). */
+ * fits (2^8 .. 2^11 slots) combined with the row cutoffs (warp_less 0 or 1,
+ * block_more 2 or 3), keeps the fastest in the handle and reports its table
+ * size (*best_ms: mean of two timed runs after one warm-up). */
 int smash_batched_autotune(smash_handle *h, int count, const smash_csr *A, const smash_csr *B, smash_dtype dtype,
                            int *best_bits, float *best_ms, void *stream);
 

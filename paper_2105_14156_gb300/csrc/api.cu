@@ -22,6 +22,7 @@ int smash_default_params(smash_params *p) {
     p->dense_blocks = 0;
     p->sym_dense_blocks = 0;
     p->warp_rows = 1;
+    p->bulk_copy = 0;
     return SMASH_OK;
 }
 
@@ -92,6 +93,7 @@ int smash_destroy(smash_handle *h) {
         release(h, h->stage);
         release(h, h->arena);
         release(h, h->learn);
+        release(h, h->rcache);
         batched_release(h);
         release(h, h->err);
         destroy_streams(h);
@@ -125,15 +127,26 @@ int smash_set_allocator(smash_handle *h, smash_alloc_fn alloc, smash_free_fn fre
     release(h, h->stage);
     release(h, h->arena);
     release(h, h->learn);
+    release(h, h->rcache);
+    h->rkey.valid = false;
+    h->wcache.valid = false;
     batched_release(h);
     // the error words move to the new allocator as well
     release(h, h->err);
     h->alloc = alloc ? alloc : default_alloc;
     h->free_fn = free_fn ? free_fn : default_free;
     h->ctx = alloc ? ctx : nullptr;
-    if (ensure(h, h->err, 256, 0) != SMASH_OK) return SMASH_ERR_ALLOC;
+    int st = SMASH_OK;
+    if (ensure(h, h->err, 256, 0) != SMASH_OK) {
+        // the handle stays usable: back to cudaMalloc / cudaFree
+        st = SMASH_ERR_ALLOC;
+        h->alloc = default_alloc;
+        h->free_fn = default_free;
+        h->ctx = nullptr;
+        if (ensure(h, h->err, 256, 0) != SMASH_OK) return SMASH_ERR_ALLOC;
+    }
     if (cudaMemset(h->err.ptr, 0, h->err.bytes) != cudaSuccess) return SMASH_ERR_CUDA;
-    return SMASH_OK;
+    return st;
 }
 
 int smash_set_timing(smash_handle *h, int enable) {
@@ -245,10 +258,18 @@ int run_symbolic(smash_handle *h, const RawOperands &op, int64_t n, Plan &pl, in
     int *err = (int *)h->err.ptr;
     h->wcache.valid = false;
     if (row_list && cudaMemsetAsync(pl.bb.bin, 0, (size_t)n, s) != cudaSuccess) return SMASH_ERR_CUDA;
+    // a full planning records the rows' counts for the numeric phase
+    RowGather *keep = nullptr;
+    if (!row_list) {
+        h->rkey.valid = false;
+        if ((st = ensure(h, h->rcache, sizeof(RowGather) * (size_t)n, s))) return st;
+        keep = (RowGather *)h->rcache.ptr;
+    }
     {
         LaunchTimer lt(h, s, "sym_rowinfo", -1, 256, row_list ? list_n : n, op.a_nnz, 0, 0, 2);
-        launch_sym_rowinfo(op, rule, pl.bb, pl.bound, nnz_out, err, h->sms, s, row_list, list_n);
+        launch_sym_rowinfo(op, rule, pl.bb, pl.bound, nnz_out, err, h->sms, s, row_list, list_n, keep);
     }
+    if (keep) rcache_set(h, op);
     {
         LaunchTimer lt(h, s, "bin_scatter", -1, 256, n, 0, 0, 0);
         launch_bin_scatter(n, pl.bb, s);
@@ -323,9 +344,11 @@ int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const
     const BinRule rule = num_rule(h, op.ncols, dt);
     int *err = (int *)h->err.ptr;
     if (row_list && cudaMemsetAsync(pl.bb.bin, 0, (size_t)n, s) != cudaSuccess) return SMASH_ERR_CUDA;
+    // the rows' counts from the symbolic phase of the same operands, if kept
+    const RowGather *kept = rcache_matches(h, op) ? (const RowGather *)h->rcache.ptr : nullptr;
     {
-        LaunchTimer lt(h, s, "num_rowinfo", -1, 256, row_list ? list_n : n, op.a_nnz, 0, out.c_nnz, 2);
-        launch_num_rowinfo(op, out.c_rp, out.c_nnz, rule, pl.bb, err, h->sms, s, row_list, list_n);
+        LaunchTimer lt(h, s, "num_rowinfo", -1, 256, row_list ? list_n : n, op.a_nnz, 0, out.c_nnz, kept ? 1 : 2);
+        launch_num_rowinfo(op, out.c_rp, out.c_nnz, rule, pl.bb, err, h->sms, s, row_list, list_n, kept);
     }
     {
         LaunchTimer lt(h, s, "bin_scatter", -1, 256, n, 0, 0, 0);
@@ -388,6 +411,8 @@ int run_bins(smash_handle *h, const RawOperands &op, int64_t n, int dt, const Nu
     const long long *maxsize = bp.maxsize;
     const long long *sums = bp.sums;
     const size_t vsz = dt ? 8 : 4;
+    // the rows' product counts kept by the symbolic phase of these operands
+    const RowGather *kept = (!out.row_nnz && rcache_matches(h, op)) ? (const RowGather *)h->rcache.ptr : nullptr;
     // Dense rows take column windows when their products pay for slicing B
     // (a pass over B's rows and entries); otherwise the global hash. Their
     // counts and the slices of B are prepared on s before the bins fork.
@@ -477,7 +502,8 @@ int run_bins(smash_handle *h, const RawOperands &op, int64_t n, int dt, const Nu
             const HashLaunch hl = hash_launch(h, tbits_of_bin(b), op.ncols);
             if (use_warp_rows(h, hl, dt)) {
                 LaunchTimer lt(h, bs, "num_warp", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);
-                launch_num_warp(dt, op, rows, counts[b], tok, hl, rule.inv_load, out, err, bs);
+                launch_num_warp(dt, op, rows, counts[b], tok, hl, rule.inv_load, kept, h->params.bulk_copy, out, err,
+                                bs);
             } else {
                 LaunchTimer lt(h, bs, "num_hash", b, group_threads(hl), counts[b], sums[b], sums[16 + b],
                                sums[32 + b]);

@@ -51,9 +51,14 @@ struct BatchArgs {
     int64_t *totals;        // [nmat]
     int *err;
     int tw_bits;            // per-warp table: 2^tw_bits slots
+    int warp_bits;          // rows whose table needs at most 2^warp_bits slots: one warp (<= tw_bits)
+    int block_bits;         // ... at most 2^block_bits slots: the whole block (<= tw_bits + 3); larger:
+                            // the regular per-product path
     int dense_max;          // per-warp dense accumulator when cols <= dense_max
     HashCfg hc;             // colbits filled per product
     float inv_load;
+    long long wait_spins;   // a grid barrier gives up after this many polls (~256 ns each)
+    int missing;            // test hook: arrivals a barrier waits for beyond the grid (0: none)
 };
 
 size_t batched_smem(int dtype, int tw_bits);

@@ -19,6 +19,10 @@ struct BatchState {
     void *pinned = nullptr;
     size_t pinned_bytes = 0;
     int tw_bits = 10;
+    int warp_less = 0;               // warp rows: tables up to 2^(tw_bits - warp_less) slots
+    int block_more = 3;              // block rows: tables up to 2^(tw_bits + block_more) slots
+    long long wait_spins = 4000000;  // grid-barrier polls (x ~256 ns: about one second)
+    int missing = 0;                 // test hook: barrier arrivals that never come
     cudaStream_t cs = nullptr;       // private stream for graph recording
     cudaGraph_t graph = nullptr;     // the recorded launch, replayed while its key holds
     cudaGraphExec_t exec = nullptr;
@@ -119,6 +123,28 @@ extern "C" {
 int smash_batched_set_table_bits(smash_handle *h, int bits) {
     if (!h || bits < 6 || bits > 12) return SMASH_ERR_INVALID_ARG;
     state_of(h).tw_bits = bits;
+    return SMASH_OK;
+}
+
+int smash_batched_set_wait(smash_handle *h, int64_t wait_spins, int missing_arrivals) {
+    if (!h || wait_spins < 0 || missing_arrivals < 0 || missing_arrivals > 1) return SMASH_ERR_INVALID_ARG;
+    BatchState &b = state_of(h);
+    b.wait_spins = wait_spins > 0 ? wait_spins : 4000000;
+    b.missing = missing_arrivals;
+    return SMASH_OK;
+}
+
+int smash_batched_set_row_cutoffs(smash_handle *h, int warp_less, int block_more) {
+    if (!h || warp_less < 0 || warp_less > 3 || block_more < 0 || block_more > 3) return SMASH_ERR_INVALID_ARG;
+    state_of(h).warp_less = warp_less;
+    state_of(h).block_more = block_more;
+    return SMASH_OK;
+}
+
+int smash_batched_get_row_cutoffs(smash_handle *h, int *warp_less, int *block_more) {
+    if (!h || !warp_less || !block_more) return SMASH_ERR_INVALID_ARG;
+    *warp_less = state_of(h).warp_less;
+    *block_more = state_of(h).block_more;
     return SMASH_OK;
 }
 
@@ -250,6 +276,10 @@ int spgemm_batched(smash_handle *h, int count, const smash_csr *A, const smash_c
     p.totals = L.totals;
     p.err = (int *)h->err.ptr;
     p.tw_bits = bs.tw_bits;
+    p.warp_bits = bs.tw_bits - bs.warp_less;
+    p.block_bits = bs.tw_bits + bs.block_more;
+    p.wait_spins = bs.wait_spins;
+    p.missing = bs.missing;
     p.dense_max = batched_dense_max(dt, bs.tw_bits);
     p.hc = HashCfg{h->params.hash_kind, 0};
     p.inv_load = 1.0f / h->params.max_load;
@@ -286,6 +316,22 @@ int spgemm_batched(smash_handle *h, int count, const smash_csr *A, const smash_c
     p.rp_pool = rp_pool;
     p.ci_pool = ci_pool;
     p.val_pool = val_pool;
+    // on any failure from here on the pools go back to the allocator and C
+    // is left empty (nothing to release for the caller)
+    auto fail = [&](int code) {
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        h->free_fn(rp_pool, h->ctx);
+        h->free_fn(ci_pool, h->ctx);
+        h->free_fn(val_pool, h->ctx);
+        for (int m = 0; m < count; ++m) {
+            C[m].nnz = 0;
+            C[m].row_ptr = nullptr;
+            C[m].col_idx = nullptr;
+            C[m].val = nullptr;
+        }
+        return code;
+    };
     // rows too large for one block: exact symbolic by the regular path, per product
     std::vector<int> huge;
     std::vector<std::pair<int, std::vector<int>>> huge_by_mat;
@@ -293,7 +339,7 @@ int spgemm_batched(smash_handle *h, int count, const smash_csr *A, const smash_c
         huge.resize(nhuge);
         if (cudaMemcpyAsync(huge.data(), L.huge, sizeof(int) * nhuge, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
-            return SMASH_ERR_CUDA;
+            return fail(SMASH_ERR_CUDA);
         std::map<int, std::vector<int>> by;
         for (int g2 : huge) {
             int m = (int)(std::upper_bound(hrs, hrs + count + 1, (int64_t)g2) - hrs) - 1;
@@ -305,17 +351,17 @@ int spgemm_batched(smash_handle *h, int count, const smash_csr *A, const smash_c
             const int m = kv.first;
             const RawOperands op = raw_ops(&A[m], &B[m]);
             Plan pl;
-            if ((st = plan_buffers(h, A[m].rows, true, s, pl))) return st;
+            if ((st = plan_buffers(h, A[m].rows, true, s, pl))) return fail(st);
             int *list = (int *)h->host;   // staged through pinned memory
-            if (ensure(h, h->learn, sizeof(int) * kv.second.size() + 256, s)) return SMASH_ERR_ALLOC;
+            if (ensure(h, h->learn, sizeof(int) * kv.second.size() + 256, s)) return fail(SMASH_ERR_ALLOC);
             if (cudaMemcpyAsync(h->learn.ptr, kv.second.data(), sizeof(int) * kv.second.size(),
                                 cudaMemcpyHostToDevice, s) != cudaSuccess ||
                 cudaStreamSynchronize(s) != cudaSuccess)
-                return SMASH_ERR_CUDA;
+                return fail(SMASH_ERR_CUDA);
             (void)list;
             if ((st = run_symbolic(h, op, A[m].rows, pl, L.nnz + hrs[m], s, (const int *)h->learn.ptr,
                                    (int64_t)kv.second.size())))
-                return st;
+                return fail(st);
         }
     }
     // the persistent launch
@@ -328,15 +374,18 @@ int spgemm_batched(smash_handle *h, int count, const smash_csr *A, const smash_c
         // the arguments through pinned memory, after the descriptors
         BatchArgs *p_pin = (BatchArgs *)(((uintptr_t)(hts + count + 1) + 63) & ~(uintptr_t)63);
         *p_pin = p;
-        if ((st = run_batched_graph(bs, dt, p_pin, args_dev, grid, s))) return st;
+        if ((st = run_batched_graph(bs, dt, p_pin, args_dev, grid, s))) return fail(st);
     }
+    // a barrier that ran out of time (or any failed check) leaves the row
+    // pointers incomplete: stop before anything reads them
+    if ((st = read_flags(h, s, true))) return fail(st);
     // base offsets and totals
     std::vector<int64_t> base(count + 1), totals(count);
     if (cudaMemcpyAsync(base.data(), L.base, sizeof(int64_t) * (count + 1), cudaMemcpyDeviceToHost, s) !=
             cudaSuccess ||
         cudaMemcpyAsync(totals.data(), L.totals, sizeof(int64_t) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
-        return SMASH_ERR_CUDA;
+        return fail(SMASH_ERR_CUDA);
     for (int m = 0; m < count; ++m) {
         C[m].nnz = totals[m];
         C[m].row_ptr = rp_pool + hrs[m] + m;
@@ -349,23 +398,23 @@ int spgemm_batched(smash_handle *h, int count, const smash_csr *A, const smash_c
         const int m = kv.first;
         const RawOperands op = raw_ops(&A[m], &B[m]);
         Plan pl;
-        if ((st = plan_buffers(h, A[m].rows, false, s, pl))) return st;
-        if (ensure(h, h->learn, sizeof(int) * kv.second.size() + 256, s)) return SMASH_ERR_ALLOC;
+        if ((st = plan_buffers(h, A[m].rows, false, s, pl))) return fail(st);
+        if (ensure(h, h->learn, sizeof(int) * kv.second.size() + 256, s)) return fail(SMASH_ERR_ALLOC);
         if (cudaMemcpyAsync(h->learn.ptr, kv.second.data(), sizeof(int) * kv.second.size(), cudaMemcpyHostToDevice,
                             s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
-            return SMASH_ERR_CUDA;
+            return fail(SMASH_ERR_CUDA);
         NumOut o;
         o.c_rp = C[m].row_ptr;
         o.c_ci = C[m].col_idx;
         o.c_val = C[m].val;
         o.c_nnz = C[m].nnz;
         if ((st = run_numeric(h, op, A[m].rows, dt, o, pl, s, (const int *)h->learn.ptr, (int64_t)kv.second.size())))
-            return st;
+            return fail(st);
     }
-    st = read_flags(h, s, true);
+    if ((st = read_flags(h, s, true))) return fail(st);
     if (stats) *stats = ls;
-    return st;
+    return SMASH_OK;
 }
 
 int smash_batched_autotune(smash_handle *h, int count, const smash_csr *A, const smash_csr *B, smash_dtype dtype,
@@ -377,12 +426,18 @@ int smash_batched_autotune(smash_handle *h, int count, const smash_csr *A, const
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best = -1;
+    int best = -1, best_wl = 0, best_bm = 3;
     float bms = 1e30f;
-    const int keep = state_of(h).tw_bits;
-    for (int bits = 8; bits <= 11; ++bits) {
+    BatchState &bst = state_of(h);
+    const int keep = bst.tw_bits, keep_wl = bst.warp_less, keep_bm = bst.block_more;
+    // the per-warp table size, and the row sizes served by one warp (32
+    // threads per row) and by the whole block (256 threads per row)
+    for (int cand = 0; cand < 4 * 2 * 2; ++cand) {
+        const int bits = 8 + cand / 4, wl = (cand >> 1) & 1, bm = 2 + (cand & 1);
         if (batched_smem(dtype == SMASH_F64, bits) > (size_t)max_smem_per_block()) continue;
-        state_of(h).tw_bits = bits;
+        bst.tw_bits = bits;
+        bst.warp_less = wl;
+        bst.block_more = bm;
         float tot = 0.f;
         int st = SMASH_OK;
         for (int rep = 0; rep < 3 && st == SMASH_OK; ++rep) {
@@ -399,15 +454,21 @@ int smash_batched_autotune(smash_handle *h, int count, const smash_csr *A, const
         if (tot < bms) {
             bms = tot;
             best = bits;
+            best_wl = wl;
+            best_bm = bm;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best < 0) {
-        state_of(h).tw_bits = keep;
+        bst.tw_bits = keep;
+        bst.warp_less = keep_wl;
+        bst.block_more = keep_bm;
         return SMASH_ERR_INTERNAL;
     }
-    state_of(h).tw_bits = best;
+    bst.tw_bits = best;
+    bst.warp_less = best_wl;
+    bst.block_more = best_bm;
     *best_bits = best;
     if (best_ms) *best_ms = bms / 2.f;
     return SMASH_OK;

@@ -71,6 +71,14 @@ struct smash_handle {
         int cpc = 0, nw = 0, dt = 0;
         smash::BSlices sl;
     } plan_cache;
+    // Per-row counts (flop_i, nnz(A_i), longest row of B) recorded by the last
+    // full symbolic planning, for the numeric planning of the same operands.
+    smash::DevBuf rcache;
+    struct {
+        bool valid = false;
+        const void *ptr[4] = {nullptr, nullptr, nullptr, nullptr};
+        int64_t dims[5] = {0, 0, 0, 0, 0};
+    } rkey;
     smash::DevBuf stage;      // learned path: capacity-padded staging of C
     smash::DevBuf arena;      // learned path: dense rows' windows
     smash::DevBuf learn;      // learned path: per-row arrays
@@ -191,6 +199,28 @@ inline void wcache_set(smash_handle *h, const RawOperands &op, int nsub, int64_t
     c.slots = slots;
 }
 
+// Identity of the operands whose per-row counts h->rcache holds.
+inline bool rcache_matches(const smash_handle *h, const RawOperands &op) {
+    const auto &c = h->rkey;
+    return c.valid && c.ptr[0] == op.a_rp && c.ptr[1] == op.a_ci && c.ptr[2] == op.b_rp && c.ptr[3] == op.b_ci &&
+           c.dims[0] == op.a_rows && c.dims[1] == op.a_nnz && c.dims[2] == op.b_rows && c.dims[3] == op.b_nnz &&
+           c.dims[4] == op.ncols;
+}
+
+inline void rcache_set(smash_handle *h, const RawOperands &op) {
+    auto &c = h->rkey;
+    c.valid = true;
+    c.ptr[0] = op.a_rp;
+    c.ptr[1] = op.a_ci;
+    c.ptr[2] = op.b_rp;
+    c.ptr[3] = op.b_ci;
+    c.dims[0] = op.a_rows;
+    c.dims[1] = op.a_nnz;
+    c.dims[2] = op.b_rows;
+    c.dims[3] = op.b_nnz;
+    c.dims[4] = op.ncols;
+}
+
 inline cudaEvent_t take_event(smash_handle *h) {
     if (!h->spare_events.empty()) {
         cudaEvent_t e = h->spare_events.back();
@@ -302,6 +332,7 @@ inline int check_params(const smash_params *p) {
         p->sym_dense_blocks != 4 && p->sym_dense_blocks != 8)
         return SMASH_ERR_INVALID_ARG;
     if (p->warp_rows != 0 && p->warp_rows != 1) return SMASH_ERR_INVALID_ARG;
+    if (p->bulk_copy != 0 && p->bulk_copy != 1) return SMASH_ERR_INVALID_ARG;
     return SMASH_OK;
 }
 
@@ -424,8 +455,11 @@ inline int read_flags(smash_handle *h, cudaStream_t s, bool clear) {
     if (clear && cudaMemsetAsync(h->err.ptr, 0, kNumErr * sizeof(int), s) != cudaSuccess) return SMASH_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SMASH_ERR_CUDA;
     const int st = status_from_flags((const long long *)hb);
-    // after a failure the dense-row counts may not describe the inputs any more
-    if (st != SMASH_OK) h->wcache.valid = false;
+    // after a failure the kept counts may not describe the inputs any more
+    if (st != SMASH_OK) {
+        h->wcache.valid = false;
+        h->rkey.valid = false;
+    }
     return st;
 }
 

@@ -23,7 +23,6 @@
 
 namespace smash {
 
-constexpr long long kBarrierSpins = 4000000;   // x ~256 ns sleep: about one second
 
 __device__ __forceinline__ int find_mat(const int64_t *start, int nmat, int64_t g) {
     int lo = 0, hi = nmat;   // last m with start[m] <= g
@@ -87,8 +86,8 @@ __global__ void __launch_bounds__(256) k_batch_rowinfo(BatchArgs p) {
             const long long ub = f < (long long)M.ncols ? f : (long long)M.ncols;
             uint8_t c;
             if (ub == 0) c = kRowEmpty;
-            else if (M.ncols <= p.dense_max || table_bits(ub, p.inv_load) <= p.tw_bits) c = kRowSmall;
-            else if (table_bits(ub, p.inv_load) <= p.tw_bits + 3) c = kRowBig;
+            else if (M.ncols <= p.dense_max || table_bits(ub, p.inv_load) <= p.warp_bits) c = kRowSmall;
+            else if (table_bits(ub, p.inv_load) <= p.block_bits) c = kRowBig;
             else c = kRowHuge;
             p.cls[g] = c;
             p.ub[g] = (int)ub;
@@ -105,8 +104,10 @@ __global__ void __launch_bounds__(256) k_batch_rowinfo(BatchArgs p) {
     }
 }
 
-// Grid barrier for a cooperative launch; returns false after a timeout.
-__device__ __forceinline__ bool grid_barrier(int *bar, int *err) {
+// Grid barrier for a cooperative launch; returns false after a timeout
+// (wait_spins polls). missing > 0 makes the barrier wait for arrivals that
+// never come, so that every block's wait runs out (a test of the time-out).
+__device__ __forceinline__ bool grid_barrier(int *bar, int *err, long long wait_spins, int missing) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -115,14 +116,14 @@ __device__ __forceinline__ bool grid_barrier(int *bar, int *err) {
         __threadfence();
         const int arrived = atomicAdd(bar, 1);
         int ok = 1;
-        if (arrived == (int)gridDim.x - 1) {
+        if (arrived == (int)gridDim.x - 1 + missing) {
             atomicExch(bar, 0);
             __threadfence();
             atomicAdd(bar + 1, 1);
         } else {
             long long it = 0;
             while (*gen == g) {
-                if (++it > kBarrierSpins) {
+                if (++it > wait_spins) {
                     raise_err(err, kErrTimeout);
                     ok = 0;
                     break;
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(kBNT) k_batched(const BatchArgs *pp) {
     int *bar = p.counters + 6;
     // phase 1: symbolic counts
     run_items<V, false>(p, p.counters + 2, sm, nbig);
-    if (!grid_barrier(bar, p.err)) return;
+    if (!grid_barrier(bar, p.err, p.wait_spins, p.missing)) return;
     // phase 2: row pointers of each product (one product per block at a time)
     __shared__ int s_m;
     for (;;) {
@@ -373,7 +374,7 @@ __global__ void __launch_bounds__(kBNT) k_batched(const BatchArgs *pp) {
             p.totals[mi] = carry;
         }
     }
-    if (!grid_barrier(bar, p.err)) return;
+    if (!grid_barrier(bar, p.err, p.wait_spins, p.missing)) return;
     // phase 3: base offsets of the products in the pools
     if (blockIdx.x == 0) {
         long long carry = 0;
@@ -394,7 +395,7 @@ __global__ void __launch_bounds__(kBNT) k_batched(const BatchArgs *pp) {
         }
         if (threadIdx.x == 0) p.base[p.nmat] = carry;
     }
-    if (!grid_barrier(bar, p.err)) return;
+    if (!grid_barrier(bar, p.err, p.wait_spins, p.missing)) return;
     // phase 4: values
     run_items<V, true>(p, p.counters + 3, sm, nbig);
 }

@@ -171,6 +171,34 @@ __global__ void __launch_bounds__(256) k_learned_bin(RawOperands op, BinRule rul
     st.flush(bb);
 }
 
+// Numeric planning from the counts the symbolic phase kept (one RowGather
+// per row): a streaming pass, no gathers from B.
+__global__ void __launch_bounds__(256) k_rowinfo_cached(RawOperands op, const int64_t *c_rp, int64_t c_nnz,
+                                                        BinRule rule, BinBuffers bb, const RowGather *rec,
+                                                        int *err, const int *row_list, int64_t nrows) {
+    __shared__ RowStats st;
+    st.init();
+    __syncthreads();
+    const int lane = lane_id();
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (int64_t base = gw * 32; base < nrows; base += warps * 32) {
+        const int64_t r = base + lane;
+        const bool valid = r < nrows;
+        int64_t i = 0;
+        RowGather rg{0, 0, 0};
+        long long size = 0;
+        if (valid) {
+            i = row_list ? row_list[r] : r;
+            rg = rec[i];
+            size = row_size(i, rg.f, op, c_rp, c_nnz, nullptr, err);
+        }
+        bin_rows(valid, i, rg.na, rg.f, size, rule, bb, nullptr, st);
+    }
+    __syncthreads();
+    st.flush(bb);
+}
+
 // Short rows: one thread per row. Long rows: appended to long_list.
 template <bool LEARN>
 __global__ void __launch_bounds__(256) k_rowinfo(RawOperands op, const int64_t *c_rp, int64_t c_nnz, BinRule rule,
@@ -219,6 +247,8 @@ __global__ void __launch_bounds__(256) k_rowinfo(RawOperands op, const int64_t *
         } else {
             long long size = 0;
             if (valid) size = row_size(i, f, op, c_rp, c_nnz, bound_out, err);
+            // the symbolic phase keeps each row's counts for the numeric phase
+            if (valid && la.gather) la.gather[i] = RowGather{f, (int)(ae - ab), (int)(mx < INT_MAX ? mx : INT_MAX)};
             bin_rows(valid, i, ae - ab, f, size, rule, bb, c_rp ? nullptr : nnz_out, st);
         }
     }
@@ -267,6 +297,8 @@ __global__ void __launch_bounds__(256) k_rowinfo_long(RawOperands op, const int6
             } else {
                 long long size = 0;
                 if (lane == 0) size = row_size(i, f, op, c_rp, c_nnz, bound_out, err);
+                if (lane == 0 && la.gather)
+                    la.gather[i] = RowGather{f, (int)(ae - ab), (int)(mx < INT_MAX ? mx : INT_MAX)};
                 bin_rows(lane == 0, i, ae - ab, f, size, rule, bb, c_rp ? nullptr : nnz_out, st);
             }
         }
@@ -450,16 +482,24 @@ void launch_learned_bin(const RawOperands &op, const BinRule &rule, BinBuffers b
 }
 
 void launch_sym_rowinfo(const RawOperands &op, const BinRule &rule, BinBuffers bb, long long *bound_out,
-                        int *nnz_out, int *err, int sms, cudaStream_t s, const int *row_list, int64_t list_n) {
+                        int *nnz_out, int *err, int sms, cudaStream_t s, const int *row_list, int64_t list_n,
+                        RowGather *keep) {
     const int64_t n = row_list ? list_n : op.a_rows;
     if (n == 0) return;
-    rowinfo<false>(op, nullptr, 0, rule, bb, bound_out, nnz_out, err, sms, s, row_list, n);
+    LearnArgs la;
+    la.gather = keep;
+    rowinfo<false>(op, nullptr, 0, rule, bb, bound_out, nnz_out, err, sms, s, row_list, n, la);
 }
 
 void launch_num_rowinfo(const RawOperands &op, const int64_t *c_rp, int64_t c_nnz, const BinRule &rule,
-                        BinBuffers bb, int *err, int sms, cudaStream_t s, const int *row_list, int64_t list_n) {
+                        BinBuffers bb, int *err, int sms, cudaStream_t s, const int *row_list, int64_t list_n,
+                        const RowGather *kept) {
     const int64_t n = row_list ? list_n : op.a_rows;
     if (n == 0) return;
+    if (kept) {
+        k_rowinfo_cached<<<rowinfo_grid(n, sms), 256, 0, s>>>(op, c_rp, c_nnz, rule, bb, kept, err, row_list, n);
+        return;
+    }
     rowinfo<false>(op, c_rp, c_nnz, rule, bb, nullptr, nullptr, err, sms, s, row_list, n);
 }
 

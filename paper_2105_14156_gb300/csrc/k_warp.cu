@@ -16,10 +16,10 @@
 // the Hashing Phase's collision resolution). The numeric kernel adds a_ik*b_kj
 // to the slot's value (atomic add) and appends every newly claimed slot to a
 // list, so that the Write-back Phase visits the row's entries only, never the
-// whole table: a counting sort of the entries by the high bits of the column
-// (bucket counts kept at insertion), then each entry's rank inside its bucket,
-// and the row streamed to C in column order. The table is returned to EMPTY
-// through the same list.
+// whole table: the entries move to registers (their slots back to EMPTY), a
+// counting sort by the high bits of the column groups them by bucket in the
+// table's own memory, each entry's rank inside its bucket gives its place, and
+// the row streams to C in column order.
 #include <climits>
 
 #include "device_common.cuh"
@@ -30,6 +30,7 @@ namespace smash {
 
 constexpr int kWarpRowWarps = 4;   // warps (rows in flight) per block
 constexpr int kWarpUnroll = 4;     // steps of 32 products whose loads are issued together
+constexpr int kWarpMaxList = 512;  // most columns a warp row may hold (16 per lane)
 
 // Per-warp scratch of the register enumerator: one batch of entries.
 template <typename V>
@@ -38,6 +39,45 @@ struct EntryScratch {
     V av[32];
     int len[32];
 };
+
+// The row of B selected by column k of A (start and length, checked), for
+// kernels that never see B sliced by column window.
+template <typename V>
+__device__ __forceinline__ void b_row_whole(const Operands<V> &op, int k, int &len, int64_t &bs, int *err) {
+    len = 0;
+    bs = 0;
+    if ((unsigned)k < (unsigned)op.b_rows) {
+        const int64_t s = __ldg(op.b_rp + k), t = __ldg(op.b_rp + k + 1);
+        if (s >= 0 && t >= s && t <= op.b_nnz) {
+            if (t - s < kMaxBRow) {
+                bs = s;
+                len = (int)(t - s);
+            } else {
+                raise_err(err, kErrBRowTooLong);
+            }
+        } else {
+            raise_err(err, kErrBadRowPtr);
+        }
+    } else {
+        raise_err(err, kErrBadIndex);
+    }
+}
+
+// Bulk copy (the TMA engine's non-tensor copy) of `bytes` bytes, a multiple
+// of 16, from this block's shared memory to global memory of this GPU, both
+// addresses 16-byte aligned; issued by one thread, tracked by bulk groups.
+__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(__cvta_generic_to_global(gdst)),
+                 "r"((unsigned)__cvta_generic_to_shared(ssrc)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Waits until the committed bulk copies have read their shared-memory source
+// (bulk_wait_read) or have completed (bulk_wait_all).
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Orders this thread's earlier shared-memory writes before later bulk copies.
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Insertion of tag j into a shared-memory table of 2^tbits slots: the slot
 // (-1: the table is full), and whether this call claimed it.
@@ -58,17 +98,23 @@ __device__ __forceinline__ int cas_insert(int *keys, int tbits, HashCfg hc, int 
 }
 
 // Every product a_ik * b_kj of A entries [ab, ae), enumerated by one warp.
-// f(act, j, a, b) is called by all 32 lanes together once per step of 32
-// products (act: the lane holds a product), so that it may use warp votes.
-template <typename V, bool NUM, typename F>
+// f(act, j, a, b, p) is called by all 32 lanes together once per step of 32
+// products (act: the lane holds a product; p: its index among the row's
+// products), so that it may use warp votes.
+// IT: type of the positions in B (int32_t when B has fewer than 2^31 entries).
+template <typename V, typename IT, bool NUM, typename F>
 __device__ __forceinline__ void warp_enum(const Operands<V> &op, int64_t ab, int64_t ae, EntryScratch<V> &es,
                                           int *err, F &&f) {
     const int lane = lane_id();
+    int pbase = 0;   // products of the earlier batches
     for (int64_t base = ab; base < ae; base += 32) {
         int len = 0;
         int64_t bs = 0;
         V av = V(0);
-        if (base + lane < ae) load_a_entry<V, NUM>(op, base + lane, len, bs, av, err);
+        if (base + lane < ae) {
+            b_row_whole(op, __ldg(op.a_ci + base + lane), len, bs, err);
+            if constexpr (NUM) av = op.a_val[base + lane];
+        }
         // entries with an empty row of B would share their end with the entry
         // before them: move the others to the low lanes, in order
         const unsigned nz = __ballot_sync(kFull, len > 0);
@@ -88,7 +134,7 @@ __device__ __forceinline__ void warp_enum(const Operands<V> &op, int64_t ab, int
         }
         const int incl = warp_incl_scan(len);
         const int total = __shfl_sync(kFull, incl, 31);
-        const int64_t start = bs - (incl - len);   // product p of this entry reads B at start + p
+        const IT start = (IT)(bs - (incl - len));   // product p of this entry reads B at start + p
         for (int q0 = 0; q0 < total; q0 += 32 * kWarpUnroll) {
             int jv[kWarpUnroll];
             V a_u[kWarpUnroll], b_u[kWarpUnroll];
@@ -105,10 +151,10 @@ __device__ __forceinline__ void warp_enum(const Operands<V> &op, int64_t ab, int
                     const int e = incl - q;
                     const unsigned ends = __reduce_or_sync(kFull, (e >= 1 && e <= 31) ? (1u << e) : 0u);
                     const int ci = c0 + __popc(ends & ((2u << lane) - 1u));
-                    const int64_t st = __shfl_sync(kFull, start, ci);
+                    const IT st = __shfl_sync(kFull, start, ci);
                     if constexpr (NUM) a_u[u] = __shfl_sync(kFull, av, ci);
                     if (act[u]) {
-                        const int64_t idx = st + q + lane;
+                        const IT idx = st + (IT)(q + lane);
                         jv[u] = __ldg(op.b_ci + idx);
                         if constexpr (NUM) b_u[u] = __ldg(op.b_val + idx);
                     }
@@ -122,15 +168,16 @@ __device__ __forceinline__ void warp_enum(const Operands<V> &op, int64_t ab, int
                         raise_err(err, kErrBadIndex);
                         ok = false;
                     }
-                    f(ok, jv[u], a_u[u], b_u[u]);
+                    f(ok, jv[u], a_u[u], b_u[u], pbase + q0 + 32 * u + lane);
                 }
             }
         }
+        pbase += total;
     }
 }
 
 // ----- symbolic --------------------------------------------------------------
-template <int NW>
+template <typename IT, int NW>
 __global__ void __launch_bounds__(NW * 32) k_sym_warp(Operands<float> op, const int *rows, int count, int *token,
                                                       int tbits, HashCfg hc, int *nnz_out, int *err) {
     using G = Group<32, NW * 32>;
@@ -152,7 +199,7 @@ __global__ void __launch_bounds__(NW * 32) k_sym_warp(Operands<float> op, const 
         int64_t ab, ae;
         a_row_range(op, i, ab, ae, err);
         int cnt = 0, full = 0;
-        warp_enum<float, false>(op, ab, ae, es, err, [&](bool act, int j, float, float) {
+        warp_enum<float, IT, false>(op, ab, ae, es, err, [&](bool act, int j, float, float, int) {
             bool ins = false;
             if (act && cas_insert(keys, tbits, hc, j, ins) < 0) full = 1;
             cnt += __popc(__ballot_sync(kFull, ins));
@@ -169,30 +216,33 @@ __global__ void __launch_bounds__(NW * 32) k_sym_warp(Operands<float> op, const 
 
 // ----- numeric ---------------------------------------------------------------
 // Shared memory of one warp: keys[T], vals[T], list[L] (slots claimed by the
-// row), bc[NB] (bucket counts), gk[L], gv[L] (entries grouped by bucket),
-// then the enumerator's scratch.
+// row), bc[NB] (bucket counts), then the enumerator's scratch. The write-out
+// groups the row's entries by bucket in keys[0..n), vals[0..n).
 template <typename V>
 __host__ __device__ constexpr size_t warp_row_bytes(int T, int L, int NB) {
-    return (size_t)T * (4 + sizeof(V)) + (size_t)L * (8 + sizeof(V)) + (size_t)NB * 4 + sizeof(EntryScratch<V>);
+    return (size_t)T * (4 + sizeof(V)) + (size_t)L * 4 + (size_t)NB * 4 + sizeof(EntryScratch<V>);
 }
 
-template <typename V, int NW>
+// K: entries held per lane in the write-out (the list room L <= 32 K).
+// rec (may be null): the rows' product counts kept by the symbolic phase. A
+// row whose exact length equals its product count has no repeated column:
+// nothing to merge, so its products skip the table and go straight to the
+// write-out's staging (keys[p], vals[p] for product p).
+template <typename V, typename IT, int K, int NW>
 __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int *rows, int count, int *token,
-                                                      int tbits, HashCfg hc, int lcap, int nbb, int bsh,
-                                                      NumOutT<V> out, int *err) {
+                                                      int tbits, HashCfg hc, int lcap, int nb, int bsh,
+                                                      const RowGather *rec, int bulk, NumOutT<V> out, int *err) {
     using G = Group<32, NW * 32>;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_row[2][NW];
     const int T = 1 << tbits;
-    const int NB = T >> nbb;
+    const int NB = nb;
     unsigned char *wb = smem + (size_t)G::gid() * warp_row_bytes<V>(T, lcap, NB);
     int *keys = (int *)wb;
     V *vals = (V *)(wb + (size_t)T * 4);
     int *list = (int *)(wb + (size_t)T * (4 + sizeof(V)));
     int *bc = list + lcap;
-    int *gk = bc + NB;
-    V *gv = (V *)(gk + lcap);
-    EntryScratch<V> &es = *(EntryScratch<V> *)(gv + lcap);
+    EntryScratch<V> &es = *(EntryScratch<V> *)(bc + NB);
     const int lane = lane_id();
     for (int s = lane; s < T; s += 32) {
         keys[s] = kEmpty;
@@ -211,25 +261,32 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
         int64_t ab = 0, ae = 0;
         if (ok) a_row_range(op, i, ab, ae, err);
         int cnt = 0, full = 0;
-        warp_enum<V, true>(op, ab, ae, es, err, [&](bool act, int j, V a, V b) {
-            bool ins = false;
-            int h = -1;
-            if (act) {
-                h = cas_insert(keys, tbits, hc, j, ins);
-                if (h >= 0) {
-                    atomicAdd(vals + h, a * b);
-                    if (ins) atomicAdd(bc + (j >> bsh), 1);
-                } else {
-                    full = 1;
+        const bool direct = rec && !out.row_nnz && ok && n_exp <= lcap && rec[i].f == (long long)n_exp;
+        if (direct) {
+            warp_enum<V, IT, true>(op, ab, ae, es, err, [&](bool act, int j, V a, V b, int p) {
+                if (act && p < lcap) {
+                    keys[p] = j;
+                    vals[p] = a * b;
                 }
-            }
-            const unsigned m = __ballot_sync(kFull, ins);
-            if (ins) {
-                const int pos = cnt + __popc(m & lanemask_lt());
-                if (pos < lcap) list[pos] = h;
-            }
-            cnt += __popc(m);
-        });
+                cnt += __popc(__ballot_sync(kFull, act));
+            });
+        } else {
+            warp_enum<V, IT, true>(op, ab, ae, es, err, [&](bool act, int j, V a, V b, int) {
+                bool ins = false;
+                int h = -1;
+                if (act) {
+                    h = cas_insert(keys, tbits, hc, j, ins);
+                    if (h >= 0) atomicAdd(vals + h, a * b);
+                    else full = 1;
+                }
+                const unsigned m = __ballot_sync(kFull, ins);
+                if (ins) {
+                    const int pos = cnt + __popc(m & lanemask_lt());
+                    if (pos < lcap) list[pos] = h;
+                }
+                cnt += __popc(m);
+            });
+        }
         full = __any_sync(kFull, full);
         const int tot = cnt;
         bool over;
@@ -245,8 +302,8 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
         }
         __syncwarp();
         if (over) {
-            // nothing is written; the table and the counts go back to zero
-            if (full || tot > lcap) {
+            // nothing is written; the table goes back to EMPTY / 0
+            if (full || tot > lcap || direct) {
                 for (int s = lane; s < T; s += 32) {
                     keys[s] = kEmpty;
                     vals[s] = V(0);
@@ -258,13 +315,12 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
                     vals[h] = V(0);
                 }
             }
-            for (int s = lane; s < NB; s += 32) bc[s] = 0;
         } else if (tot <= 32) {
             // rank of each entry among the row's (at most 32) columns
             int k = INT_MAX;
             V v = V(0);
             if (lane < tot) {
-                const int h = list[lane];
+                const int h = direct ? lane : list[lane];
                 k = keys[h];
                 v = vals[h];
                 keys[h] = kEmpty;
@@ -276,9 +332,27 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
                 out.c_ci[c0 + rank] = k;
                 out.c_val[c0 + rank] = v;
             }
-            for (int s = lane; s < NB; s += 32) bc[s] = 0;
         } else {
-            // bucket starts: each lane sums a run of consecutive buckets
+            // 1. the entries into registers, their slots back to EMPTY / 0,
+            //    counts per bucket (bucket = column >> bsh, monotone in the column)
+            int kk[K];
+            V vv[K];
+#pragma unroll
+            for (int x = 0; x < K; ++x) {
+                const int q = lane + 32 * x;
+                kk[x] = INT_MAX;
+                vv[x] = V(0);
+                if (q < tot) {
+                    const int h = direct ? q : list[q];
+                    kk[x] = keys[h];
+                    vv[x] = vals[h];
+                    keys[h] = kEmpty;
+                    vals[h] = V(0);
+                    atomicAdd(bc + (kk[x] >> bsh), 1);
+                }
+            }
+            __syncwarp();
+            // 2. bucket starts: each lane sums a run of consecutive buckets
             {
                 const int run = (NB + 31) >> 5;
                 const int b0 = min(lane * run, NB), b1 = min(b0 + run, NB);
@@ -292,34 +366,96 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
                 }
             }
             __syncwarp();
-            // group the entries by bucket; the table goes back to EMPTY / 0
-            for (int q = lane; q < tot; q += 32) {
-                const int h = list[q];
-                const int k = keys[h];
-                const V v = vals[h];
-                keys[h] = kEmpty;
-                vals[h] = V(0);
-                const int p = atomicAdd(bc + (k >> bsh), 1);
-                gk[p] = k;
-                gv[p] = v;
+            // 3. grouped by bucket into keys[0..tot), vals[0..tot)
+#pragma unroll
+            for (int x = 0; x < K; ++x) {
+                if (lane + 32 * x < tot) {
+                    const int p = atomicAdd(bc + (kk[x] >> bsh), 1);
+                    keys[p] = kk[x];
+                    vals[p] = vv[x];
+                }
             }
             __syncwarp();
-            // bc[b] is now the end of bucket b: rank inside the bucket
-            for (int q = lane; q < tot; q += 32) {
-                const int k = gk[q];
-                const int b = k >> bsh;
-                const int e = bc[b];
-                const int s0 = b ? bc[b - 1] : 0;
-                int rk = 0;
-                for (int x = s0; x < e; ++x) rk += gk[x] < k ? 1 : 0;
-                out.c_ci[c0 + s0 + rk] = k;
-                out.c_val[c0 + s0 + rk] = gv[q];
+            // 4. bc[b] is now the end of bucket b: each entry's place is its
+            //    bucket's start plus the smaller columns in its bucket.
+            // 5. with bulk != 0 (C's arrays 16-byte aligned) the sorted row is
+            //    staged in the table's memory, element e at e + (c0 mod 16 bytes),
+            //    and streamed to C: the aligned middle by one bulk copy per
+            //    array, the ragged ends by the lanes that hold them (Version 3's
+            //    bulk copy-out); otherwise every lane stores its entries
+            constexpr int UK = 4, UV = 16 / (int)sizeof(V);
+            if (bulk && tot + UK <= T) {
+                int pos[K];
+#pragma unroll
+                for (int x = 0; x < K; ++x) {
+                    pos[x] = -1;
+                    if (lane + 32 * x < tot) {
+                        const int b = kk[x] >> bsh;
+                        const int e = bc[b];
+                        const int s0 = b ? bc[b - 1] : 0;
+                        int rk = 0;
+                        for (int y = s0; y < e; ++y) rk += keys[y] < kk[x] ? 1 : 0;
+                        pos[x] = s0 + rk;
+                    }
+                }
+                __syncwarp();
+                const int ok_off = (int)(c0 % UK), ov_off = (int)(c0 % UV);
+#pragma unroll
+                for (int x = 0; x < K; ++x) {
+                    if (pos[x] >= 0) {
+                        keys[ok_off + pos[x]] = kk[x];
+                        vals[ov_off + pos[x]] = vv[x];
+                    }
+                }
+                fence_async_smem();
+                __syncwarp();
+                const int64_t gk0 = (c0 + UK - 1) / UK * UK, gk1 = (c0 + tot) / UK * UK;
+                const int64_t gv0 = (c0 + UV - 1) / UV * UV, gv1 = (c0 + tot) / UV * UV;
+                if (lane == 0) {
+                    if (gk1 > gk0)
+                        bulk_store(out.c_ci + gk0, keys + ok_off + (gk0 - c0), (unsigned)((gk1 - gk0) * 4));
+                    if (gv1 > gv0)
+                        bulk_store(out.c_val + gv0, vals + ov_off + (gv0 - c0), (unsigned)((gv1 - gv0) * sizeof(V)));
+                    bulk_commit();
+                }
+#pragma unroll
+                for (int x = 0; x < K; ++x) {
+                    if (pos[x] >= 0) {
+                        const int64_t g = c0 + pos[x];
+                        if (g < gk0 || g >= gk1) out.c_ci[g] = kk[x];
+                        if (g < gv0 || g >= gv1) out.c_val[g] = vv[x];
+                    }
+                }
+                if (lane == 0) bulk_wait_read();
+                __syncwarp();
+            } else {
+#pragma unroll
+                for (int x = 0; x < K; ++x) {
+                    if (lane + 32 * x < tot) {
+                        const int b = kk[x] >> bsh;
+                        const int e = bc[b];
+                        const int s0 = b ? bc[b - 1] : 0;
+                        int rk = 0;
+                        for (int y = s0; y < e; ++y) rk += keys[y] < kk[x] ? 1 : 0;
+                        out.c_ci[c0 + s0 + rk] = kk[x];
+                        out.c_val[c0 + s0 + rk] = vv[x];
+                    }
+                }
+                __syncwarp();
             }
-            __syncwarp();
-            for (int s = lane; s < NB; s += 32) bc[s] = 0;
+            const int used = min(T, tot + UK);
+            for (int q = lane; q < used; q += 32) {
+                keys[q] = kEmpty;
+                vals[q] = V(0);
+            }
         }
+        // bucket counts back to zero (the insertion left them untouched when
+        // the row took no bucket write-out)
+        if (!over && tot > 32)
+            for (int s = lane; s < NB; s += 32) bc[s] = 0;
         __syncwarp();
     }
+    if (bulk && lane == 0) bulk_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -358,15 +494,22 @@ void launch_sym_warp(const RawOperands &r, const int *rows, int count, int *toke
     if (count <= 0) return;
     const Operands<float> op = warp_operands<float>(r);
     const size_t smem = sym_warp_smem(hl.tbits);
-    auto kern = k_sym_warp<kWarpRowWarps>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const HashCfg hc{hl.hash_kind, hl.colbits};
-    kern<<<warp_grid(kern, smem, hl.sms, count), kWarpRowWarps * 32, smem, s>>>(op, rows, count, token, hl.tbits, hc,
-                                                                              nnz_out, err);
+    if (r.b_nnz < INT_MAX) {
+        auto kern = k_sym_warp<int32_t, kWarpRowWarps>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<warp_grid(kern, smem, hl.sms, count), kWarpRowWarps * 32, smem, s>>>(op, rows, count, token,
+                                                                                  hl.tbits, hc, nnz_out, err);
+    } else {
+        auto kern = k_sym_warp<int64_t, kWarpRowWarps>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<warp_grid(kern, smem, hl.sms, count), kWarpRowWarps * 32, smem, s>>>(op, rows, count, token,
+                                                                                  hl.tbits, hc, nnz_out, err);
+    }
 }
 
 // List room L: the most columns a row of the bin may hold (T * max_load,
-// rounded up to 32, at most T); NB = T / 4 buckets over the column range.
+// rounded up to 32, at most T); NB = T / 2 buckets over the column range.
 static int warp_lcap(int tbits, float inv_load) {
     const int T = 1 << tbits;
     int L = (int)((double)T / (double)inv_load + 0.999);
@@ -374,38 +517,64 @@ static int warp_lcap(int tbits, float inv_load) {
     return L < 32 ? 32 : (L > T ? T : L);
 }
 
+static int warp_buckets(int tbits) { return (1 << tbits) >> 1; }
+
 size_t num_warp_smem(int dtype, int tbits, float inv_load) {
     const int T = 1 << tbits;
     const int L = warp_lcap(tbits, inv_load);
-    const int NB = T >> 2;
+    if (L > kWarpMaxList) return SIZE_MAX;   // more entries than the write-out's registers hold
+    const int NB = warp_buckets(tbits);
     const size_t per = dtype ? warp_row_bytes<double>(T, L, NB) : warp_row_bytes<float>(T, L, NB);
     return (size_t)kWarpRowWarps * per;
 }
 
-template <typename V>
-static void num_warp_typed(const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
-                           float inv_load, const NumOut &o, int *err, cudaStream_t s) {
-    const Operands<V> op = warp_operands<V>(r);
-    const NumOutT<V> out{o.c_rp, o.c_ci, (V *)o.c_val, o.c_nnz, o.row_nnz};
-    const int L = warp_lcap(hl.tbits, inv_load);
-    const int nbb = 2;
-    const int NB = (1 << hl.tbits) >> nbb;
+template <typename V, typename IT, int K>
+static void num_warp_go(const Operands<V> &op, const int *rows, int count, int *token, const HashLaunch &hl,
+                        int L, const RowGather *rec, int bulk_copy, const NumOutT<V> &out, int *err, cudaStream_t s,
+                        size_t smem) {
+    const int NB = warp_buckets(hl.tbits);
     int nbbits = 0;
     while ((1 << nbbits) < NB) ++nbbits;
     const int bsh = hl.colbits > nbbits ? hl.colbits - nbbits : 0;
-    const size_t smem = num_warp_smem(sizeof(V) == 8, hl.tbits, inv_load);
-    auto kern = k_num_warp<V, kWarpRowWarps>;
+    // bulk copies need 16-byte aligned destinations: C's arrays must start
+    // on a 16-byte boundary (the row offsets are handled in the kernel)
+    const int bulk = (bulk_copy && (uintptr_t)out.c_ci % 16 == 0 && (uintptr_t)out.c_val % 16 == 0) ? 1 : 0;
+    auto kern = k_num_warp<V, IT, K, kWarpRowWarps>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const HashCfg hc{hl.hash_kind, hl.colbits};
     kern<<<warp_grid(kern, smem, hl.sms, count), kWarpRowWarps * 32, smem, s>>>(op, rows, count, token, hl.tbits, hc,
-                                                                              L, nbb, bsh, out, err);
+                                                                              L, NB, bsh, rec, bulk, out, err);
+}
+
+template <typename V, typename IT>
+static void num_warp_k(const Operands<V> &op, const int *rows, int count, int *token, const HashLaunch &hl, int L,
+                       const RowGather *rec, int bulk_copy, const NumOutT<V> &out, int *err, cudaStream_t s,
+                       size_t smem) {
+    const int k = (L + 31) / 32;
+    if (k <= 2) num_warp_go<V, IT, 2>(op, rows, count, token, hl, L, rec, bulk_copy, out, err, s, smem);
+    else if (k <= 4) num_warp_go<V, IT, 4>(op, rows, count, token, hl, L, rec, bulk_copy, out, err, s, smem);
+    else if (k <= 8) num_warp_go<V, IT, 8>(op, rows, count, token, hl, L, rec, bulk_copy, out, err, s, smem);
+    else num_warp_go<V, IT, 16>(op, rows, count, token, hl, L, rec, bulk_copy, out, err, s, smem);
+}
+
+template <typename V>
+static void num_warp_typed(const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
+                           float inv_load, const RowGather *rec, int bulk_copy, const NumOut &o, int *err,
+                           cudaStream_t s) {
+    const Operands<V> op = warp_operands<V>(r);
+    const NumOutT<V> out{o.c_rp, o.c_ci, (V *)o.c_val, o.c_nnz, o.row_nnz};
+    const int L = warp_lcap(hl.tbits, inv_load);
+    const size_t smem = num_warp_smem(sizeof(V) == 8, hl.tbits, inv_load);
+    if (r.b_nnz < INT_MAX) num_warp_k<V, int32_t>(op, rows, count, token, hl, L, rec, bulk_copy, out, err, s, smem);
+    else num_warp_k<V, int64_t>(op, rows, count, token, hl, L, rec, bulk_copy, out, err, s, smem);
 }
 
 void launch_num_warp(int dtype, const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
-                     float inv_load, const NumOut &out, int *err, cudaStream_t s) {
+                     float inv_load, const RowGather *rec, int bulk_copy, const NumOut &out, int *err,
+                     cudaStream_t s) {
     if (count <= 0) return;
-    if (dtype) num_warp_typed<double>(r, rows, count, token, hl, inv_load, out, err, s);
-    else num_warp_typed<float>(r, rows, count, token, hl, inv_load, out, err, s);
+    if (dtype) num_warp_typed<double>(r, rows, count, token, hl, inv_load, rec, bulk_copy, out, err, s);
+    else num_warp_typed<float>(r, rows, count, token, hl, inv_load, rec, bulk_copy, out, err, s);
 }
 
 }  // namespace smash

@@ -42,24 +42,28 @@ struct BinBuffers {
     long long *sums;   // [3][16] per bin: sum nnz(A_i), sum flop_i, sum size bound
 };
 
-// k_rows.cu. With row_list != nullptr only the listed rows are planned (the
-// caller clears bb.bin first so that the other rows stay in the empty bin).
-void launch_sym_rowinfo(const RawOperands &op, const BinRule &rule, BinBuffers bb, long long *bound_out,
-                        int *nnz_out, int *err, int sms, cudaStream_t s, const int *row_list = nullptr,
-                        int64_t list_n = 0);
-void launch_num_rowinfo(const RawOperands &op, const int64_t *c_rp, int64_t c_nnz, const BinRule &rule,
-                        BinBuffers bb, int *err, int sms, cudaStream_t s, const int *row_list = nullptr,
-                        int64_t list_n = 0);
-// Learned planning (k_rows.cu): features, the predictor and each row's
-// capacity cap_i (mlp.cuh) in the planning passes; rows binned by cap_i.
-// Two passes: the rows' flop counts and longest rows of B (gather, one row
-// per thread, long rows per warp), then the predictor on the tensor cores
-// and the bins.
+// Per-row counts of the planning passes.
 struct RowGather {
     long long f;   // flop_i
     int na;        // nnz(A_i)
     int mx;        // longest selected row of B
 };
+// k_rows.cu. With row_list != nullptr only the listed rows are planned (the
+// caller clears bb.bin first so that the other rows stay in the empty bin).
+// keep != nullptr: the symbolic planning also records every planned row's
+// counts there; kept != nullptr: the numeric planning reads them instead of
+// gathering from B again.
+void launch_sym_rowinfo(const RawOperands &op, const BinRule &rule, BinBuffers bb, long long *bound_out,
+                        int *nnz_out, int *err, int sms, cudaStream_t s, const int *row_list = nullptr,
+                        int64_t list_n = 0, RowGather *keep = nullptr);
+void launch_num_rowinfo(const RawOperands &op, const int64_t *c_rp, int64_t c_nnz, const BinRule &rule,
+                        BinBuffers bb, int *err, int sms, cudaStream_t s, const int *row_list = nullptr,
+                        int64_t list_n = 0, const RowGather *kept = nullptr);
+// Learned planning (k_rows.cu): features, the predictor and each row's
+// capacity cap_i (mlp.cuh) in the planning passes; rows binned by cap_i.
+// Two passes: the rows' flop counts and longest rows of B (gather, one row
+// per thread, long rows per warp), then the predictor on the tensor cores
+// and the bins.
 struct LearnArgs {
     const void *wb = nullptr;     // bf16 weights (device)
     const float *norm = nullptr;  // mean[6], inv_std[6] (device)
@@ -169,8 +173,12 @@ size_t sym_warp_smem(int tbits);
 size_t num_warp_smem(int dtype, int tbits, float inv_load);
 void launch_sym_warp(const RawOperands &op, const int *rows, int count, int *token, const HashLaunch &hl,
                      int *nnz_out, int *err, cudaStream_t s);
+// rec (may be null): per-row counts kept by the symbolic phase; rows whose
+// exact length equals their product count skip the table.
+// bulk_copy: stream sorted rows to C by bulk copies from shared memory.
 void launch_num_warp(int dtype, const RawOperands &op, const int *rows, int count, int *token,
-                     const HashLaunch &hl, float inv_load, const NumOut &out, int *err, cudaStream_t s);
+                     const HashLaunch &hl, float inv_load, const RowGather *rec, int bulk_copy, const NumOut &out,
+                     int *err, cudaStream_t s);
 // Thread-per-row bins (tbits <= BinRule::tiny_tbits, k_tiny.cu): list length of a bin, and
 // the symbolic count / numeric merge of its rows.
 int tiny_list_len(int tbits, float max_load);

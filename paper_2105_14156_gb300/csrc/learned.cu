@@ -17,6 +17,8 @@ using namespace smash::host;
 struct smash_model {
     smash_handle *h = nullptr;
     DevBuf block;
+    smash_free_fn free_fn = nullptr;   // the allocator that provided block
+    void *ctx = nullptr;
     float *params = nullptr;  // fp32 master weights
     float *grad = nullptr;
     float *m = nullptr;
@@ -94,6 +96,8 @@ int smash_model_create(smash_handle *h, smash_model **out, uint64_t seed) {
         delete m;
         return SMASH_ERR_ALLOC;
     }
+    m->free_fn = h->free_fn;
+    m->ctx = h->ctx;
     cudaDeviceSynchronize();
     Carver c(m->block.ptr);
     m->params = c.take<float>(P);
@@ -118,7 +122,8 @@ int smash_model_create(smash_handle *h, smash_model **out, uint64_t seed) {
     }
     if (cudaMemcpy(m->norm, norm, sizeof(norm), cudaMemcpyHostToDevice) != cudaSuccess ||
         upload_params(m, p.data(), 0) != SMASH_OK) {
-        release(h, m->block);
+        cudaDeviceSynchronize();
+        m->free_fn(m->block.ptr, m->ctx);
         delete m;
         return SMASH_ERR_CUDA;
     }
@@ -130,7 +135,8 @@ int smash_model_destroy(smash_model *m) {
     if (!m) return SMASH_ERR_INVALID_ARG;
     {
         DeviceGuard g(m->h->device);
-        release(m->h, m->block);
+        cudaDeviceSynchronize();
+        if (m->block.ptr) m->free_fn(m->block.ptr, m->ctx);   // with the allocator that provided it
     }
     delete m;
     return SMASH_OK;
@@ -400,12 +406,32 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
     C->row_ptr = nullptr;
     C->col_idx = nullptr;
     C->val = nullptr;
+    // C's arrays go back to the allocator if the call fails
+    struct CGuard {
+        smash_handle *h;
+        smash_csr *C;
+        bool keep = false;
+        ~CGuard() {
+            if (keep) return;
+            cudaDeviceSynchronize();
+            cudaGetLastError();
+            if (C->row_ptr) h->free_fn(C->row_ptr, h->ctx);
+            if (C->col_idx) h->free_fn(C->col_idx, h->ctx);
+            if (C->val) h->free_fn(C->val, h->ctx);
+            C->row_ptr = nullptr;
+            C->col_idx = nullptr;
+            C->val = nullptr;
+            C->nnz = 0;
+        }
+    } guard{h, C};
     C->row_ptr = (int64_t *)h->alloc(sizeof(int64_t) * (size_t)(n + 1), h->ctx);
     if (!C->row_ptr) return SMASH_ERR_ALLOC;
     if (n == 0 || A->nnz == 0 || B->nnz == 0) {
         cudaMemsetAsync(C->row_ptr, 0, sizeof(int64_t) * (size_t)(n + 1), s);
         if (stats) *stats = ls;
-        return cudaStreamSynchronize(s) == cudaSuccess ? SMASH_OK : SMASH_ERR_CUDA;
+        const int rc = cudaStreamSynchronize(s) == cudaSuccess ? SMASH_OK : SMASH_ERR_CUDA;
+        guard.keep = rc == SMASH_OK;
+        return rc;
     }
     const RawOperands op = raw_ops(A, B);
     int *err = (int *)h->err.ptr;
@@ -572,6 +598,7 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
     st = read_flags(h, s, true);
     h->stats.c_nnz = cnnz;
     if (stats) *stats = ls;
+    guard.keep = st == SMASH_OK;
     return st;
 }
 

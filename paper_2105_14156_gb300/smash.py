@@ -29,7 +29,8 @@ EXPORTS = [
     "smash_model_save", "smash_model_load", "smash_row_features", "smash_mlp_train", "smash_mlp_gradient",
     "smash_mlp_predict", "smash_mlp_predict_tc", "spgemm_learned", "smash_free_csr", "spgemm_symbolic_noalloc",
     "spgemm_batched", "smash_batched_set_table_bits", "smash_batched_get_table_bits", "smash_batched_autotune",
-    "smash_training_rows",
+    "smash_training_rows", "smash_batched_set_wait", "smash_batched_set_row_cutoffs",
+    "smash_batched_get_row_cutoffs",
 ]
 
 
@@ -88,7 +89,7 @@ class Params(ctypes.Structure):
                 ("dense_ratio", ctypes.c_int32), ("bitmap_ratio", ctypes.c_int32),
                 ("spill_blocks_per_sm", ctypes.c_int32), ("sym_dense_ratio", ctypes.c_int32),
                 ("dense_blocks", ctypes.c_int32), ("sym_dense_blocks", ctypes.c_int32),
-                ("warp_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("warp_rows", ctypes.c_int32), ("bulk_copy", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -165,6 +166,9 @@ def load_library(path: str = LIB_PATH):
                                        ctypes.c_int, ctypes.POINTER(CsrStruct), ctypes.POINTER(BatchedStats), P]
         lib.smash_batched_set_table_bits.argtypes = [P, ctypes.c_int]
         lib.smash_batched_get_table_bits.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
+        lib.smash_batched_set_wait.argtypes = [P, ctypes.c_int64, ctypes.c_int]
+        lib.smash_batched_set_row_cutoffs.argtypes = [P, ctypes.c_int, ctypes.c_int]
+        lib.smash_batched_get_row_cutoffs.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         lib.smash_batched_autotune.argtypes = [P, ctypes.c_int, ctypes.POINTER(CsrStruct),
                                                ctypes.POINTER(CsrStruct), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_float), P]
@@ -309,6 +313,22 @@ class Handle:
 
         self._alloc_cb = ALLOC(_alloc)   # keep the callbacks alive
         self._free_cb = FREE(_free)
+        _check(self.lib.smash_set_allocator(self.h, ctypes.cast(self._alloc_cb, ctypes.c_void_p),
+                                            ctypes.cast(self._free_cb, ctypes.c_void_p), None),
+               "smash_set_allocator")
+
+    def set_allocator(self, alloc=None, free=None):
+        """Route the handle's device allocations through Python callables:
+        alloc(nbytes) -> device pointer (int, 0 on failure), free(ptr). None
+        restores cudaMalloc / cudaFree."""
+        ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+        FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+        if alloc is None:
+            _check(self.lib.smash_set_allocator(self.h, None, None, None), "smash_set_allocator")
+            self._alloc_cb = self._free_cb = None
+            return
+        self._alloc_cb = ALLOC(lambda nbytes, ctx: alloc(int(nbytes)) or None)
+        self._free_cb = FREE(lambda ptr, ctx: free(ptr))
         _check(self.lib.smash_set_allocator(self.h, ctypes.cast(self._alloc_cb, ctypes.c_void_p),
                                             ctypes.cast(self._free_cb, ctypes.c_void_p), None),
                "smash_set_allocator")
@@ -510,7 +530,24 @@ def _batched_table_bits(self, bits=None):
     return int(b.value)
 
 
+def _batched_set_wait(self, wait_spins: int = 0, missing_arrivals: int = 0):
+    _check(self.lib.smash_batched_set_wait(self.h, int(wait_spins), int(missing_arrivals)), "smash_batched_set_wait")
+
+
+def _batched_row_cutoffs(self, warp_less=None, block_more=None):
+    """Set (when given) and return (warp_less, block_more) of the batched kernel."""
+    if warp_less is not None:
+        _check(self.lib.smash_batched_set_row_cutoffs(self.h, int(warp_less), int(block_more)),
+               "smash_batched_set_row_cutoffs")
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    _check(self.lib.smash_batched_get_row_cutoffs(self.h, ctypes.byref(a), ctypes.byref(b)),
+           "smash_batched_get_row_cutoffs")
+    return int(a.value), int(b.value)
+
+
 Handle.spgemm_batched = _batched
+Handle.batched_row_cutoffs = _batched_row_cutoffs
+Handle.batched_set_wait = _batched_set_wait
 Handle.batched_autotune = _batched_autotune
 Handle.batched_table_bits = _batched_table_bits
 

@@ -97,3 +97,22 @@ def test_batched_repeat_and_autotune(handle):
         owner.free()
         for (A, B), C in zip(pairs, host):
             assert_matches_oracle(C, A, B)
+
+
+@pytest.mark.parametrize("cutoffs", [(0, 3), (1, 2), (3, 0), (2, 1)])
+def test_batched_row_cutoffs(handle, cutoffs):
+    """Rows moved between the warp, block and regular paths by the cutoffs:
+    the products are the same."""
+    pairs = [
+        (rmat(10, 16, GRAPH500_ABCD, seed=91, values="f32"), rmat(10, 16, GRAPH500_ABCD, seed=92, values="f32")),
+        (random_csr(300, 400, 0.05, 93, values="f32"), random_csr(400, 30000, 0.004, 94, values="f32")),
+    ] + small_pairs(6, seed=13)
+    handle.batched_table_bits(9)
+    handle.batched_row_cutoffs(*cutoffs)
+    try:
+        host, stats = run_batch(handle, pairs)
+    finally:
+        handle.batched_row_cutoffs(0, 3)
+        handle.batched_table_bits(10)
+    for (A, B), C in zip(pairs, host):
+        assert_matches_oracle(C, A, B)

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 DEFAULT = dict(hash_kind=1, max_load=0.5, sym_max_tbits=15, num_max_tbits=14, group_shift=4, dense_ratio=4,
                bitmap_ratio=4, spill_blocks_per_sm=1, sym_dense_ratio=64, dense_blocks=0,
-               sym_dense_blocks=0, warp_rows=1)
+               sym_dense_blocks=0, warp_rows=1, bulk_copy=0)
 
 # Parameter sets that force each path.
 PATHS = {
@@ -35,6 +35,7 @@ PATHS = {
     "symbolic_dense_eight_blocks_per_sm": dict(sym_dense_ratio=1 << 20, sym_dense_blocks=8),
     "group_per_row": dict(group_shift=0),
     "warp_rows_staged": dict(warp_rows=0),
+    "bulk_copy_out": dict(bulk_copy=1),
     "warp_rows_wide": dict(group_shift=6),
     "bitonic_only": dict(bitmap_ratio=0),
     "bitmap_always": dict(bitmap_ratio=1 << 20),
@@ -281,3 +282,22 @@ def test_repeatable_structure(handle):
     C2 = run(handle, A, A)
     assert np.array_equal(C1.row_ptr, C2.row_ptr)
     assert np.array_equal(C1.col_idx, C2.col_idx)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_output_arrays_not_16_byte_aligned(handle, dtype):
+    """C's arrays starting off a 16-byte boundary: the rows are stored by the
+    lanes instead of bulk copies; the result is the same."""
+    import torch
+    from paper_2105_14156_gb300 import smash
+    handle.set_params(**dict(DEFAULT, bulk_copy=1))
+    A = rmat(11, 8, (0.45, 0.15, 0.15, 0.25), seed=23, values=dtype)
+    dA = smash.to_device(A)
+    c_rp, nnz = handle.symbolic(dA, dA)
+    ci = torch.empty(nnz + 1, dtype=torch.int32, device="cuda")[1:]
+    val = torch.empty(nnz + 1, dtype=dA.val.dtype, device="cuda")[1:]
+    assert ci.data_ptr() % 16 != 0 and val.data_ptr() % 16 != 0
+    out = smash.DeviceCsr(A.rows, A.cols, c_rp, ci, val)
+    C = handle.numeric(dA, dA, c_rp, nnz, out=out)
+    handle.check()
+    assert_matches_oracle(C.to_host(), A, A)
