@@ -77,8 +77,9 @@ __device__ __forceinline__ void writeout_bitonic(int *keys, V *vals, int T, int 
     int n = 0;
     for (int s0 = 0; s0 < T; s0 += GS) {
         const int s = s0 + t;
-        const int k = keys[s];
-        const V v = vals[s];
+        // (a table smaller than the group: the threads past its end hold nothing)
+        const int k = s < T ? keys[s] : kEmpty;
+        const V v = s < T ? vals[s] : V(0);
         const int occ = k != kEmpty ? 1 : 0;
         int ct;
         const int pos = n + G::template excl_scan<int>(occ, red, &ct);
