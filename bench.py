@@ -1,27 +1,34 @@
 """Benchmark of the SMASH row-wise hash SpGEMM on GB300, through the C ABI.
 
-Main line (value): one step = the whole plain two-pass path on R-MAT scale 16
-(edge factor 16, Graph500 a,b,c,d, float64 U[-1,1]), C = A*A with A and B
-separate copies resident in HBM: per-row product counts and binning, the
-symbolic hash pass, the row-pointer scan, allocation of C, the numeric pass
-(shared-memory tables, dense rows as column-window work items, global-memory
-spill, per-row sorted write-out). L2 (129 MB) is flushed between timed steps
-by writing a 256 MiB buffer outside the timed region. value = useful GFLOP/s
-= 2 * products / step time (CUDA events on the launching stream).
+Main line (value): R-MAT scale 20 (1,048,576 x 1,048,576), edge factor 8,
+(a,b,c,d) = (.45,.15,.15,.25), float32 U[-1,1], C = A*A with learned sizing
+(the row-size network trained on the device on 200 seeded R-MAT matrices of
+scales 12-16, outside the timed region) and the planner parameters chosen by
+the autotuner; heavy rows take the global-memory hash. One step = the whole
+spgemm_learned call with A and B resident in HBM: per-row counts, the network
+and the bins, one hashing pass into a capacity-sized staging buffer, the
+exact fallback for rows that did not fit, C's row pointer, C's allocation and
+assembly. L2 (129 MB) is flushed between timed steps by writing a 256 MiB
+buffer outside the timed region. value = useful GFLOP/s = 2 * products / step
+time (CUDA events on the launching stream).
 
-Variants (same JSON line, "variants"): learned sizing on R-MAT scale 18
-(float32) against the plain path; 512 batched products in one persistent
-launch against 512 separate plain calls; R-MAT scale 20 (float32) with learned
-sizing and autotuned planner parameters, with its HBM roofline fraction.
+Variants (same JSON line, "variants", each timed over --variant-steps steps):
+the plain two-pass path and the one-pass path sized by the bound min(flop_i,
+cols) (the pipeline without the network) on the same workload; R-MAT scale 18
+(learned / bound / plain); 512 batched products in one persistent launch
+against 512 separate plain calls and against one plain call on their
+block-diagonal concatenation; R-MAT scale 16 float64 (plain); the paper-like
+product of two independent R-MAT scale-14 matrices (float64, plain).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl smash|reference]
-                       [--variants all|none]
+                       [--variants all|none] [--workload NAME] [--path learned|plain|bound]
 With torchrun (N > 1) every rank runs an independent replica (the rows of C
 are independent; no exchange step): value = all ranks' products / max time.
 """
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
 import glob
 import hashlib
 import json
@@ -39,12 +46,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SpGEMM useful GFLOP/s and HBM GB/s: learned/batched vs plain hash, same GB300"
 WORKLOADS = {
+    "rmat20_f32": "R-MAT scale 20 (1048576 x 1048576), edge factor 8, (a,b,c,d)=(0.45,0.15,0.15,0.25), "
+                  "float32 U[-1,1], C = A*A (A and B separate copies)",
     "rmat16_f64": "R-MAT scale 16 (65536 x 65536), edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), "
-                  "float64 values U[-1,1], C = A*A (A and B separate copies), plain two-pass hash",
+                  "float64 values U[-1,1], C = A*A (A and B separate copies)",
     "rmat10_int": "R-MAT scale 10, edge factor 8, (0.57,0.19,0.19,0.05), float32 integer values {1..4}, C = A*A",
     "rmat18_f32": "R-MAT scale 18, edge factor 16, (0.57,0.19,0.19,0.05), float32 U[-1,1], C = A*A",
-    "rmat20_f32": "R-MAT scale 20, edge factor 8, (0.45,0.15,0.15,0.25), float32 U[-1,1], C = A*A",
 }
+PATHS = {"learned": "learned sizing (row-size network) + autotuned planner",
+         "bound": "one pass sized by min(flop_i, cols) + autotuned planner",
+         "plain": "plain two-pass (symbolic, then numeric) + autotuned planner"}
 TRAIN_SEEDS = list(range(200))
 
 
@@ -174,42 +185,85 @@ def replica_gflops(world: int, products: int, seconds: float) -> float:
     return world * metrics.useful_gflops(products, seconds)
 
 
-def cpu_baseline(A, B, flop, budget_products: float, seed: int = 0):
-    """The oracle, as it stands, on a seeded random sample of rows."""
+def oracle_rows(A, B, rows, threads: int):
+    """The oracle, as it stands, on the given rows: in one call (threads = 1)
+    or in contiguous row chunks on `threads` host threads (its C calls release
+    the interpreter lock)."""
     import oracle
-    oracle.build()
+    if threads <= 1:
+        oracle.spgemm(A, B, rows=rows)
+        return
+    chunks = np.array_split(rows, 4 * threads)
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda c: oracle.spgemm(A, B, rows=c), [c for c in chunks if c.size]))
+
+
+def sample_rows(A, flop, budget_products: float, seed: int):
     rng = np.random.default_rng(seed)
     order = rng.permutation(A.rows)
     cum = np.cumsum(flop[order])
     k = int(np.searchsorted(cum, budget_products)) + 1
-    rows = np.sort(order[:min(k, A.rows)])
-    t0 = time.perf_counter()
-    oracle.spgemm(A, B, rows=rows)
-    dt = time.perf_counter() - t0
+    return np.sort(order[:min(k, A.rows)])
+
+
+def cpu_baseline(A, B, flop, budget_products: float, seed: int = 0):
+    """The oracle as it stands on a seeded random sample of rows, single-threaded
+    and on all host cores (the main figure)."""
+    import oracle
+    oracle.build()
+    rows = sample_rows(A, flop, budget_products, seed)
     prods = int(flop[rows].sum())
-    return {"value": 2.0 * prods / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": "%d of %d rows drawn at random (seed %d), %d of %d products, %.1f s single-threaded"
-                      % (rows.size, A.rows, seed, prods, int(flop.sum()), dt)}
+    cores = os.cpu_count() or 1
+    out = {}
+    for threads in (1, cores):
+        t0 = time.perf_counter()
+        oracle_rows(A, B, rows, threads)
+        dt = time.perf_counter() - t0
+        out[threads] = (2.0 * prods / dt / 1e9, dt)
+    cpu = "unknown"
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                cpu = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    sample = "%d of %d rows drawn at random (seed %d), %d of %d products" % (rows.size, A.rows, seed, prods,
+                                                                            int(flop.sum()))
+    return {"value": out[cores][0], "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": sample + ", %.1f s on %d threads" % (out[cores][1], cores),
+            "host_cpu": cpu,
+            "single_thread": {"value": out[1][0], "unit": "GFLOP/s", "cores": 1,
+                              "sample": sample + ", %.1f s on 1 thread" % out[1][1]}}
 
 
 def run_reference(args, A, B, flop, rank):
-    """Reference arm: the CPU oracle as it stands, on bounded samples of the workload."""
+    """Reference arm: the CPU oracle as it stands, on all host cores, on bounded
+    samples of the workload."""
     if rank != 0:
         return 0
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    per_step = float(os.environ.get("SMASH_REF_STEP_PRODUCTS", "1e8"))
     vals = []
-    per_step = float(os.environ.get("SMASH_REF_STEP_PRODUCTS", "2e7"))
     for k in range(args.warmup + args.steps):
-        cb = cpu_baseline(A, B, flop, per_step, seed=k)
+        rows = sample_rows(A, flop, per_step, seed=k)
+        prods = int(flop[rows].sum())
+        t0 = time.perf_counter()
+        oracle_rows(A, B, rows, cores)
+        dt = time.perf_counter() - t0
         if k >= args.warmup:
-            vals.append(cb["value"])
+            vals.append(2.0 * prods / dt / 1e9)
     value = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 2.0 * per_step / (value * 1e9) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if A.val.dtype == np.float64 else "f32", "data": "synthetic",
             "config": {"workload": args.workload, "description": WORKLOADS[args.workload]},
-            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-                             "sample": "each step: rows drawn at random until about %.0e products" % per_step},
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": "each step: rows drawn at random until about %.0e products, %d threads"
+                                       % (per_step, cores)},
             "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -244,23 +298,38 @@ def kernel_bytes(t, vb, nnz_b, total_products):
     return None
 
 
+def step_fn(h, path, dA, dB, model, stream, stats=None):
+    """One product on the chosen path; returns a callable for timed()."""
+    if path == "plain":
+        return lambda: h.spgemm(dA, dB, stream)
+
+    def f():
+        C, st, owner = h.spgemm_learned(dA, dB, model if path == "learned" else None, margin=0.15, stream=stream)
+        if stats is not None:
+            stats.update(st)
+        owner.free()
+    return f
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="smash", choices=["smash", "reference"])
-    ap.add_argument("--workload", default="rmat16_f64", choices=sorted(WORKLOADS))
-    ap.add_argument("--cpu-products", type=float, default=2e8)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--workload", default="rmat20_f32", choices=sorted(WORKLOADS))
+    ap.add_argument("--path", default="learned", choices=sorted(PATHS))
+    ap.add_argument("--cpu-products", type=float, default=1e8)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--variants", default="all", choices=["all", "none"])
-    ap.add_argument("--variant-steps", type=int, default=3)
+    ap.add_argument("--variant-steps", type=int, default=10)
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     args.e2e_steps = max(args.e2e_steps, 1)
 
     from paper_2105_14156_gb300 import metrics
-    from paper_2105_14156_gb300.rmat import batched_workload, workload
+    from paper_2105_14156_gb300.rmat import workload
 
     rank, world, local, dist = dist_setup()
     A = workload(args.workload)
@@ -275,8 +344,9 @@ def main():
         return rc
 
     do_var = args.variants == "all" and world == 1
-    train_mats = None
-    if do_var:
+    need_model = args.path == "learned" or do_var
+    train_mats, gen_train_s = None, 0.0
+    if need_model:
         # CPU work first: the spawn pool starts before the first CUDA call
         from paper_2105_14156_gb300 import learned
         t0 = time.perf_counter()
@@ -284,7 +354,7 @@ def main():
         gen_train_s = time.perf_counter() - t0
 
     import torch
-    from paper_2105_14156_gb300 import build, smash
+    from paper_2105_14156_gb300 import autotune, build, learned, smash
 
     build.build()
     torch.cuda.set_device(local)
@@ -296,14 +366,22 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step():
-        return h.spgemm(dA, dB, stream)
+    model, training = None, None
+    if need_model:
+        model, loss, train_s, nsamp = learned.train(h, train_mats, epochs=8, batch=4096)
+        training = {"matrices": len(train_mats), "samples": nsamp, "final_mse": loss, "device_train_s": train_s,
+                    "cpu_generation_s": gen_train_s, "epochs": 8, "batch": 4096}
+        del train_mats
+    tuned = None
+    if not args.no_autotune:
+        tuned, _ = autotune.tune(h, dA, dB, args.workload, cache_path=None)
 
+    stats = {}
+    step = step_fn(h, args.path, dA, dB, model, stream, stats)
     for _ in range(args.warmup):
         C = step()
+        del C
     h.check(stream)
-    c_nnz = C.nnz
-    del C
     vb = A.val.dtype.itemsize
 
     sampler = ClockSampler(local)
@@ -324,24 +402,28 @@ def main():
     sampler.stop()
     clocks = sampler.summary(t_wall0, t_wall1)
     h.check(stream)
+    if args.path == "plain":
+        c_nnz = h.stats().c_nnz
+    else:
+        c_nnz = stats["c_nnz"]
 
     ms = replica_max(sum(times) / len(times), dist, dev)
 
-    # dominant kernel: roofline from the live per-launch event timing
+    # dominant kernel: roofline from the live per-launch event timing (launch
+    # groups of one phase run side by side on four streams: a group's window
+    # counts from when its stream reaches it)
     peaks, peak_src = load_peaks()
     launches = int(sum(t["kernels"] for t in kt))
     dom = max((t for t in kt if kernel_bytes(t, vb, B.nnz, products) is not None), key=lambda t: t["ms"])
     per_launch_ms = dom["ms"] / dom["launches"]
     per_launch_bytes = kernel_bytes(dom, vb, B.nnz, products) / dom["launches"]
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
-    traffic = recorded_traffic(dom["name"], args.workload)
+    traffic = recorded_traffic(dom["name"] + "_b%d" % dom["bin"], args.workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "kernel": "%s (bin %d)" % (dom["name"], dom["bin"]),
                 "share_of_step": dom["ms"] / args.steps / ms,
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src}
-    # the dominant kernels merge one product per shared-memory atomic add: the
-    # measured atomic rate is their compute ceiling
     apeak = smem_atomic_peak(vb)
     if apeak:
         arate = dom["products"] / (dom["ms"] / 1e3) / 1e9
@@ -360,7 +442,12 @@ def main():
         t0 = time.perf_counter()
         dAe = smash.DeviceCsr(A.rows, A.cols, *[t.to(dev, non_blocking=True) for t in pinned["A"]])
         dBe = smash.DeviceCsr(B.rows, B.cols, *[t.to(dev, non_blocking=True) for t in pinned["B"]])
-        Ce = h.spgemm(dAe, dBe, stream)
+        owner = None
+        if args.path == "plain":
+            Ce = h.spgemm(dAe, dBe, stream)
+        else:
+            Ce, _, owner = h.spgemm_learned(dAe, dBe, model if args.path == "learned" else None, margin=0.15,
+                                            stream=stream)
         if out_host is None or out_host[1].numel() != Ce.nnz:
             out_host = [torch.empty(Ce.rows + 1, dtype=torch.int64).pin_memory(),
                         torch.empty(Ce.nnz, dtype=torch.int32).pin_memory(),
@@ -373,7 +460,10 @@ def main():
         d2h = sum(t.numel() * t.element_size() for t in out_host)
         if k > 0:
             e2e_times.append(dt)
-        del dAe, dBe, Ce
+        del Ce
+        if owner is not None:
+            owner.free()
+        del dAe, dBe
     e2e_s = replica_max(statistics.median(e2e_times), dist, dev)
     del out_host, pinned
 
@@ -384,28 +474,34 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if vb == 8 else "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "products": products,
-                   "nnz_a": A.nnz, "nnz_c": c_nnz,
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "path": PATHS[args.path],
+                   "products": products, "nnz_a": A.nnz, "nnz_c": c_nnz,
                    "l2": "flushed between timed steps (256 MiB write outside the timed region)",
-                   "parallelism": "replicas" if world > 1 else "single"},
-        "hbm_gbs": achieved_step,
+                   "parallelism": "replicas" if world > 1 else "single", "autotuned": tuned},
+        "hbm_gbs_per_gpu": achieved_step,
         "step_roofline": {"bound": "hbm", "achieved": achieved_step, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                          "frac": achieved_step / peaks["hbm_gbs"],
-                          "note": "bytes(A)+bytes(B)+bytes(C) per step over the step time"},
+                          "frac": achieved_step / peaks["hbm_gbs"], "per_gpu": True,
+                          "note": "bytes(A)+bytes(B)+bytes(C) per step over the step time, one GPU"},
         "roofline": roofline,
         "kernels": [{k: t[k] for k in ("name", "bin", "launches", "rows", "products", "ms")} for t in
-                    sorted(kt, key=lambda t: -t["ms"])[:8]],
+                    sorted(kt, key=lambda t: -t["ms"])[:10]],
         "e2e": {"value": replica_gflops(world, products, e2e_s), "unit": "GFLOP/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clocks,
         "gpu_launches": launches,
     }
+    if args.path != "plain":
+        line["learned_stats"] = {k: stats.get(k) for k in ("rows", "overflow_rows", "staged_nnz", "c_nnz")}
+    if training:
+        line["training"] = training
 
     if do_var:
-        line["variants"] = run_variants(h, dev, flush, stream, args, train_mats, gen_train_s, peaks)
+        line["variants"] = run_variants(h, dev, flush, stream, args, model, peaks, dA, dB, products, ms)
 
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(A, B, flop, args.cpu_products)
+    if model is not None:
+        model.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -414,53 +510,58 @@ def main():
     return 0
 
 
-def run_variants(h, dev, flush, stream, args, train_mats, gen_train_s, peaks):
+def run_variants(h, dev, flush, stream, args, model, peaks, dA, dB, products, main_ms):
     import torch
-    from paper_2105_14156_gb300 import autotune, learned, metrics, smash
-    from paper_2105_14156_gb300.rmat import batched_workload, workload
-    K = max(1, args.variant_steps)
+    from paper_2105_14156_gb300 import autotune, metrics, smash
+    from paper_2105_14156_gb300.rmat import batched_workload, block_diagonal, paper_like_pair, workload
+    K = max(10, args.variant_steps)
     out = {}
 
     def gf(prods, ms_):
         return metrics.useful_gflops(prods, ms_ / 1e3)
 
-    # learned sizing: R-MAT scale 18, float32
-    t0 = time.perf_counter()
-    model, loss, train_s, nsamp = learned.train(h, train_mats, epochs=8, batch=4096)
+    def median_ms(fn, steps=K):
+        fn()
+        return statistics.median(timed(fn, steps, flush, stream))
+
+    # the other paths on the main workload, same tuned parameters
+    vb = dA.val.element_size()
+    for path in ("plain", "bound", "learned"):
+        if path == args.path:
+            continue
+        st = {}
+        t = median_ms(step_fn(h, path, dA, dB, model, stream, st))
+        out["main_" + path] = {"ms": t, "gflops": gf(products, t), "main_over_this": t / main_ms,
+                               "overflow_rows": st.get("overflow_rows"), "staged_nnz": st.get("staged_nnz")}
+
+    # R-MAT scale 18, float32: learned / bound / plain (default parameters)
+    saved = h.params.as_dict()
+    h.set_params(**smash.default_params().as_dict())
     A18 = workload("rmat18_f32")
     p18 = int(row_products(A18, A18).sum())
     d18a, d18b = smash.to_device(A18, dev), smash.to_device(A18, dev)
-    plain = lambda: h.spgemm(d18a, d18b, stream)
-    plain()
-    t_plain = statistics.median(timed(plain, K, flush, stream))
-    stats = {}
-
-    def lstep():
-        C, st, owner = h.spgemm_learned(d18a, d18b, model, margin=0.15, stream=stream)
-        stats.update(st)
-        owner.free()
-
-    lstep()
-    t_learn = statistics.median(timed(lstep, K, flush, stream))
-    out["learned_rmat18_f32"] = {
-        "products": p18, "c_nnz": stats.get("c_nnz"),
-        "plain_ms": t_plain, "learned_ms": t_learn,
-        "plain_gflops": gf(p18, t_plain), "learned_gflops": gf(p18, t_learn),
-        "speedup_vs_plain": t_plain / t_learn,
-        "overflow_rows": stats.get("overflow_rows"), "rows": stats.get("rows"),
-        "staged_over_cnnz": (stats["staged_nnz"] / stats["c_nnz"]) if stats.get("c_nnz") else None,
-        "training": {"matrices": len(train_mats), "samples": nsamp, "final_mse": loss, "device_train_s": train_s,
-                     "cpu_generation_s": gen_train_s, "epochs": 8, "batch": 4096},
-    }
+    res18 = {}
+    for path in ("plain", "bound", "learned"):
+        st = {}
+        t = median_ms(step_fn(h, path, d18a, d18b, model, stream, st))
+        res18[path] = {"ms": t, "gflops": gf(p18, t), "overflow_rows": st.get("overflow_rows"),
+                       "staged_over_cnnz": (st["staged_nnz"] / st["c_nnz"]) if st.get("c_nnz") else None}
+    res18["products"] = p18
+    res18["learned_over_plain"] = res18["plain"]["ms"] / res18["learned"]["ms"]
+    res18["learned_over_bound"] = res18["bound"]["ms"] / res18["learned"]["ms"]
+    out["rmat18_f32"] = res18
     del d18a, d18b, A18
     torch.cuda.empty_cache()
 
-    # batched: 512 products in one persistent launch vs 512 separate plain calls
+    # batched: 512 products in one persistent launch; 512 separate plain calls;
+    # one plain call on the block-diagonal concatenation (the same products,
+    # no per-call host round trips)
     pairs = batched_workload(512, seed=7)
     dev_pairs = [(smash.to_device(a, dev), smash.to_device(b, dev)) for a, b in pairs]
     pb = int(sum(row_products(a, b).sum() for a, b in pairs))
-    binp = smash.BatchedInputs(dev_pairs)   # descriptors built once, like a user's repeated calls
+    binp = smash.BatchedInputs(dev_pairs)
     bits, _ = h.batched_autotune(binp, stream)
+    cut = h.batched_row_cutoffs()
     bstats = {}
 
     def bstep():
@@ -468,50 +569,50 @@ def run_variants(h, dev, flush, stream, args, train_mats, gen_train_s, peaks):
         bstats.update(st)
         owner.free()
 
-    bstep()
-    t_batch = statistics.median(timed(bstep, K, flush, stream))
+    t_batch = median_ms(bstep)
 
     def sstep():
         for a, b in dev_pairs:
             h.spgemm(a, b, stream)
 
-    sstep()
-    t_sep = statistics.median(timed(sstep, max(1, K - 1), flush, stream))
+    t_sep = median_ms(sstep, max(3, K // 3))
+    Abd, Bbd = block_diagonal(pairs)
+    dAbd, dBbd = smash.to_device(Abd, dev), smash.to_device(Bbd, dev)
+    t_bd = median_ms(lambda: h.spgemm(dAbd, dBbd, stream))
     out["batched_512"] = {"products_flop": pb, "c_nnz": bstats.get("c_nnz"), "batched_ms": t_batch,
-                          "separate_ms": t_sep, "batched_gflops": gf(pb, t_batch),
-                          "separate_gflops": gf(pb, t_sep), "speedup_vs_separate": t_sep / t_batch,
-                          "table_bits": bits, "big_rows": bstats.get("big_rows"),
-                          "huge_rows": bstats.get("huge_rows")}
-    del dev_pairs, pairs
+                          "separate_ms": t_sep, "block_diagonal_ms": t_bd,
+                          "batched_gflops": gf(pb, t_batch), "separate_gflops": gf(pb, t_sep),
+                          "block_diagonal_gflops": gf(pb, t_bd),
+                          "speedup_vs_separate": t_sep / t_batch, "speedup_vs_block_diagonal": t_bd / t_batch,
+                          "table_bits": bits, "row_cutoffs": {"warp_less": cut[0], "block_more": cut[1]},
+                          "big_rows": bstats.get("big_rows"), "huge_rows": bstats.get("huge_rows")}
+    del dev_pairs, pairs, binp, dAbd, dBbd
+    torch.cuda.empty_cache()
 
-    # R-MAT scale 20, float32: learned sizing + autotuned planner
-    A20 = workload("rmat20_f32")
-    p20 = int(row_products(A20, A20).sum())
-    d20a, d20b = smash.to_device(A20, dev), smash.to_device(A20, dev)
-    saved = h.params.as_dict()
-    tuned, _ = autotune.tune(h, d20a, d20b, "rmat20_f32", cache_path=None)
-    plain20 = lambda: h.spgemm(d20a, d20b, stream)
-    plain20()
-    t_p20 = statistics.median(timed(plain20, K, flush, stream))
-    st20 = {}
+    # R-MAT scale 16, float64, plain two-pass (default parameters)
+    A16 = workload("rmat16_f64")
+    p16 = int(row_products(A16, A16).sum())
+    d16a, d16b = smash.to_device(A16, dev), smash.to_device(A16, dev)
+    t16 = median_ms(lambda: h.spgemm(d16a, d16b, stream))
+    c16 = h.stats().c_nnz
+    b16 = metrics.spgemm_bytes(A16.rows, A16.nnz, A16.rows, A16.nnz, A16.rows, c16, 8)
+    out["rmat16_f64"] = {"products": p16, "c_nnz": c16, "plain_ms": t16, "plain_gflops": gf(p16, t16),
+                         "hbm_roofline_frac": b16 / (t16 / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    del d16a, d16b, A16
 
-    def l20():
-        C, st, owner = h.spgemm_learned(d20a, d20b, model, margin=0.15, stream=stream)
-        st20.update(st)
-        owner.free()
-
-    l20()
-    t_l20 = statistics.median(timed(l20, K, flush, stream))
-    bytes20 = metrics.spgemm_bytes(A20.rows, A20.nnz, A20.rows, A20.nnz, A20.rows, st20["c_nnz"], 4)
-    best = min(t_p20, t_l20)
-    out["rmat20_f32"] = {"products": p20, "c_nnz": st20["c_nnz"], "plain_autotuned_ms": t_p20, "learned_ms": t_l20,
-                         "plain_gflops": gf(p20, t_p20), "learned_gflops": gf(p20, t_l20),
-                         "hbm_roofline_frac": bytes20 / (best / 1e3) / 1e9 / peaks["hbm_gbs"],
-                         "bytes_a_b_c": bytes20, "autotuned_params": tuned,
-                         "overflow_rows": st20.get("overflow_rows")}
+    # the paper-like product: two independent R-MAT scale-14 matrices, float64
+    Ap, Bp = paper_like_pair()
+    pp = int(row_products(Ap, Bp).sum())
+    dap, dbp = smash.to_device(Ap, dev), smash.to_device(Bp, dev)
+    tp = median_ms(lambda: h.spgemm(dap, dbp, stream))
+    cp_ = h.stats().c_nnz
+    out["paper_like_ab_f64"] = {
+        "workload": "two independent R-MAT scale 14, edge factor 16, (.45,.15,.15,.25), float64, C = A*B, plain",
+        "nnz_a": Ap.nnz, "nnz_b": Bp.nnz, "products": pp, "c_nnz": cp_, "cf": pp / cp_ if cp_ else None,
+        "plain_ms": tp, "plain_gflops": gf(pp, tp),
+        "paper_context": "105.4 ms for the paper's 16K x 16K R-MAT pair (Version 3, simulated PIUMA block; "
+                         "other hardware and matrices: context only)"}
     h.set_params(**saved)
-    del d20a, d20b
-    model.close()
     return out
 
 

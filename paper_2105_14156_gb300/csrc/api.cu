@@ -358,7 +358,7 @@ int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const
     if ((st = last_cuda_status())) return st;
     BinPlan bp;
     if ((st = fetch_bins(h, pl, s, bp.counts, bp.offsets, bp.maxsize, bp.stats, bp.sums))) return st;
-    return run_bins(h, op, n, dt, out, pl, bp, s, nullptr);
+    return run_bins(h, op, n, dt, out, pl, bp, s, nullptr, nullptr);
 }
 
 bool dense_windows(const smash_handle *h, const RawOperands &op, int dt, long long products, int &cpc, int &nw) {
@@ -402,7 +402,7 @@ int window_plan(smash_handle *h, const RawOperands &op, int dt, int cpc, int nw,
 }
 
 int run_bins(smash_handle *h, const RawOperands &op, int64_t n, int dt, const NumOut &out, Plan &pl,
-             const BinPlan &bp, cudaStream_t s, const WinArena *arena) {
+             const BinPlan &bp, cudaStream_t s, const WinArena *arena, const RowGather *cap_rec) {
     int st;
     const BinRule rule = num_rule(h, op.ncols, dt);
     int *err = (int *)h->err.ptr;
@@ -412,7 +412,9 @@ int run_bins(smash_handle *h, const RawOperands &op, int64_t n, int dt, const Nu
     const long long *sums = bp.sums;
     const size_t vsz = dt ? 8 : 4;
     // the rows' product counts kept by the symbolic phase of these operands
-    const RowGather *kept = (!out.row_nnz && rcache_matches(h, op)) ? (const RowGather *)h->rcache.ptr : nullptr;
+    // (capacity mode: the counts of the learned planning)
+    const RowGather *kept =
+        out.row_nnz ? cap_rec : (rcache_matches(h, op) ? (const RowGather *)h->rcache.ptr : nullptr);
     // Dense rows take column windows when their products pay for slicing B
     // (a pass over B's rows and entries); otherwise the global hash. Their
     // counts and the slices of B are prepared on s before the bins fork.

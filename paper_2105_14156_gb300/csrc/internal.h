@@ -625,8 +625,9 @@ struct BinPlan {
     int counts[16], offsets[17];
     long long maxsize[16], stats[4], sums[48];
 };
+// cap_rec (capacity mode): the rows' counts from the learned planning.
 int run_bins(smash_handle *h, const RawOperands &op, int64_t n, int dt, const NumOut &out, Plan &pl,
-             const BinPlan &bp, cudaStream_t s, const WinArena *arena);
+             const BinPlan &bp, cudaStream_t s, const WinArena *arena, const RowGather *cap_rec = nullptr);
 // Whether the dense bin (with `products` products) takes column windows, and
 // their width and number.
 bool dense_windows(const smash_handle *h, const RawOperands &op, int dt, long long products, int &cpc, int &nw);

@@ -224,10 +224,14 @@ __host__ __device__ constexpr size_t warp_row_bytes(int T, int L, int NB) {
 }
 
 // K: entries held per lane in the write-out (the list room L <= 32 K).
-// rec (may be null): the rows' product counts kept by the symbolic phase. A
-// row whose exact length equals its product count has no repeated column:
-// nothing to merge, so its products skip the table and go straight to the
-// write-out's staging (keys[p], vals[p] for product p).
+// rec (may be null): the rows' product counts (kept by the symbolic phase, or
+// gathered by the learned planning). In exact mode a row whose length equals
+// its product count has no repeated column: nothing to merge, so its products
+// skip the table and go straight to the write-out's staging (keys[p], vals[p]
+// for product p). In capacity mode a row whose products fit its capacity is
+// staged the same way and its equal columns are summed after the sort
+// (expand, sort, merge): cheaper than hashing when few columns repeat, which
+// is what such a capacity says.
 template <typename V, typename IT, int K, int NW>
 __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int *rows, int count, int *token,
                                                       int tbits, HashCfg hc, int lcap, int nb, int bsh,
@@ -261,8 +265,14 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
         int64_t ab = 0, ae = 0;
         if (ok) a_row_range(op, i, ab, ae, err);
         int cnt = 0, full = 0;
-        const bool direct = rec && !out.row_nnz && ok && n_exp <= lcap && rec[i].f == (long long)n_exp;
-        if (direct) {
+        // direct: exact mode, the row's length equals its product count (no
+        // repeated column). merge: capacity mode, the row's products fit its
+        // capacity (the size model sees few repeated columns); its products
+        // are staged as they are and equal columns summed after the sort.
+        const long long f_i = rec && ok ? rec[i].f : -1;
+        const bool direct = !out.row_nnz && f_i >= 0 && n_exp <= lcap && f_i == (long long)n_exp;
+        const bool merge = out.row_nnz && f_i >= 0 && f_i <= (long long)n_exp && f_i <= lcap && 2 * f_i <= T;
+        if (direct || merge) {
             warp_enum<V, IT, true>(op, ab, ae, es, err, [&](bool act, int j, V a, V b, int p) {
                 if (act && p < lcap) {
                     keys[p] = j;
@@ -292,7 +302,8 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
         bool over;
         if (out.row_nnz) {
             over = full || tot > n_exp || tot > lcap;
-            if (lane == 0) out.row_nnz[i] = over ? -1 : tot;
+            // (a merged row's length is known after the merge)
+            if (lane == 0 && (over || !merge)) out.row_nnz[i] = over ? -1 : tot;
         } else {
             over = full || tot != n_exp || tot > lcap;
             if (lane == 0) {
@@ -303,7 +314,7 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
         __syncwarp();
         if (over) {
             // nothing is written; the table goes back to EMPTY / 0
-            if (full || tot > lcap || direct) {
+            if (full || tot > lcap || direct || merge) {
                 for (int s = lane; s < T; s += 32) {
                     keys[s] = kEmpty;
                     vals[s] = V(0);
@@ -314,6 +325,104 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
                     keys[h] = kEmpty;
                     vals[h] = V(0);
                 }
+            }
+        } else if (merge) {
+            // expanded products, sorted by column, equal columns summed
+            // 1. the products into registers, their staging back to EMPTY / 0,
+            //    counts per bucket
+            int kk[K], pp[K];
+            V vv[K];
+#pragma unroll
+            for (int x = 0; x < K; ++x) {
+                const int q = lane + 32 * x;
+                kk[x] = INT_MAX;
+                vv[x] = V(0);
+                pp[x] = -1;
+                if (q < tot) {
+                    kk[x] = keys[q];
+                    vv[x] = vals[q];
+                    keys[q] = kEmpty;
+                    vals[q] = V(0);
+                    atomicAdd(bc + (kk[x] >> bsh), 1);
+                }
+            }
+            __syncwarp();
+            {
+                const int run = (NB + 31) >> 5;
+                const int b0 = min(lane * run, NB), b1 = min(b0 + run, NB);
+                int loc = 0;
+                for (int b = b0; b < b1; ++b) loc += bc[b];
+                int acc = warp_incl_scan(loc) - loc;
+                for (int b = b0; b < b1; ++b) {
+                    const int c = bc[b];
+                    bc[b] = acc;
+                    acc += c;
+                }
+            }
+            __syncwarp();
+            // 2. grouped by bucket into keys[0..tot)
+#pragma unroll
+            for (int x = 0; x < K; ++x) {
+                if (lane + 32 * x < tot) {
+                    pp[x] = atomicAdd(bc + (kk[x] >> bsh), 1);
+                    keys[pp[x]] = kk[x];
+                }
+            }
+            __syncwarp();
+            // 3. place of each product in the sorted sequence: its bucket's
+            //    start plus the smaller columns of the bucket, equal columns
+            //    ordered by their grouped position
+#pragma unroll
+            for (int x = 0; x < K; ++x) {
+                if (lane + 32 * x < tot) {
+                    const int b = kk[x] >> bsh;
+                    const int e = bc[b];
+                    const int s0 = b ? bc[b - 1] : 0;
+                    int rk = 0;
+                    for (int y = s0; y < e; ++y) {
+                        const int ky = keys[y];
+                        rk += (ky < kk[x] || (ky == kk[x] && y < pp[x])) ? 1 : 0;
+                    }
+                    pp[x] = s0 + rk;
+                }
+            }
+            __syncwarp();
+            // 4. the sorted sequence in keys[tot..2 tot), vals[tot..2 tot)
+#pragma unroll
+            for (int x = 0; x < K; ++x) {
+                if (lane + 32 * x < tot) {
+                    keys[tot + pp[x]] = kk[x];
+                    vals[tot + pp[x]] = vv[x];
+                }
+            }
+            __syncwarp();
+            // 5. the first of each run of equal columns sums the run and takes
+            //    the next place of the row
+            int run_tot = 0;
+#pragma unroll
+            for (int x = 0; x < K; ++x) {
+                const int q = lane + 32 * x;
+                bool first = false;
+                int sk = 0;
+                if (q < tot) {
+                    sk = keys[tot + q];
+                    first = q == 0 || keys[tot + q - 1] != sk;
+                }
+                const unsigned m = __ballot_sync(kFull, first);
+                if (first) {
+                    V v = vals[tot + q];
+                    for (int y = q + 1; y < tot && keys[tot + y] == sk; ++y) v += vals[tot + y];
+                    const int d = run_tot + __popc(m & lanemask_lt());
+                    out.c_ci[c0 + d] = sk;
+                    out.c_val[c0 + d] = v;
+                }
+                run_tot += __popc(m);
+            }
+            if (lane == 0) out.row_nnz[i] = run_tot;
+            __syncwarp();
+            for (int q = lane; q < 2 * tot; q += 32) {
+                keys[q] = kEmpty;
+                vals[q] = V(0);
             }
         } else if (tot <= 32) {
             // rank of each entry among the row's (at most 32) columns
@@ -451,7 +560,7 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
         }
         // bucket counts back to zero (the insertion left them untouched when
         // the row took no bucket write-out)
-        if (!over && tot > 32)
+        if (!over && (tot > 32 || merge))
             for (int s = lane; s < NB; s += 32) bc[s] = 0;
         __syncwarp();
     }

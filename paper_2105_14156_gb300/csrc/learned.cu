@@ -543,7 +543,7 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
     so.c_val = stage_val;
     so.c_nnz = staged;
     so.row_nnz = row_nnz;
-    if ((st = run_bins(h, op, n, dt, so, pl, bp, s, use_arena ? &ar : nullptr))) return st;
+    if ((st = run_bins(h, op, n, dt, so, pl, bp, s, use_arena ? &ar : nullptr, gather))) return st;
     // 4. rows that did not fit
     {
         LaunchTimer lt(h, s, "overflow_list", -1, 256, n, 0, 0, 0);

@@ -192,6 +192,35 @@ def batched_workload(count: int = 512, seed: int = 7, **kw):
     return [batched_pair(seed, i, **kw) for i in range(count)]
 
 
+def block_diagonal(pairs):
+    """(diag(A_1, ..., A_m), diag(B_1, ..., B_m)): the products of a batch laid
+    out as one product whose rows and columns are the batch's, block by block."""
+    def diag(mats):
+        rows = sum(M.rows for M in mats)
+        cols = sum(M.cols for M in mats)
+        rp = np.zeros(rows + 1, dtype=np.int64)
+        ci, val = [], []
+        r0 = c0 = e0 = 0
+        for M in mats:
+            rp[r0 + 1:r0 + M.rows + 1] = M.row_ptr[1:] + e0
+            ci.append(M.col_idx.astype(np.int64) + c0)
+            val.append(M.val)
+            r0 += M.rows
+            c0 += M.cols
+            e0 += M.nnz
+        return Csr(rows, cols, rp, np.concatenate(ci).astype(np.int32), np.concatenate(val))
+    return diag([a for a, _ in pairs]), diag([b for _, b in pairs])
+
+
+def paper_like_pair():
+    """Two independently drawn R-MAT matrices of scale 14 (16K x 16K), edge
+    factor 16, (a,b,c,d) = (.45,.15,.15,.25), float64 values: the closest seeded
+    stand-in for the pair of 16K x 16K R-MAT matrices multiplied in the paper's
+    evaluation (whose R-MAT parameters are not given)."""
+    abcd = (0.45, 0.15, 0.15, 0.25)
+    return rmat(14, 16, abcd, seed=1, values="f64"), rmat(14, 16, abcd, seed=2, values="f64")
+
+
 def training_matrix(seed: int, edge_factor: int = 16) -> Csr:
     """Training set member ``seed``: R-MAT scale 12 + (seed mod 5), float32 U[-1,1]."""
     return rmat(12 + (seed % 5), edge_factor, GRAPH500_ABCD, seed=10_000 + seed, values="f32")
@@ -207,4 +236,6 @@ def workload(name: str):
         return rmat(18, 16, GRAPH500_ABCD, seed=1, values="f32")
     if name == "rmat20_f32":
         return rmat(20, 8, (0.45, 0.15, 0.15, 0.25), seed=1, values="f32")
+    if name == "rmat14_pair_f64":
+        return paper_like_pair()
     raise KeyError(name)
