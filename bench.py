@@ -298,17 +298,30 @@ def kernel_bytes(t, vb, nnz_b, total_products):
     return None
 
 
-def step_fn(h, path, dA, dB, model, stream, stats=None):
+def step_fn(h, path, dA, dB, model, stream, stats=None, margin=0.15):
     """One product on the chosen path; returns a callable for timed()."""
     if path == "plain":
         return lambda: h.spgemm(dA, dB, stream)
 
     def f():
-        C, st, owner = h.spgemm_learned(dA, dB, model if path == "learned" else None, margin=0.15, stream=stream)
+        C, st, owner = h.spgemm_learned(dA, dB, model if path == "learned" else None, margin=margin, stream=stream)
         if stats is not None:
             stats.update(st)
         owner.free()
     return f
+
+
+def tune_margin(h, dA, dB, model, stream, flush, candidates=(0.05, 0.15, 0.3, 0.6)):
+    """The learned path's capacity margin with the shortest product (median of
+    3 timed runs each), the learned-sizing counterpart of the planner's tuner."""
+    best, best_ms = 0.15, float("inf")
+    for m in candidates:
+        f = step_fn(h, "learned", dA, dB, model, stream, margin=m)
+        f()
+        t = statistics.median(timed(f, 3, flush, stream))
+        if t < best_ms:
+            best, best_ms = m, t
+    return best
 
 
 def main():
@@ -373,11 +386,15 @@ def main():
                     "cpu_generation_s": gen_train_s, "epochs": 8, "batch": 4096}
         del train_mats
     tuned = None
+    margin = 0.15
     if not args.no_autotune:
         tuned, _ = autotune.tune(h, dA, dB, args.workload, cache_path=None)
+        if args.path == "learned":
+            margin = tune_margin(h, dA, dB, model, stream, flush)
+            tuned = dict(tuned, margin=margin)
 
     stats = {}
-    step = step_fn(h, args.path, dA, dB, model, stream, stats)
+    step = step_fn(h, args.path, dA, dB, model, stream, stats, margin)
     for _ in range(args.warmup):
         C = step()
         del C
@@ -446,7 +463,7 @@ def main():
         if args.path == "plain":
             Ce = h.spgemm(dAe, dBe, stream)
         else:
-            Ce, _, owner = h.spgemm_learned(dAe, dBe, model if args.path == "learned" else None, margin=0.15,
+            Ce, _, owner = h.spgemm_learned(dAe, dBe, model if args.path == "learned" else None, margin=margin,
                                             stream=stream)
         if out_host is None or out_host[1].numel() != Ce.nnz:
             out_host = [torch.empty(Ce.rows + 1, dtype=torch.int64).pin_memory(),
@@ -496,7 +513,7 @@ def main():
         line["training"] = training
 
     if do_var:
-        line["variants"] = run_variants(h, dev, flush, stream, args, model, peaks, dA, dB, products, ms)
+        line["variants"] = run_variants(h, dev, flush, stream, args, model, peaks, dA, dB, products, ms, margin)
 
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(A, B, flop, args.cpu_products)
@@ -510,7 +527,7 @@ def main():
     return 0
 
 
-def run_variants(h, dev, flush, stream, args, model, peaks, dA, dB, products, main_ms):
+def run_variants(h, dev, flush, stream, args, model, peaks, dA, dB, products, main_ms, margin):
     import torch
     from paper_2105_14156_gb300 import autotune, metrics, smash
     from paper_2105_14156_gb300.rmat import batched_workload, block_diagonal, paper_like_pair, workload
@@ -530,7 +547,7 @@ def run_variants(h, dev, flush, stream, args, model, peaks, dA, dB, products, ma
         if path == args.path:
             continue
         st = {}
-        t = median_ms(step_fn(h, path, dA, dB, model, stream, st))
+        t = median_ms(step_fn(h, path, dA, dB, model, stream, st, margin))
         out["main_" + path] = {"ms": t, "gflops": gf(products, t), "main_over_this": t / main_ms,
                                "overflow_rows": st.get("overflow_rows"), "staged_nnz": st.get("staged_nnz")}
 

@@ -42,7 +42,8 @@ struct BatchArgs {
     int *nnz;               // [nrows]
     int *big;               // [nrows] list of big rows
     int *huge;              // [nrows] list of huge rows
-    int *counters;          // [8]: 0 nbig, 1 nhuge, 2..4 item tokens, 5 matrix token, 6..7 barrier
+    int *counters;          // [12]: 0 nbig, 1 nhuge, 2..4 item tokens, 5 matrix token, 6..7 barrier,
+                            // 8..9 row-chunk tokens of the two row phases
     unsigned long long *sums;   // [4]: sum ub, sum flop
     int64_t *rp_pool;       // row pointers: product m at row_start[m] + m
     int32_t *ci_pool;
@@ -57,6 +58,12 @@ struct BatchArgs {
     int dense_max;          // per-warp dense accumulator when cols <= dense_max
     HashCfg hc;             // colbits filled per product
     float inv_load;
+    // dense-accumulator rows in one pass: the first phase computes their values
+    // and stages each sorted row at stage_off[g] (room: min(flop, cols)); the
+    // last phase copies it to its exact place (null: two passes, as the rest)
+    const int64_t *stage_off;
+    int32_t *stage_ci;
+    void *stage_val;
     long long wait_spins;   // a grid barrier gives up after this many polls (~256 ns each)
     int missing;            // test hook: arrivals a barrier waits for beyond the grid (0: none)
 };

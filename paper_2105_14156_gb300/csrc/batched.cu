@@ -57,7 +57,7 @@ int run_batched_graph(BatchState &b, int dt, const BatchArgs *p_host, BatchArgs 
         if (!b.cs && cudaStreamCreateWithFlags(&b.cs, cudaStreamNonBlocking) != cudaSuccess) ok = false;
         if (ok && cudaStreamBeginCapture(b.cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) ok = false;
         if (ok) {
-            const bool m = cudaMemsetAsync(p_host->counters + 2, 0, sizeof(int) * 6, b.cs) == cudaSuccess;
+            const bool m = cudaMemsetAsync(p_host->counters + 2, 0, sizeof(int) * 10, b.cs) == cudaSuccess;
             const int e = launch_batched(dt, p_dev, p_host->tw_bits, grid, b.cs);
             const bool endok = cudaStreamEndCapture(b.cs, &b.graph) == cudaSuccess;
             ok = m && e == 0 && endok && b.graph;
@@ -74,7 +74,7 @@ int run_batched_graph(BatchState &b, int dt, const BatchArgs *p_host, BatchArgs 
     if (ok) return SMASH_OK;
     cudaGetLastError();
     drop_graph(b);
-    if (cudaMemsetAsync(p_host->counters + 2, 0, sizeof(int) * 6, s) != cudaSuccess) return SMASH_ERR_CUDA;
+    if (cudaMemsetAsync(p_host->counters + 2, 0, sizeof(int) * 10, s) != cudaSuccess) return SMASH_ERR_CUDA;
     if (launch_batched(dt, p_dev, p_host->tw_bits, grid, s) != 0) {
         cudaGetLastError();
         return SMASH_ERR_CUDA;
@@ -199,7 +199,7 @@ int spgemm_batched(smash_handle *h, int count, const smash_csr *A, const smash_c
     carve_size<int>(need, nrows);
     carve_size<int>(need, nrows);
     carve_size<int>(need, nrows);
-    carve_size<int>(need, 8);
+    carve_size<int>(need, 12);
     carve_size<unsigned long long>(need, 4);
     carve_size<int64_t>(need, count + 1);
     carve_size<int64_t>(need, count);
@@ -215,7 +215,7 @@ int spgemm_batched(smash_handle *h, int count, const smash_csr *A, const smash_c
     L.nnz = c.take<int>(nrows);
     L.big = c.take<int>(nrows);
     L.huge = c.take<int>(nrows);
-    L.counters = c.take<int>(8);
+    L.counters = c.take<int>(12);
     L.sums = c.take<unsigned long long>(4);
     L.base = c.take<int64_t>(count + 1);
     L.totals = c.take<int64_t>(count);
@@ -254,7 +254,7 @@ int spgemm_batched(smash_handle *h, int count, const smash_csr *A, const smash_c
     if (cudaMemcpyAsync(L.mats, hm, sizeof(BatchMat) * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(L.row_start, hrs, sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(L.tile_start, hts, sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(L.counters, 0, sizeof(int) * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(L.counters, 0, sizeof(int) * 12, s) != cudaSuccess ||
         cudaMemsetAsync(L.sums, 0, sizeof(unsigned long long) * 4, s) != cudaSuccess)
         return SMASH_ERR_CUDA;
     BatchArgs p;
@@ -316,6 +316,33 @@ int spgemm_batched(smash_handle *h, int count, const smash_csr *A, const smash_c
     p.rp_pool = rp_pool;
     p.ci_pool = ci_pool;
     p.val_pool = val_pool;
+    // staging of the one-pass (dense-accumulator) rows: room min(flop, cols)
+    // per row at the exclusive prefix of those rooms
+    p.stage_off = nullptr;
+    p.stage_ci = nullptr;
+    p.stage_val = nullptr;
+    {
+        size_t need = 0;
+        carve_size<int64_t>(need, (size_t)nrows + 1);
+        carve_size<long long>(need, 1);
+        carve_size<char>(need, scan_scratch_bytes(nrows));
+        carve_size<int32_t>(need, (size_t)(sum_ub > 0 ? sum_ub : 1));
+        carve_size<char>(need, vsz * (size_t)(sum_ub > 0 ? sum_ub : 1));
+        if ((st = ensure(h, h->stage, need, s))) {
+            h->free_fn(rp_pool, h->ctx);
+            h->free_fn(ci_pool, h->ctx);
+            h->free_fn(val_pool, h->ctx);
+            return st;
+        }
+        Carver sc(h->stage.ptr);
+        int64_t *so = sc.take<int64_t>((size_t)nrows + 1);
+        long long *tot = sc.take<long long>(1);
+        void *scr = sc.take<char>(scan_scratch_bytes(nrows));
+        p.stage_ci = sc.take<int32_t>((size_t)(sum_ub > 0 ? sum_ub : 1));
+        p.stage_val = sc.take<char>(vsz * (size_t)(sum_ub > 0 ? sum_ub : 1));
+        p.stage_off = so;
+        launch_scan_rowptr(L.ub, nrows, so, tot, scr, s);
+    }
     // on any failure from here on the pools go back to the allocator and C
     // is left empty (nothing to release for the caller)
     auto fail = [&](int code) {

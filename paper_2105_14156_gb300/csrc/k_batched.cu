@@ -153,6 +153,51 @@ __device__ void warp_row(const BatchArgs &p, const BatchMat &M, int64_t g, int64
     int64_t ab, ae;
     a_row_range(op, r, ab, ae, p.err);
     const int T = 1 << p.tw_bits;
+    if (M.ncols <= p.dense_max && NUM && p.stage_ci) {
+        // one-pass row: copy the row staged by the first phase to its place
+        const int64_t so = p.stage_off[g];
+        for (int q = lane; q < n_exp; q += 32) {
+            p.ci_pool[base + c0 + q] = p.stage_ci[so + q];
+            ((V *)p.val_pool)[base + c0 + q] = ((const V *)p.stage_val)[so + q];
+        }
+        return;
+    }
+    if (M.ncols <= p.dense_max && !NUM && p.stage_ci) {
+        // one-pass row: values, count and the sorted row (staged) at once
+        const int words = (M.ncols + 31) >> 5;
+        V *acc = (V *)wtab;
+        unsigned *bm = (unsigned *)(wtab + (((size_t)M.ncols * sizeof(V) + 15) & ~(size_t)15));
+        for (int w = lane; w < words; w += 32) bm[w] = 0u;
+        for (int j = lane; j < M.ncols; j += 32) acc[j] = V(0);
+        __syncwarp();
+        warp_products<V, true>(op, ab, ae, p.err, [&](int j, V a, V bkj) {
+            atomicAdd(acc + j, a * bkj);
+            const unsigned bit = 1u << (j & 31);
+            if (!(*(volatile unsigned *)(bm + (j >> 5)) & bit)) atomicOr(bm + (j >> 5), bit);
+        });
+        __syncwarp();
+        const int64_t so = p.stage_off[g];
+        const int room = p.ub[g];
+        int run = 0;
+        for (int w = 0; w < words; ++w) {
+            const unsigned bits = bm[w];
+            const int j = (w << 5) + lane;
+            if ((bits >> lane) & 1u) {
+                const int pos = run + __popc(bits & lanemask_lt());
+                if (pos < room) {
+                    p.stage_ci[so + pos] = j;
+                    ((V *)p.stage_val)[so + pos] = acc[j];
+                }
+            }
+            run += __popc(bits);
+        }
+        if (lane == 0) {
+            p.nnz[g] = run;
+            if (run > room) raise_err(p.err, kErrTableFull);
+        }
+        __syncwarp();
+        return;
+    }
     if (M.ncols <= p.dense_max) {
         // dense accumulator over the columns of B (values, then the bitmap)
         const int words = (M.ncols + 31) >> 5;
@@ -270,21 +315,52 @@ __device__ void block_row(const BatchArgs &p, const BatchMat &M, int64_t g, int6
     __syncthreads();
 }
 
-// Items: [0, nbig) big rows, then [nbig, nbig + ntiles) tiles.
+// Work of one phase: the big rows first, one per block (claimed with one
+// counter); then every warp claims chunks of 32 consecutive rows of the
+// flattened row space on its own (a second counter) and serves the small rows
+// among them, with no block-wide wait between rows of unequal cost.
+constexpr int kRowChunk = 32;
+
 template <typename V, bool NUM>
-__device__ bool run_items(const BatchArgs &p, int *token, const BatchSmem<V> &sm, int nbig) {
+__device__ bool run_items(const BatchArgs &p, int *token, int *chunks, const BatchSmem<V> &sm, int nbig) {
     __shared__ long long s_item;
     const int w = threadIdx.x >> 5;
+    const int lane = lane_id();
     const size_t wbytes = ((size_t)1 << p.tw_bits) * (4 + sizeof(V));
-    const long long total = (long long)nbig + p.ntiles;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(token, 1);
         __syncthreads();
         const long long it = s_item;
         __syncthreads();
-        if (it >= total) break;
-        if (it < nbig) {
-            const int64_t g = p.big[it];
+        if (it >= nbig) break;
+        const int64_t g = p.big[it];
+        const int mi = find_mat(p.row_start, p.nmat, g);
+        const BatchMat &M = p.mats[mi];
+        const int64_t r = g - p.row_start[mi];
+        int64_t c0 = 0;
+        int n_exp = 0;
+        int64_t base = 0;
+        if (NUM) {
+            const int64_t *rp = p.rp_pool + p.row_start[mi] + mi;
+            c0 = rp[r];
+            n_exp = (int)(rp[r + 1] - rp[r]);
+            base = p.base[mi];
+        }
+        block_row<V, NUM>(p, M, g, r, sm, c0, n_exp, base);
+    }
+    // small rows: `chunks` counts the chunks of kRowChunk rows handed out
+    unsigned char *wtab = sm.tab + (size_t)w * wbytes;
+    for (;;) {
+        int ch = 0;
+        if (lane == 0) ch = atomicAdd(chunks, 1);
+        ch = __shfl_sync(kFull, ch, 0);
+        const int64_t g0 = (int64_t)ch * kRowChunk;
+        if (g0 >= p.nrows) break;
+        const int64_t g1 = g0 + kRowChunk < p.nrows ? g0 + kRowChunk : p.nrows;
+        // the small rows of the chunk, one at a time
+        const bool mine = g0 + lane < g1 && p.cls[g0 + lane] == kRowSmall;
+        for (unsigned todo = __ballot_sync(kFull, mine); todo; todo &= todo - 1) {
+            const int64_t g = g0 + __ffs(todo) - 1;
             const int mi = find_mat(p.row_start, p.nmat, g);
             const BatchMat &M = p.mats[mi];
             const int64_t r = g - p.row_start[mi];
@@ -297,28 +373,7 @@ __device__ bool run_items(const BatchArgs &p, int *token, const BatchSmem<V> &sm
                 n_exp = (int)(rp[r + 1] - rp[r]);
                 base = p.base[mi];
             }
-            block_row<V, NUM>(p, M, g, r, sm, c0, n_exp, base);
-        } else {
-            const int64_t tile = it - nbig;
-            const int mi = find_mat(p.tile_start, p.nmat, tile);
-            const BatchMat &M = p.mats[mi];
-            const int64_t r = (tile - p.tile_start[mi]) * kBW + w;
-            if (r < M.a_rows) {
-                const int64_t g = p.row_start[mi] + r;
-                if (p.cls[g] == kRowSmall) {
-                    int64_t c0 = 0;
-                    int n_exp = 0;
-                    int64_t base = 0;
-                    if (NUM) {
-                        const int64_t *rp = p.rp_pool + p.row_start[mi] + mi;
-                        c0 = rp[r];
-                        n_exp = (int)(rp[r + 1] - rp[r]);
-                        base = p.base[mi];
-                    }
-                    warp_row<V, NUM>(p, M, g, r, sm.tab + (size_t)w * wbytes, c0, n_exp, base);
-                }
-            }
-            __syncthreads();
+            warp_row<V, NUM>(p, M, g, r, wtab, c0, n_exp, base);
         }
     }
     return true;
@@ -341,7 +396,7 @@ __global__ void __launch_bounds__(kBNT) k_batched(const BatchArgs *pp) {
     const int nbig = p.counters[0];
     int *bar = p.counters + 6;
     // phase 1: symbolic counts
-    run_items<V, false>(p, p.counters + 2, sm, nbig);
+    run_items<V, false>(p, p.counters + 2, p.counters + 8, sm, nbig);
     if (!grid_barrier(bar, p.err, p.wait_spins, p.missing)) return;
     // phase 2: row pointers of each product (one product per block at a time)
     __shared__ int s_m;
@@ -397,7 +452,7 @@ __global__ void __launch_bounds__(kBNT) k_batched(const BatchArgs *pp) {
     }
     if (!grid_barrier(bar, p.err, p.wait_spins, p.missing)) return;
     // phase 4: values
-    run_items<V, true>(p, p.counters + 3, sm, nbig);
+    run_items<V, true>(p, p.counters + 3, p.counters + 9, sm, nbig);
 }
 
 // ---------------------------------------------------------------------------

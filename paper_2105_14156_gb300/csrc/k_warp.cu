@@ -1,15 +1,9 @@
 // Warp rows: one warp per row of C, for the bins whose tables hold up to a
 // few hundred columns (the bulk of the rows of R-MAT products).
 //
-// Hashing Phase, with the row's partial products enumerated from registers:
-// lane l of each batch of 32 entries of A_i holds entry l (where the row of B
-// it selects starts, its length and a_ik), entries whose row of B is empty
-// moved out of the way; a scan of the lengths lays the batch's products on
-// one line, and each step hands 32 consecutive products to the 32 lanes. The
-// entry of product q + l is the number of entries that end at or before it:
-// those ending before the step (one ballot) plus those ending inside it (one
-// OR-reduction of one bit per end, then a popcount below the lane). Loads of
-// B are coalesced: consecutive lanes read consecutive entries of a row of B.
+// Hashing Phase, with the row's partial products enumerated from registers
+// (warp_enum.cuh: lanes hold a batch of A's entries, each step hands 32
+// consecutive products to the 32 lanes, loads of B coalesced).
 //
 // Insertion tries the compare-and-swap EMPTY -> j first; a slot that holds
 // another tag sends the lane one slot on (linear probing with wrap-around,
@@ -24,44 +18,13 @@
 
 #include "device_common.cuh"
 #include "kernels.h"
+#include "warp_enum.cuh"
 #include "writeout.cuh"
 
 namespace smash {
 
 constexpr int kWarpRowWarps = 4;   // warps (rows in flight) per block
-constexpr int kWarpUnroll = 4;     // steps of 32 products whose loads are issued together
 constexpr int kWarpMaxList = 512;  // most columns a warp row may hold (16 per lane)
-
-// Per-warp scratch of the register enumerator: one batch of entries.
-template <typename V>
-struct EntryScratch {
-    int64_t start[32];
-    V av[32];
-    int len[32];
-};
-
-// The row of B selected by column k of A (start and length, checked), for
-// kernels that never see B sliced by column window.
-template <typename V>
-__device__ __forceinline__ void b_row_whole(const Operands<V> &op, int k, int &len, int64_t &bs, int *err) {
-    len = 0;
-    bs = 0;
-    if ((unsigned)k < (unsigned)op.b_rows) {
-        const int64_t s = __ldg(op.b_rp + k), t = __ldg(op.b_rp + k + 1);
-        if (s >= 0 && t >= s && t <= op.b_nnz) {
-            if (t - s < kMaxBRow) {
-                bs = s;
-                len = (int)(t - s);
-            } else {
-                raise_err(err, kErrBRowTooLong);
-            }
-        } else {
-            raise_err(err, kErrBadRowPtr);
-        }
-    } else {
-        raise_err(err, kErrBadIndex);
-    }
-}
 
 // Bulk copy (the TMA engine's non-tensor copy) of `bytes` bytes, a multiple
 // of 16, from this block's shared memory to global memory of this GPU, both
@@ -78,103 +41,6 @@ __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.w
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // Orders this thread's earlier shared-memory writes before later bulk copies.
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// Insertion of tag j into a shared-memory table of 2^tbits slots: the slot
-// (-1: the table is full), and whether this call claimed it.
-__device__ __forceinline__ int cas_insert(int *keys, int tbits, HashCfg hc, int j, bool &ins) {
-    const uint32_t mask = (1u << tbits) - 1u;
-    uint32_t h = hash_slot(j, tbits, hc) & mask;
-    ins = false;
-    for (uint32_t n = 0; n <= mask; ++n) {
-        const int old = atomicCAS(keys + h, kEmpty, j);
-        if (old == kEmpty) {
-            ins = true;
-            return (int)h;
-        }
-        if (old == j) return (int)h;
-        h = (h + 1u) & mask;
-    }
-    return -1;
-}
-
-// Every product a_ik * b_kj of A entries [ab, ae), enumerated by one warp.
-// f(act, j, a, b, p) is called by all 32 lanes together once per step of 32
-// products (act: the lane holds a product; p: its index among the row's
-// products), so that it may use warp votes.
-// IT: type of the positions in B (int32_t when B has fewer than 2^31 entries).
-template <typename V, typename IT, bool NUM, typename F>
-__device__ __forceinline__ void warp_enum(const Operands<V> &op, int64_t ab, int64_t ae, EntryScratch<V> &es,
-                                          int *err, F &&f) {
-    const int lane = lane_id();
-    int pbase = 0;   // products of the earlier batches
-    for (int64_t base = ab; base < ae; base += 32) {
-        int len = 0;
-        int64_t bs = 0;
-        V av = V(0);
-        if (base + lane < ae) {
-            b_row_whole(op, __ldg(op.a_ci + base + lane), len, bs, err);
-            if constexpr (NUM) av = op.a_val[base + lane];
-        }
-        // entries with an empty row of B would share their end with the entry
-        // before them: move the others to the low lanes, in order
-        const unsigned nz = __ballot_sync(kFull, len > 0);
-        const int nv = __popc(nz);
-        if (nv < 32 && nz != (1u << nv) - 1u) {
-            if (len > 0) {
-                const int d = __popc(nz & lanemask_lt());
-                es.start[d] = bs;
-                es.len[d] = len;
-                if constexpr (NUM) es.av[d] = av;
-            }
-            __syncwarp();
-            len = lane < nv ? es.len[lane] : 0;
-            bs = lane < nv ? es.start[lane] : 0;
-            if constexpr (NUM) av = lane < nv ? es.av[lane] : V(0);
-            __syncwarp();
-        }
-        const int incl = warp_incl_scan(len);
-        const int total = __shfl_sync(kFull, incl, 31);
-        const IT start = (IT)(bs - (incl - len));   // product p of this entry reads B at start + p
-        for (int q0 = 0; q0 < total; q0 += 32 * kWarpUnroll) {
-            int jv[kWarpUnroll];
-            V a_u[kWarpUnroll], b_u[kWarpUnroll];
-            bool act[kWarpUnroll];
-#pragma unroll
-            for (int u = 0; u < kWarpUnroll; ++u) {
-                const int q = q0 + 32 * u;
-                act[u] = q + lane < total;
-                jv[u] = 0;
-                a_u[u] = V(0);
-                b_u[u] = V(0);
-                if (q < total) {
-                    const int c0 = __popc(__ballot_sync(kFull, incl <= q));
-                    const int e = incl - q;
-                    const unsigned ends = __reduce_or_sync(kFull, (e >= 1 && e <= 31) ? (1u << e) : 0u);
-                    const int ci = c0 + __popc(ends & ((2u << lane) - 1u));
-                    const IT st = __shfl_sync(kFull, start, ci);
-                    if constexpr (NUM) a_u[u] = __shfl_sync(kFull, av, ci);
-                    if (act[u]) {
-                        const IT idx = st + (IT)(q + lane);
-                        jv[u] = __ldg(op.b_ci + idx);
-                        if constexpr (NUM) b_u[u] = __ldg(op.b_val + idx);
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kWarpUnroll; ++u) {
-                if (q0 + 32 * u < total) {
-                    bool ok = act[u];
-                    if (ok && (unsigned)jv[u] >= (unsigned)op.ncols) {
-                        raise_err(err, kErrBadIndex);
-                        ok = false;
-                    }
-                    f(ok, jv[u], a_u[u], b_u[u], pbase + q0 + 32 * u + lane);
-                }
-            }
-        }
-        pbase += total;
-    }
-}
 
 // ----- symbolic --------------------------------------------------------------
 template <typename IT, int NW>
