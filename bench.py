@@ -291,9 +291,9 @@ def kernel_bytes(t, vb, nnz_b, total_products):
     B's bytes shared out over the launch groups by their products."""
     rows, a_nnz, prods, c_nnz = t["rows"], t["a_nnz"], t["products"], t["c_nnz"]
     share = prods / total_products if total_products else 0.0
-    if t["name"].startswith("sym_") or t["name"] == "num_dense_count":
+    if t["name"] in ("sym_hash", "sym_warp", "sym_tiny", "sym_dense", "sym_spill", "num_dense_count"):
         return 12 * rows + 4 * a_nnz + 4 * nnz_b * share
-    if t["name"].startswith("num_"):
+    if t["name"] in ("num_hash", "num_warp", "num_group", "num_tiny", "num_spill", "num_dense_window"):
         return 16 * rows + (4 + vb) * (a_nnz + c_nnz) + (4 + vb) * nnz_b * share
     return None
 
@@ -337,6 +337,8 @@ def main():
     ap.add_argument("--variants", default="all", choices=["all", "none"])
     ap.add_argument("--variant-steps", type=int, default=10)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--save-model", default=None, help="write the trained row-size model to this file")
+    ap.add_argument("--load-model", default=None, help="use this trained model instead of training one")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     args.e2e_steps = max(args.e2e_steps, 1)
@@ -359,7 +361,7 @@ def main():
     do_var = args.variants == "all" and world == 1
     need_model = args.path == "learned" or do_var
     train_mats, gen_train_s = None, 0.0
-    if need_model:
+    if need_model and not args.load_model:
         # CPU work first: the spawn pool starts before the first CUDA call
         from paper_2105_14156_gb300 import learned
         t0 = time.perf_counter()
@@ -380,11 +382,17 @@ def main():
     stream = torch.cuda.current_stream()
 
     model, training = None, None
-    if need_model:
+    if need_model and args.load_model:
+        model = smash.Model(h)
+        model.load(args.load_model)
+        training = {"loaded": args.load_model}
+    elif need_model:
         model, loss, train_s, nsamp = learned.train(h, train_mats, epochs=8, batch=4096)
         training = {"matrices": len(train_mats), "samples": nsamp, "final_mse": loss, "device_train_s": train_s,
                     "cpu_generation_s": gen_train_s, "epochs": 8, "batch": 4096}
         del train_mats
+    if model is not None and args.save_model:
+        model.save(args.save_model)
     tuned = None
     margin = 0.15
     if not args.no_autotune:
@@ -426,12 +434,15 @@ def main():
 
     ms = replica_max(sum(times) / len(times), dist, dev)
 
-    # dominant kernel: roofline from the live per-launch event timing (launch
-    # groups of one phase run side by side on four streams: a group's window
-    # counts from when its stream reaches it)
+    # dominant kernel: the launch group that moves the most algorithmic bytes,
+    # roofline from its live per-launch event timing. The bins of a phase run
+    # side by side on four streams, most products first, so this group starts
+    # on an idle GPU and its event window is its own duration (the windows of
+    # groups launched after it also count the time spent waiting for SMs).
     peaks, peak_src = load_peaks()
     launches = int(sum(t["kernels"] for t in kt))
-    dom = max((t for t in kt if kernel_bytes(t, vb, B.nnz, products) is not None), key=lambda t: t["ms"])
+    dom = max((t for t in kt if kernel_bytes(t, vb, B.nnz, products) is not None),
+              key=lambda t: kernel_bytes(t, vb, B.nnz, products))
     per_launch_ms = dom["ms"] / dom["launches"]
     per_launch_bytes = kernel_bytes(dom, vb, B.nnz, products) / dom["launches"]
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9

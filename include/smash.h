@@ -91,7 +91,12 @@ typedef struct {
     int32_t bulk_copy;       /* warp rows: 1 stages each sorted row in shared memory and streams it to C
                                 with bulk (TMA engine) copies, Version 3's copy-out; 0 (default): each lane
                                 stores its entries (measured faster for rows of a few hundred entries) */
-    int32_t reserved[3];
+    int32_t group_rows;      /* numeric rows served by a block of 64-1024 threads: 1: the products of a row
+                                spread over the block's warps, compare-and-swap-first probing, list-driven
+                                write-out (and no table for rows without repeated columns); 0 (default): the
+                                staged enumeration with a write-out that scans the whole table (measured
+                                faster on R-MAT products) */
+    int32_t reserved[2];
 } smash_params;
 
 /* Per-call statistics (the last symbolic or numeric call of the handle). */

@@ -333,6 +333,7 @@ inline int check_params(const smash_params *p) {
         return SMASH_ERR_INVALID_ARG;
     if (p->warp_rows != 0 && p->warp_rows != 1) return SMASH_ERR_INVALID_ARG;
     if (p->bulk_copy != 0 && p->bulk_copy != 1) return SMASH_ERR_INVALID_ARG;
+    if (p->group_rows != 0 && p->group_rows != 1) return SMASH_ERR_INVALID_ARG;
     return SMASH_OK;
 }
 
@@ -588,6 +589,14 @@ inline bool use_warp_rows(const smash_handle *h, const HashLaunch &hl, int dtype
     if (!h->params.warp_rows || group_threads(hl) != 32) return false;
     const size_t need = dtype < 0 ? sym_warp_smem(hl.tbits) : num_warp_smem(dtype, hl.tbits, 1.0f / h->params.max_load);
     return need <= (size_t)max_smem_per_block();
+}
+
+// Whether a bin runs the numeric group-row kernel (k_group.cu): a block of
+// 64 or more threads per row, and its shared memory fits.
+inline bool use_group_rows(const smash_handle *h, const HashLaunch &hl, int dtype) {
+    if (!h->params.group_rows || group_threads(hl) < 64) return false;
+    return num_group_smem(dtype, hl.tbits, 1.0f / h->params.max_load, hl.group_shift) <=
+           (size_t)max_smem_per_block();
 }
 
 inline HashLaunch hash_launch(const smash_handle *h, int tbits, int64_t ncols) {

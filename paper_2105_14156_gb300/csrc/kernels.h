@@ -179,6 +179,12 @@ void launch_sym_warp(const RawOperands &op, const int *rows, int count, int *tok
 void launch_num_warp(int dtype, const RawOperands &op, const int *rows, int count, int *token,
                      const HashLaunch &hl, float inv_load, const RowGather *rec, int bulk_copy, const NumOut &out,
                      int *err, cudaStream_t s);
+// Group rows (k_group.cu): a block of 64-1024 threads per row, the numeric
+// phase of the warp rows spread over the block's warps.
+size_t num_group_smem(int dtype, int tbits, float inv_load, int group_shift);
+void launch_num_group(int dtype, const RawOperands &op, const int *rows, int count, int *token,
+                      const HashLaunch &hl, float inv_load, const RowGather *rec, const NumOut &out, int *err,
+                      cudaStream_t s);
 // Thread-per-row bins (tbits <= BinRule::tiny_tbits, k_tiny.cu): list length of a bin, and
 // the symbolic count / numeric merge of its rows.
 int tiny_list_len(int tbits, float max_load);

@@ -148,4 +148,114 @@ __device__ __forceinline__ void warp_enum(const Operands<V> &op, int64_t ab, int
     }
 }
 
+// Every product of A entries [ab, ae), enumerated by a group of GS threads
+// (one block, GS = NT): batches of GS entries are staged in shared memory
+// (entries with an empty row of B dropped), the batch's products are split
+// into one contiguous range per warp, and each warp walks its range 32
+// products a step; a lane finds its entry from the set of entry ends inside
+// the step (step_entry). f(act, j, a, b, p) is called by all 32 lanes of a
+// warp together once per step of its range (p: the product's index among the
+// row's products). sc: the group's product scratch (prod_scratch_bytes).
+template <typename V, typename IT, bool NUM, int GS, typename F>
+__device__ __forceinline__ void group_enum(const Operands<V> &op, int64_t ab, int64_t ae, const ProdScratch<V> &sc,
+                                           int *err, F &&f) {
+    using G = Group<GS, GS>;
+    const int t = G::tid();
+    const int lane = lane_id();
+    const int w = G::wid();
+    int pbase = 0;
+    int k_next = -1;
+    V av_next = V(0);
+    if (ab + t < ae) {
+        k_next = __ldg(op.a_ci + ab + t);
+        if constexpr (NUM) av_next = op.a_val[ab + t];
+    }
+    for (int64_t base = ab; base < ae; base += GS) {
+        int len = 0;
+        int64_t bs = 0;
+        const V av = av_next;
+        if (base + t < ae) b_row_whole(op, k_next, len, bs, err);
+        const long long packed = ((long long)(len > 0 ? 1 : 0) << 32) | (long long)len;
+        long long tot64;
+        const long long ex = G::template excl_scan<long long, false>(packed, (long long *)sc.red64, &tot64);
+        const int cidx = (int)(ex >> 32);
+        const int excl = (int)(ex & 0xffffffffll);
+        const int nf = (int)(tot64 >> 32);
+        const int total = (int)(tot64 & 0xffffffffll);
+        if (len > 0) {
+            sc.incl[cidx] = excl + len;
+            sc.start[cidx] = bs - excl;
+            if constexpr (NUM) sc.av[cidx] = av;
+        }
+        if (base + GS + t < ae) {
+            k_next = __ldg(op.a_ci + base + GS + t);
+            if constexpr (NUM) av_next = op.a_val[base + GS + t];
+        }
+        G::sync();
+        const int per = ((total + G::kWarps - 1) / G::kWarps + 31) & ~31;
+        const int lo = min(w * per, total);
+        const int hi = min(lo + per, total);
+        if (lo < hi) {
+            int a = 0, b = nf;
+            while (a < b) {
+                const int m = (a + b) >> 1;
+                if (sc.incl[m] <= lo) a = m + 1;
+                else b = m;
+            }
+            int c0 = a;
+            for (int pb = lo; pb < hi; pb += 32 * kWarpUnroll) {
+                int jv[kWarpUnroll];
+                V av_u[kWarpUnroll], bv[kWarpUnroll];
+                bool act[kWarpUnroll];
+#pragma unroll
+                for (int u = 0; u < kWarpUnroll; ++u) {
+                    const int q = pb + 32 * u;
+                    act[u] = false;
+                    jv[u] = 0;
+                    av_u[u] = V(0);
+                    bv[u] = V(0);
+                    if (q < hi) {
+                        act[u] = q + lane < hi;
+                        const int e0 = sc.incl[c0] - q;   // same for all lanes
+                        int ci;
+                        if (e0 >= 32) {
+                            ci = c0;                      // the whole step lies in entry c0
+                            if (e0 == 32) ++c0;
+                        } else {
+                            const int c = c0 + lane;
+                            const int e = c < nf ? sc.incl[c] - q : INT_MAX;
+                            ci = c0 + step_entry(e);
+                            c0 += __popc(__ballot_sync(kFull, e <= 32));
+                        }
+                        if (act[u]) {
+                            const IT idx = (IT)sc.start[ci] + (IT)(q + lane);
+                            jv[u] = __ldg(op.b_ci + idx);
+                            if constexpr (NUM) {
+                                bv[u] = __ldg(op.b_val + idx);
+                                av_u[u] = sc.av[ci];
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kWarpUnroll; ++u) {
+                    const int q = pb + 32 * u;
+                    if (q < hi) {
+                        bool ok = act[u];
+                        if (ok && (unsigned)jv[u] >= (unsigned)op.ncols) {
+                            raise_err(err, kErrBadIndex);
+                            ok = false;
+                        }
+                        f(ok, jv[u], av_u[u], bv[u], pbase + q + lane);
+                    }
+                }
+            }
+        }
+        pbase += total;
+        // the next batch stages its entries only after the first barrier of
+        // its scan, which every warp reaches after its walk
+    }
+    G::sync();
+}
+
 }  // namespace smash

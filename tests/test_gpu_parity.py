@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 DEFAULT = dict(hash_kind=1, max_load=0.5, sym_max_tbits=15, num_max_tbits=14, group_shift=4, dense_ratio=4,
                bitmap_ratio=4, spill_blocks_per_sm=1, sym_dense_ratio=64, dense_blocks=0,
-               sym_dense_blocks=0, warp_rows=1, bulk_copy=0)
+               sym_dense_blocks=0, warp_rows=1, bulk_copy=0, group_rows=0)
 
 # Parameter sets that force each path.
 PATHS = {
@@ -36,6 +36,7 @@ PATHS = {
     "group_per_row": dict(group_shift=0),
     "warp_rows_staged": dict(warp_rows=0),
     "bulk_copy_out": dict(bulk_copy=1),
+    "group_rows_listed": dict(group_rows=1),
     "warp_rows_wide": dict(group_shift=6),
     "bitonic_only": dict(bitmap_ratio=0),
     "bitmap_always": dict(bitmap_ratio=1 << 20),
