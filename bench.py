@@ -337,6 +337,8 @@ def main():
     ap.add_argument("--variants", default="all", choices=["all", "none"])
     ap.add_argument("--variant-steps", type=int, default=10)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--params", default=None,
+                    help='planner parameters as JSON, e.g. \'{"hash_kind": 2}\' (implies --no-autotune)')
     ap.add_argument("--save-model", default=None, help="write the trained row-size model to this file")
     ap.add_argument("--load-model", default=None, help="use this trained model instead of training one")
     args = ap.parse_args()
@@ -395,6 +397,10 @@ def main():
         model.save(args.save_model)
     tuned = None
     margin = 0.15
+    if args.params:
+        h.set_params(**json.loads(args.params))
+        tuned = dict(json.loads(args.params), given=True)
+        args.no_autotune = True
     if not args.no_autotune:
         tuned, _ = autotune.tune(h, dA, dB, args.workload, cache_path=None)
         if args.path == "learned":

@@ -290,6 +290,54 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
                 keys[q] = kEmpty;
                 vals[q] = V(0);
             }
+        } else if (hc.kind == 2 && !direct) {
+            // Version 1's write-back: the order-preserving hash (the high bits
+            // of the column) leaves the table almost sorted in slot order, so
+            // the occupied slots are compacted in order (in place: a chunk is
+            // read before anything lands on it), the local disorder that
+            // collisions left is sorted out by odd-even transposition passes
+            // until one pass of each parity swaps nothing, and the row streams
+            // to C; then the whole table goes back to EMPTY / 0.
+            int filled = 0;
+            for (int s0 = 0; s0 < T; s0 += 32) {
+                const int k = keys[s0 + lane];
+                const V v = vals[s0 + lane];
+                const bool occ = k != kEmpty;
+                const unsigned m = __ballot_sync(kFull, occ);
+                __syncwarp();
+                if (occ) {
+                    const int d = filled + __popc(m & lanemask_lt());
+                    keys[d] = k;
+                    vals[d] = v;
+                }
+                filled += __popc(m);
+                __syncwarp();
+            }
+            for (int pass = 0, quiet = 0; quiet < 2 && pass < tot + 2; ++pass) {
+                bool swapped = false;
+                for (int x = 2 * lane + (pass & 1); x + 1 < tot; x += 64) {
+                    const int a = keys[x], b = keys[x + 1];
+                    if (a > b) {
+                        keys[x] = b;
+                        keys[x + 1] = a;
+                        const V va = vals[x];
+                        vals[x] = vals[x + 1];
+                        vals[x + 1] = va;
+                        swapped = true;
+                    }
+                }
+                __syncwarp();
+                quiet = __any_sync(kFull, swapped) ? 0 : quiet + 1;
+            }
+            for (int q = lane; q < tot; q += 32) {
+                out.c_ci[c0 + q] = keys[q];
+                out.c_val[c0 + q] = vals[q];
+            }
+            __syncwarp();
+            for (int s0 = lane; s0 < T; s0 += 32) {
+                keys[s0] = kEmpty;
+                vals[s0] = V(0);
+            }
         } else if (tot <= 32) {
             // rank of each entry among the row's (at most 32) columns
             int k = INT_MAX;
