@@ -96,7 +96,12 @@ typedef struct {
                                 write-out (and no table for rows without repeated columns); 0 (default): the
                                 staged enumeration with a write-out that scans the whole table (measured
                                 faster on R-MAT products) */
-    int32_t reserved[2];
+    int32_t row_window;      /* rows of a bin served together by one warp with one shared-memory table
+                                whose tags are (row, column) (the paper's windows of rows): 0 disables,
+                                else 2..32 rows per window (fewer where the window would hold more
+                                than 256 entries or a tag would not fit 31 bits); default 0 */
+    int32_t row_window_tbits; /* row windows take the bins whose per-row table has at most
+                                 2^row_window_tbits slots; [5, 8]; default 6 */
 } smash_params;
 
 /* Per-call statistics (the last symbolic or numeric call of the handle). */

@@ -24,6 +24,8 @@ int smash_default_params(smash_params *p) {
     p->warp_rows = 1;
     p->bulk_copy = 0;
     p->group_rows = 0;
+    p->row_window = 0;
+    p->row_window_tbits = 6;
     return SMASH_OK;
 }
 
@@ -321,6 +323,10 @@ int run_symbolic(smash_handle *h, const RawOperands &op, int64_t n, Plan &pl, in
             LaunchTimer lt(h, bs, "sym_spill", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
             launch_sym_spill(op, rows, counts[b], tok, hl, rule.inv_load, pl.bound, spill_tb, (int *)h->tables.ptr,
                              nnz_out, err, bs);
+        } else if (RowWin rw; row_window_of(h, tbits_of_bin(b), op.ncols, -1, rw)) {
+            const HashLaunch hl = hash_launch(h, tbits_of_bin(b), op.ncols);
+            LaunchTimer lt(h, bs, "sym_rowwin", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);
+            launch_sym_rowwin(op, rows, counts[b], tok, rw, hl, nnz_out, err, bs);
         } else if (tbits_of_bin(b) <= rule.tiny_tbits && counts[b] >= tiny_min_rows(h)) {
             LaunchTimer lt(h, bs, "sym_tiny", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);
             launch_sym_tiny(op, rows, counts[b], tbits_of_bin(b), h->params.max_load, h->sms, nnz_out, err, bs);
@@ -496,6 +502,11 @@ int run_bins(smash_handle *h, const RawOperands &op, int64_t n, int dt, const Nu
             const HashLaunch hl = hash_launch(h, spill_tb, op.ncols);
             LaunchTimer lt(h, bs, "num_spill", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
             launch_num_spill(dt, op, rows, counts[b], tok, hl, rule.inv_load, spill_tb, h->tables.ptr, out, err, bs);
+        } else if (RowWin rw; row_window_of(h, tbits_of_bin(b), op.ncols, dt, rw)) {
+            cudaStream_t bs = fk.get(q++);
+            const HashLaunch hl = hash_launch(h, tbits_of_bin(b), op.ncols);
+            LaunchTimer lt(h, bs, "num_rowwin", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);
+            launch_num_rowwin(dt, op, rows, counts[b], tok, rw, hl, kept, out, err, bs);
         } else if (tbits_of_bin(b) <= rule.tiny_tbits && counts[b] >= tiny_min_rows(h)) {
             cudaStream_t bs = fk.get(q++);
             LaunchTimer lt(h, bs, "num_tiny", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);

@@ -334,6 +334,8 @@ inline int check_params(const smash_params *p) {
     if (p->warp_rows != 0 && p->warp_rows != 1) return SMASH_ERR_INVALID_ARG;
     if (p->bulk_copy != 0 && p->bulk_copy != 1) return SMASH_ERR_INVALID_ARG;
     if (p->group_rows != 0 && p->group_rows != 1) return SMASH_ERR_INVALID_ARG;
+    if (p->row_window != 0 && (p->row_window < 2 || p->row_window > 32)) return SMASH_ERR_INVALID_ARG;
+    if (p->row_window_tbits < kMinTBits || p->row_window_tbits > 8) return SMASH_ERR_INVALID_ARG;
     return SMASH_OK;
 }
 
@@ -597,6 +599,38 @@ inline bool use_group_rows(const smash_handle *h, const HashLaunch &hl, int dtyp
     if (!h->params.group_rows || group_threads(hl) < 64) return false;
     return num_group_smem(dtype, hl.tbits, 1.0f / h->params.max_load, hl.group_shift) <=
            (size_t)max_smem_per_block();
+}
+
+// The row window of the bin of tables of 2^tbits slots (false: the bin takes
+// another kernel). A row of the bin holds at most L = T / inv_load columns;
+// a window takes W <= row_window rows with W * L <= 256 and tags of at most
+// 31 bits. dtype < 0: the symbolic phase.
+inline bool row_window_of(const smash_handle *h, int tbits, int64_t ncols, int dtype, RowWin &rw) {
+    if (h->params.row_window < 2 || tbits > h->params.row_window_tbits) return false;
+    const int T = 1 << tbits;
+    const double inv = (double)(1.0f / h->params.max_load);
+    int L = (int)((double)T / inv + 1e-9);
+    L = L < 1 ? 1 : (L > T ? T : L);
+    int W = h->params.row_window;
+    if (W * L > 256) W = 256 / L;
+    const int cb = colbits_of(ncols);
+    if (cb > 30) return false;
+    while (W > (1 << (31 - cb))) W >>= 1;
+    if (W < 2) return false;
+    int wbits = 0;
+    while ((1 << wbits) < W) ++wbits;
+    int tw = 0;
+    while ((1 << tw) < W * T) ++tw;
+    rw.W = W;
+    rw.wbits = wbits;
+    rw.cb = cb;
+    rw.tbits = tw;
+    rw.lcap = (W * L + 31) & ~31;
+    rw.ts = (1 << tw) > 2 * rw.lcap ? (1 << tw) : 2 * rw.lcap;
+    rw.nb = 1 << (tw - 1);
+    rw.bsh = cb + wbits > tw - 1 ? cb + wbits - (tw - 1) : 0;
+    const size_t need = dtype < 0 ? sym_rowwin_smem(rw) : num_rowwin_smem(rw, dtype);
+    return need <= (size_t)max_smem_per_block();
 }
 
 inline HashLaunch hash_launch(const smash_handle *h, int tbits, int64_t ncols) {

@@ -185,6 +185,28 @@ size_t num_group_smem(int dtype, int tbits, float inv_load, int group_shift);
 void launch_num_group(int dtype, const RawOperands &op, const int *rows, int count, int *token,
                       const HashLaunch &hl, float inv_load, const RowGather *rec, const NumOut &out, int *err,
                       cudaStream_t s);
+// Row windows (k_rowwin.cu): a warp serves a window of W consecutive rows of
+// a bin with one shared-memory table whose tags are (row of the window,
+// column). Built by host::row_window_of.
+struct RowWin {
+    int W;      // rows per window (2..32)
+    int wbits;  // bits of a row of the window: W <= 2^wbits
+    int cb;     // bits of a column: tag = (row << cb) | column, cb + wbits <= 31
+    int tbits;  // the window's hash table holds 2^tbits slots
+    int ts;     // slots of the table region (>= 2 lcap: the write-out's sorted sequence)
+    int lcap;   // most entries a window holds (W times the bin's row room, multiple of 32, <= 256)
+    int nb;     // buckets of the write-out (2^(tbits-1))
+    int bsh;    // bucket of a tag: tag >> bsh
+};
+size_t sym_rowwin_smem(const RowWin &rw);
+size_t num_rowwin_smem(const RowWin &rw, int dtype);
+void launch_sym_rowwin(const RawOperands &op, const int *rows, int count, int *token, const RowWin &rw,
+                       const HashLaunch &hl, int *nnz_out, int *err, cudaStream_t s);
+// rec (may be null): per-row product counts; a window whose rows have no
+// repeated column (exact mode) or fit their capacities (capacity mode) is
+// staged without the table.
+void launch_num_rowwin(int dtype, const RawOperands &op, const int *rows, int count, int *token, const RowWin &rw,
+                       const HashLaunch &hl, const RowGather *rec, const NumOut &out, int *err, cudaStream_t s);
 // Thread-per-row bins (tbits <= BinRule::tiny_tbits, k_tiny.cu): list length of a bin, and
 // the symbolic count / numeric merge of its rows.
 int tiny_list_len(int tbits, float max_load);

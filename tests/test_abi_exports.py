@@ -57,3 +57,35 @@ def test_host_only_calls(lib):
     # argument checks happen before any device work
     assert lib.smash_create(None, 0, None) == 1
     assert lib.spgemm_symbolic(None, None, None, None, None, None) == 1
+
+
+STRUCTS = {"smash_csr": "CsrStruct", "smash_params": "Params", "smash_stats": "Stats",
+           "smash_kernel_time": "KernelTime", "smash_train_cfg": "TrainCfg",
+           "smash_learned_stats": "LearnedStats", "smash_batched_stats": "BatchedStats"}
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    the C compiler gives the header's struct (a host C program, no GPU)."""
+    import shutil
+    import subprocess
+    from paper_2105_14156_gb300 import smash
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "smash.h"', "int main(void) {"]
+    expect = []
+    for cname, pname in STRUCTS.items():
+        cls = getattr(smash, pname)
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        expect.append(ctypes.sizeof(cls))
+        for f, _ in cls._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {f}));')
+            expect.append(getattr(cls, f).offset)
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == expect

@@ -182,6 +182,40 @@ def test_learned_many_tiny_rows(handle, trained, margin, values):
     assert stats["c_nnz"] == Ch.col_idx.size
 
 
+@pytest.mark.parametrize("margin", [0.15, -0.6, 3.0])
+@pytest.mark.parametrize("values", ["f32", "f64"])
+def test_learned_row_windows(handle, trained, margin, values):
+    """Row windows in capacity mode: windows whose rows fit their predicted
+    room are staged and merged, the others hashed; rows over their room
+    (forced by the negative margin) are marked and redone by the exact
+    fallback, the other rows of their window are kept."""
+    from paper_2105_14156_gb300 import smash
+    from tests.helpers import random_csr
+    model, _, _ = trained
+    A = random_csr(30011, 20000, 0.00015, 191, values=values)
+    B = random_csr(20000, 50000, 0.00006, 192, values=values, sort_cols=False, dup_frac=0.2)
+    defaults = handle.params.as_dict()
+    handle.set_params(row_window=16, row_window_tbits=8)
+    try:
+        C, stats, owner = handle.spgemm_learned(smash.to_device(A), smash.to_device(B), model, margin=margin)
+        handle.check()
+        Ch = C.to_host()
+        owner.free()
+        R = rmat(12, 8, GRAPH500_ABCD, seed=193, values=values)
+        dR = smash.to_device(R)
+        C2, stats2, owner2 = handle.spgemm_learned(dR, dR, model, margin=margin)
+        handle.check()
+        C2h = C2.to_host()
+        owner2.free()
+    finally:
+        handle.set_params(**defaults)
+    assert_matches_oracle(Ch, A, B)
+    assert stats["c_nnz"] == Ch.col_idx.size
+    assert_matches_oracle(C2h, R, R)
+    if margin < 0:
+        assert stats["overflow_rows"] > 0
+
+
 @pytest.mark.parametrize("margin", [0.15, -0.9, 3.0])
 @pytest.mark.parametrize("dense_blocks", [2, 4])
 def test_learned_dense_rows_in_arena(handle, trained, margin, dense_blocks):

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 DEFAULT = dict(hash_kind=1, max_load=0.5, sym_max_tbits=15, num_max_tbits=14, group_shift=4, dense_ratio=4,
                bitmap_ratio=4, spill_blocks_per_sm=1, sym_dense_ratio=64, dense_blocks=0,
-               sym_dense_blocks=0, warp_rows=1, bulk_copy=0, group_rows=0)
+               sym_dense_blocks=0, warp_rows=1, bulk_copy=0, group_rows=0, row_window=0, row_window_tbits=6)
 
 # Parameter sets that force each path.
 PATHS = {
@@ -38,6 +38,9 @@ PATHS = {
     "bulk_copy_out": dict(bulk_copy=1),
     "group_rows_listed": dict(group_rows=1),
     "warp_rows_wide": dict(group_shift=6),
+    "row_windows": dict(row_window=16),
+    "row_windows_wide": dict(row_window=32, row_window_tbits=8),
+    "row_windows_high_bits": dict(row_window=8, hash_kind=2),
     "bitonic_only": dict(bitmap_ratio=0),
     "bitmap_always": dict(bitmap_ratio=1 << 20),
     "hash_low_bits": dict(hash_kind=0),
@@ -210,6 +213,35 @@ def test_tiny_rows_thread_per_row(handle, dtype, max_load):
     B2 = random_csr(300, 8, 0.5, 84, values=dtype)
     C2 = run(handle, A2, B2, max_load=max_load)
     assert_matches_oracle(C2, A2, B2)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("max_load", [0.5, 0.7])
+@pytest.mark.parametrize("window", [2, 5, 16, 32])
+def test_row_windows(handle, dtype, max_load, window):
+    """Windows of short rows sharing one (row, column)-tagged table per warp:
+    unsorted rows of B with duplicate columns (hashed windows), rows without
+    repeated columns (staged windows), empty rows inside a window, a last
+    window cut short (the row count is not a multiple of the window), and
+    rows whose many products collapse onto few columns."""
+    A = random_csr(30011, 20000, 0.00015, 181, values=dtype)
+    B = random_csr(20000, 50000, 0.00006, 182, values=dtype, sort_cols=False, dup_frac=0.2)
+    C = run(handle, A, B, max_load=max_load, row_window=window, row_window_tbits=8)
+    assert_matches_oracle(C, A, B)
+    Bs = random_csr(20000, 50000, 0.00006, 183, values=dtype)
+    C = run(handle, A, Bs, max_load=max_load, row_window=window, row_window_tbits=7)
+    assert_matches_oracle(C, A, Bs)
+    A2 = random_csr(401, 300, 0.2, 184, values=dtype)
+    B2 = random_csr(300, 8, 0.5, 185, values=dtype)
+    C2 = run(handle, A2, B2, max_load=max_load, row_window=window, row_window_tbits=5)
+    assert_matches_oracle(C2, A2, B2)
+
+
+def test_row_windows_integer_values_exact(handle):
+    """Small-integer float32 data through the row windows: sums are exact."""
+    A = rmat(12, 2, GRAPH500_ABCD, seed=186, values="int4")
+    C = run(handle, A, A, row_window=16, row_window_tbits=8)
+    assert_matches_oracle(C, A, A, exact=True)
 
 
 def test_tiny_rows_integer_values_exact(handle):
