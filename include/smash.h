@@ -99,9 +99,15 @@ typedef struct {
     int32_t row_window;      /* rows of a bin served together by one warp with one shared-memory table
                                 whose tags are (row, column) (the paper's windows of rows): 0 disables,
                                 else 2..32 rows per window (fewer where the window would hold more
-                                than 256 entries or a tag would not fit 31 bits); default 0 */
+                                than 256 entries or a tag would not fit 31 bits); default 16 */
     int32_t row_window_tbits; /* row windows take the bins whose per-row table has at most
-                                 2^row_window_tbits slots; [5, 8]; default 6 */
+                                 2^row_window_tbits slots, except the 32-slot bins that the
+                                 thread-per-row kernel takes (enough rows: measured faster there);
+                                 [5, 8]; default 7 */
+    int32_t dense_owner;     /* dense rows: 1: each warp of a block owns a slice of the column window (B is
+                                sliced per warp) and adds its products with plain shared-memory updates, lanes
+                                that hit one column in the same step taking turns (no atomics; the float add
+                                has no native shared-memory atomic on this GPU); 0: atomic adds */
 } smash_params;
 
 /* Per-call statistics (the last symbolic or numeric call of the handle). */

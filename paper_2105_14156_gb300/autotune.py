@@ -21,6 +21,8 @@ SPACE = [
     ("sym_dense_ratio", [16, 64, 256]),
     ("bitmap_ratio", [1, 4, 16]),
     ("dense_blocks", [1, 2, 4]),
+    ("dense_owner", [0, 1]),
+    ("row_window_tbits", [6, 7, 8]),
 ]
 
 

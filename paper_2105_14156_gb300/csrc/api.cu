@@ -24,8 +24,9 @@ int smash_default_params(smash_params *p) {
     p->warp_rows = 1;
     p->bulk_copy = 0;
     p->group_rows = 0;
-    p->row_window = 0;
-    p->row_window_tbits = 6;
+    p->row_window = 16;
+    p->row_window_tbits = 7;
+    p->dense_owner = 0;
     return SMASH_OK;
 }
 
@@ -323,7 +324,7 @@ int run_symbolic(smash_handle *h, const RawOperands &op, int64_t n, Plan &pl, in
             LaunchTimer lt(h, bs, "sym_spill", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
             launch_sym_spill(op, rows, counts[b], tok, hl, rule.inv_load, pl.bound, spill_tb, (int *)h->tables.ptr,
                              nnz_out, err, bs);
-        } else if (RowWin rw; row_window_of(h, tbits_of_bin(b), op.ncols, -1, rw)) {
+        } else if (RowWin rw; !tiny_first(h, rule, b, counts[b]) && row_window_of(h, tbits_of_bin(b), op.ncols, -1, rw)) {
             const HashLaunch hl = hash_launch(h, tbits_of_bin(b), op.ncols);
             LaunchTimer lt(h, bs, "sym_rowwin", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);
             launch_sym_rowwin(op, rows, counts[b], tok, rw, hl, nnz_out, err, bs);
@@ -368,30 +369,55 @@ int run_numeric(smash_handle *h, const RawOperands &op, int64_t n, int dt, const
     return run_bins(h, op, n, dt, out, pl, bp, s, nullptr, nullptr);
 }
 
-bool dense_windows(const smash_handle *h, const RawOperands &op, int dt, long long products, int &cpc, int &nw) {
-    cpc = num_window_cols(dt, dense_blocks_of(h, dt));
-    if (cpc <= 0 || op.b_nnz >= INT_MAX) return false;   // window bounds are int32 positions in B
-    nw = (int)((op.ncols + cpc - 1) / cpc);
+bool dense_windows(const smash_handle *h, const RawOperands &op, int dt, long long products, int &cpc, int &nw,
+                   int &per) {
+    per = 1;
+    if (op.b_nnz >= INT_MAX) return false;   // window bounds are int32 positions in B
+    const int bps = dense_blocks_of(h, dt);
     const double vsz = dt ? 8.0 : 4.0;
-    const double plan = nw > 1 ? 4.0 * (double)op.b_rows * (nw + 1) + 2.0 * (4 + vsz) * (double)op.b_nnz : 0.0;
-    return 16.0 * (double)products >= plan;
+    // slicing B costs a pass over its rows (and a copy when they are unsorted)
+    auto pays = [&](long long nsl) {
+        if (nsl > window_plan_max_slices()) return false;
+        const double plan =
+            nsl > 1 ? 4.0 * (double)op.b_rows * (double)(nsl + 1) + 2.0 * (4 + vsz) * (double)op.b_nnz : 0.0;
+        return 16.0 * (double)products >= plan;
+    };
+    if (h->params.dense_owner) {
+        const int c = num_window_cols(dt, bps, true);
+        const int S = window_warps(bps);
+        if (c > 0) {
+            const int n = (int)((op.ncols + c - 1) / c);
+            if (pays((long long)n * S)) {
+                cpc = c;
+                nw = n;
+                per = S;
+                return true;
+            }
+        }
+    }
+    cpc = num_window_cols(dt, bps, false);
+    if (cpc <= 0) return false;
+    nw = (int)((op.ncols + cpc - 1) / cpc);
+    return pays(nw);
 }
 
-int window_plan(smash_handle *h, const RawOperands &op, int dt, int cpc, int nw, cudaStream_t s, BSlices &sl) {
+int window_plan(smash_handle *h, const RawOperands &op, int dt, int cpc, int nw, int per, cudaStream_t s,
+                BSlices &sl) {
     auto &pc = h->plan_cache;
     if (pc.valid && pc.b_rp == op.b_rp && pc.b_ci == op.b_ci && pc.b_val == op.b_val && pc.b_nnz == op.b_nnz &&
-        pc.b_rows == op.b_rows && pc.ncols == op.ncols && pc.cpc == cpc && pc.nw == nw && pc.dt == dt) {
+        pc.b_rows == op.b_rows && pc.ncols == op.ncols && pc.cpc == cpc && pc.nw == nw && pc.per == per &&
+        pc.dt == dt) {
         sl = pc.sl;
         return SMASH_OK;
     }
     const size_t vsz = dt ? 8 : 4;
     const void *before = h->split.ptr;
     int st;
-    if ((st = ensure(h, h->split, 256 + window_plan_bytes(op, nw, vsz), s))) return st;
+    if ((st = ensure(h, h->split, 256 + window_plan_bytes(op, nw * per, vsz), s))) return st;
     (void)before;
     {
         LaunchTimer lt(h, s, "dense_plan", -1, 256, op.b_rows, 0, 0, op.b_nnz, 0);
-        lt.add_kernels(launch_window_plan(dt, op, nw, cpc, (char *)h->split.ptr + 256, sl, h->sms, s,
+        lt.add_kernels(launch_window_plan(dt, op, nw, per, cpc, (char *)h->split.ptr + 256, sl, h->sms, s,
                                           (int *)((char *)h->host + 1536)));
     }
     pc.valid = true;
@@ -403,6 +429,7 @@ int window_plan(smash_handle *h, const RawOperands &op, int dt, int cpc, int nw,
     pc.ncols = op.ncols;
     pc.cpc = cpc;
     pc.nw = nw;
+    pc.per = per;
     pc.dt = dt;
     pc.sl = sl;
     return SMASH_OK;
@@ -426,8 +453,8 @@ int run_bins(smash_handle *h, const RawOperands &op, int64_t n, int dt, const Nu
     // (a pass over B's rows and entries); otherwise the global hash. Their
     // counts and the slices of B are prepared on s before the bins fork.
     const int bd = kBinDense;
-    int cpc = 0, nw = 0;
-    const bool windows = counts[bd] && dense_windows(h, op, dt, sums[16 + bd], cpc, nw);
+    int cpc = 0, nw = 0, per = 1;
+    const bool windows = counts[bd] && dense_windows(h, op, dt, sums[16 + bd], cpc, nw, per);
     HashLaunch hld = hash_launch(h, 0, op.ncols);
     hld.dense_blocks = dense_blocks_of(h, dt);
     WinCount wc;
@@ -465,7 +492,7 @@ int run_bins(smash_handle *h, const RawOperands &op, int64_t n, int dt, const Nu
             h->wcache.slots = base + counts[bd];
         }
         // 2. column windows: slices of B
-        if ((st = window_plan(h, op, dt, cpc, nw, s, sl))) return st;
+        if ((st = window_plan(h, op, dt, cpc, nw, per, s, sl))) return st;
     }
     // global-memory tables of the spill bin (and of dense rows without windows)
     int spill_tb = 0;
@@ -502,15 +529,15 @@ int run_bins(smash_handle *h, const RawOperands &op, int64_t n, int dt, const Nu
             const HashLaunch hl = hash_launch(h, spill_tb, op.ncols);
             LaunchTimer lt(h, bs, "num_spill", b, 1024, counts[b], sums[b], sums[16 + b], sums[32 + b]);
             launch_num_spill(dt, op, rows, counts[b], tok, hl, rule.inv_load, spill_tb, h->tables.ptr, out, err, bs);
+        } else if (tbits_of_bin(b) <= rule.tiny_tbits && counts[b] >= tiny_min_rows(h)) {
+            cudaStream_t bs = fk.get(q++);
+            LaunchTimer lt(h, bs, "num_tiny", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);
+            launch_num_tiny(dt, op, rows, counts[b], tbits_of_bin(b), h->params.max_load, h->sms, out, err, bs);
         } else if (RowWin rw; row_window_of(h, tbits_of_bin(b), op.ncols, dt, rw)) {
             cudaStream_t bs = fk.get(q++);
             const HashLaunch hl = hash_launch(h, tbits_of_bin(b), op.ncols);
             LaunchTimer lt(h, bs, "num_rowwin", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);
             launch_num_rowwin(dt, op, rows, counts[b], tok, rw, hl, kept, out, err, bs);
-        } else if (tbits_of_bin(b) <= rule.tiny_tbits && counts[b] >= tiny_min_rows(h)) {
-            cudaStream_t bs = fk.get(q++);
-            LaunchTimer lt(h, bs, "num_tiny", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);
-            launch_num_tiny(dt, op, rows, counts[b], tbits_of_bin(b), h->params.max_load, h->sms, out, err, bs);
         } else {
             cudaStream_t bs = fk.get(q++);
             const HashLaunch hl = hash_launch(h, tbits_of_bin(b), op.ncols);

@@ -68,7 +68,7 @@ struct smash_handle {
         bool valid = false;
         const void *b_rp = nullptr, *b_ci = nullptr, *b_val = nullptr;
         int64_t b_nnz = 0, b_rows = 0, ncols = 0;
-        int cpc = 0, nw = 0, dt = 0;
+        int cpc = 0, nw = 0, per = 1, dt = 0;
         smash::BSlices sl;
     } plan_cache;
     // Per-row counts (flop_i, nnz(A_i), longest row of B) recorded by the last
@@ -336,6 +336,7 @@ inline int check_params(const smash_params *p) {
     if (p->group_rows != 0 && p->group_rows != 1) return SMASH_ERR_INVALID_ARG;
     if (p->row_window != 0 && (p->row_window < 2 || p->row_window > 32)) return SMASH_ERR_INVALID_ARG;
     if (p->row_window_tbits < kMinTBits || p->row_window_tbits > 8) return SMASH_ERR_INVALID_ARG;
+    if (p->dense_owner != 0 && p->dense_owner != 1) return SMASH_ERR_INVALID_ARG;
     return SMASH_OK;
 }
 
@@ -539,6 +540,14 @@ inline int dense_blocks_of(const smash_handle *h, int dtype) {
 // fewer rows than one 128-thread block per SM take the warp-per-row hash.
 inline int tiny_min_rows(const smash_handle *h) { return h->sms * 128; }
 
+// The thread-per-row kernel keeps the 32-slot bins that have enough rows in
+// both phases (measured faster there than row windows); row windows take the
+// symbolic 64-slot bin before it.
+inline bool tiny_first(const smash_handle *h, const BinRule &r, int bin, int count) {
+    const int tb = tbits_of_bin(bin);
+    return tb <= r.tiny_tbits && tb <= kTinyNumTBits && count >= tiny_min_rows(h);
+}
+
 inline BinRule sym_rule(const smash_handle *h, int64_t ncols) {
     BinRule r;
     r.inv_load = 1.0f / h->params.max_load;
@@ -558,7 +567,7 @@ inline BinRule num_rule(const smash_handle *h, int64_t ncols, int dtype) {
     r.inv_load = 1.0f / h->params.max_load;
     // dense rows need their columns counted in one bitmap (count pass) and a
     // column window that fits shared memory
-    const bool dense_fits = ncols <= dense_bitmap_max_cols() && num_window_cols(dtype, dense_blocks_of(h, dtype)) > 0;
+    const bool dense_fits = ncols <= dense_bitmap_max_cols() && num_window_cols(dtype, dense_blocks_of(h, dtype), false) > 0;
     r.dense_ok = (h->params.dense_ratio > 0 && dense_fits) ? 1 : 0;
     r.dense_min = r.dense_ok ? (ncols + h->params.dense_ratio - 1) / h->params.dense_ratio : (1ll << 62);
     if (r.dense_min < 1) r.dense_min = 1;
@@ -673,7 +682,10 @@ int run_bins(smash_handle *h, const RawOperands &op, int64_t n, int dt, const Nu
              const BinPlan &bp, cudaStream_t s, const WinArena *arena, const RowGather *cap_rec = nullptr);
 // Whether the dense bin (with `products` products) takes column windows, and
 // their width and number.
-bool dense_windows(const smash_handle *h, const RawOperands &op, int dt, long long products, int &cpc, int &nw);
+// Whether the dense rows take column windows (cpc columns, nw windows, per
+// slices of B per window: > 1 when each warp owns a slice).
+bool dense_windows(const smash_handle *h, const RawOperands &op, int dt, long long products, int &cpc, int &nw,
+                   int &per);
 
 }  // namespace host
 }  // namespace smash

@@ -152,7 +152,95 @@ __device__ __forceinline__ int nth_set_bit(unsigned x, int n) {
     return pos;
 }
 
-template <typename V, int NT>
+constexpr int kEnumUnroll = 4;   // steps of 32 products whose loads are issued together
+
+// Every product of A entries [ab, ae) whose column lies in slice op.slice of
+// the sliced B, enumerated by one warp: lane l of a batch of 32 entries holds
+// entry l's slice (start, length, a_ik), entries with an empty slice are
+// moved out of the way by shuffles, a scan lays the batch's products on one
+// line and each step hands 32 consecutive products to the 32 lanes (as in
+// the warp-row enumerator). f(act, j, a, b) is called by all 32 lanes together
+// once per step.
+template <typename V, typename F>
+__device__ __forceinline__ void slice_enum(const Operands<V> &op, int64_t ab, int64_t ae, int *err, F &&f) {
+    const int lane = lane_id();
+    for (int64_t base = ab; base < ae; base += 32) {
+        int len = 0;
+        int32_t bs = 0;
+        V av = V(0);
+        if (base + lane < ae) {
+            const int k = __ldg(op.a_ci + base + lane);
+            if ((unsigned)k < (unsigned)op.b_rows) {
+                const int32_t *w = op.b_woff + (size_t)k * (op.nslices + 1) + op.slice;
+                bs = w[0];
+                len = w[1] - bs;
+            } else {
+                raise_err(err, kErrBadIndex);
+            }
+            av = op.a_val[base + lane];
+        }
+        const unsigned nz = __ballot_sync(kFull, len > 0);
+        if (nz == 0u) continue;
+        const int nv = __popc(nz);
+        if (nv < 32 && nz != (1u << nv) - 1u) {
+            const int src = lane < nv ? nth_set_bit(nz, lane) : 0;
+            len = __shfl_sync(kFull, len, src);
+            bs = __shfl_sync(kFull, bs, src);
+            av = __shfl_sync(kFull, av, src);
+            if (lane >= nv) len = 0;
+        }
+        const int incl = warp_incl_scan(len);
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int32_t start = bs - (incl - len);   // product p of this entry reads B at start + p
+        for (int q0 = 0; q0 < total; q0 += 32 * kEnumUnroll) {
+            int jv[kEnumUnroll];
+            V a_u[kEnumUnroll], b_u[kEnumUnroll];
+            bool act[kEnumUnroll];
+#pragma unroll
+            for (int u = 0; u < kEnumUnroll; ++u) {
+                const int q = q0 + 32 * u;
+                act[u] = q + lane < total;
+                jv[u] = -1;
+                a_u[u] = V(0);
+                b_u[u] = V(0);
+                if (q < total) {
+                    const int c0 = __popc(__ballot_sync(kFull, incl <= q));
+                    const int e = incl - q;
+                    const unsigned ends = __reduce_or_sync(kFull, (e >= 1 && e <= 31) ? (1u << e) : 0u);
+                    const int ci = c0 + __popc(ends & ((2u << lane) - 1u));
+                    const int32_t st = __shfl_sync(kFull, start, ci);
+                    a_u[u] = __shfl_sync(kFull, av, ci);
+                    if (act[u]) {
+                        jv[u] = __ldg(op.b_ci + st + q + lane);
+                        b_u[u] = __ldg(op.b_val + st + q + lane);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kEnumUnroll; ++u) {
+                if (q0 + 32 * u < total) {
+                    bool ok = act[u];
+                    if (ok && (unsigned)jv[u] >= (unsigned)op.ncols) {
+                        raise_err(err, kErrBadIndex);
+                        ok = false;
+                    }
+                    f(ok, jv[u], a_u[u], b_u[u]);
+                }
+            }
+        }
+    }
+}
+
+// OWN (owner computes): warp q of the block owns the window's columns of
+// every kWarps-th group of 32 columns from group q on (B sliced by warp:
+// slices [w * kWarps, (w + 1) * kWarps) make up window w; interleaved, so
+// that columns crowded at one end of the window spread over all warps) and
+// adds its products with plain shared-memory read-modify-writes:
+// no other warp touches its columns, and lanes of one step that hit the same
+// column take turns (each writes its lane to the column's owner byte, the
+// lane that reads itself back adds; the others try again), so no atomic and
+// no compare-and-swap retry, and each product costs one add.
+template <typename V, int NT, bool OWN>
 __global__ void __launch_bounds__(NT) k_num_window(Operands<V> op, const int *rows, int count, int nw, int cpc,
                                                    int subs_per_win, WinCount wc, WinArena ar, NumOutT<V> out,
                                                    unsigned long long *token, int *err) {
@@ -167,6 +255,7 @@ __global__ void __launch_bounds__(NT) k_num_window(Operands<V> op, const int *ro
     V *acc = (V *)smem;
     unsigned *bm = (unsigned *)(smem + (size_t)cpc * sizeof(V));
     const ProdScratch<V> sc = carve_prod_scratch<V, NT>((unsigned char *)(bm + words));
+    unsigned char *own = (unsigned char *)(bm + words);   // OWN: owner byte of each column
     const int t = threadIdx.x;
     const int lane = lane_id();
     const int wp = t >> 5;
@@ -230,18 +319,41 @@ __global__ void __launch_bounds__(NT) k_num_window(Operands<V> op, const int *ro
         }
         const int lo = w * cpc;
         const int width = min(cpc, op.ncols - lo);
-        op.slice = w;
         int64_t ab = 0, ae = 0;
         a_row_range(op, i, ab, ae, err);
-        group_products<V, true, NT, NT>(op, ab, ae, sc, err, [&](int j, V a, V bkj) {
-            const unsigned off = (unsigned)(j - lo);
-            if (off < (unsigned)width) {
-                atomicAdd(acc + off, a * bkj);
-                const unsigned bit = 1u << (off & 31);
-                unsigned *bw = bm + (off >> 5);
-                if (!(*(volatile unsigned *)bw & bit)) atomicOr(bw, bit);
-            }
-        });
+        if constexpr (OWN) {
+            op.slice = w * kWarps + wp;
+            slice_enum<V>(op, ab, ae, err, [&](bool act, int j, V a, V bkj) {
+                const unsigned off = (unsigned)(j - lo);
+                bool pend = act && off < (unsigned)width && ((off >> 5) & (kWarps - 1)) == (unsigned)wp;
+                const V v = a * bkj;
+                while (__any_sync(kFull, pend)) {
+                    if (pend) own[off] = (unsigned char)lane;
+                    __syncwarp();
+                    const bool win = pend && own[off] == (unsigned char)lane;
+                    if (win) {
+                        acc[off] += v;
+                        const unsigned bit = 1u << (off & 31);
+                        unsigned *bw = bm + (off >> 5);
+                        if (!(*(volatile unsigned *)bw & bit)) atomicOr(bw, bit);
+                    }
+                    __syncwarp();
+                    pend = pend && !win;
+                }
+            });
+            __syncthreads();
+        } else {
+            op.slice = w;
+            group_products<V, true, NT, NT>(op, ab, ae, sc, err, [&](int j, V a, V bkj) {
+                const unsigned off = (unsigned)(j - lo);
+                if (off < (unsigned)width) {
+                    atomicAdd(acc + off, a * bkj);
+                    const unsigned bit = 1u << (off & 31);
+                    unsigned *bw = bm + (off >> 5);
+                    if (!(*(volatile unsigned *)bw & bit)) atomicOr(bw, bit);
+                }
+            });
+        }
         // write-out in chunks of 32 bitmap words (1024 columns): chunk totals,
         // their prefix, then every chunk's columns in order.
         const int wwords = (width + 31) >> 5;
@@ -647,17 +759,22 @@ int dense_bitmap_max_cols() {
 
 static int window_threads(int blocks_per_sm) { return blocks_per_sm <= 1 ? 1024 : blocks_per_sm == 2 ? 512 : 256; }
 
+// Accumulator, occupancy bitmap, then the product staging (atomic adds) or
+// the columns' owner bytes (owner computes).
 template <typename V, int NT>
-static size_t window_smem(int cpc) {
-    return (size_t)cpc * sizeof(V) + (size_t)(cpc / 32) * 4 + num_scratch_bytes<V, NT>();
+static size_t window_smem(int cpc, bool own) {
+    return (size_t)cpc * sizeof(V) + (size_t)(cpc / 32) * 4 + (own ? (size_t)cpc : num_scratch_bytes<V, NT>());
 }
 
 template <typename V>
-static size_t window_smem_nt(int cpc, int nt) {
-    return nt == 1024 ? window_smem<V, 1024>(cpc) : nt == 512 ? window_smem<V, 512>(cpc) : window_smem<V, 256>(cpc);
+static size_t window_smem_nt(int cpc, int nt, bool own) {
+    return nt == 1024 ? window_smem<V, 1024>(cpc, own)
+                      : nt == 512 ? window_smem<V, 512>(cpc, own) : window_smem<V, 256>(cpc, own);
 }
 
-int num_window_cols(int dtype, int blocks_per_sm) {
+int window_warps(int blocks_per_sm) { return window_threads(blocks_per_sm < 1 ? 1 : blocks_per_sm) / 32; }
+
+int num_window_cols(int dtype, int blocks_per_sm, bool own) {
     const int bps = blocks_per_sm < 1 ? 1 : blocks_per_sm;
     const int nt = window_threads(bps);
     // per-block budget: the SM's shared memory shared by bps blocks (1 KB
@@ -666,7 +783,7 @@ int num_window_cols(int dtype, int blocks_per_sm) {
     if (budget > max_smem_per_block() - 1024) budget = max_smem_per_block() - 1024;
     int best = 0;
     for (int cpc = kSubCols; cpc <= kMaxWinCols; cpc += kSubCols) {
-        const size_t need = dtype ? window_smem_nt<double>(cpc, nt) : window_smem_nt<float>(cpc, nt);
+        const size_t need = dtype ? window_smem_nt<double>(cpc, nt, own) : window_smem_nt<float>(cpc, nt, own);
         if ((long long)need <= budget) best = cpc;
     }
     return best;
@@ -676,6 +793,7 @@ template <typename V, int NT>
 static void num_window_go(Operands<V> op, const BSlices &sl, const int *rows, int count, unsigned long long *token,
                           const HashLaunch &hl, const WinCount &wc, const WinArena &ar, const NumOutT<V> &out,
                           int *err, cudaStream_t s) {
+    const bool own = sl.per_win > 1;   // one slice per warp: owner computes
     int cpc = sl.cpc;
     int subs = cpc / kSubCols;
     if (sl.nslices <= 1) {
@@ -687,13 +805,20 @@ static void num_window_go(Operands<V> op, const BSlices &sl, const int *rows, in
         op.b_woff = sl.woff;
         op.nslices = sl.nslices;
     }
-    const size_t smem = window_smem<V, NT>(cpc);
-    auto kern = k_num_window<V, NT>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int nw = sl.nslices <= 1 ? 1 : sl.nslices;
+    const int nw = sl.nslices <= 1 ? 1 : sl.nslices / sl.per_win;
     const long long items = (long long)count * nw;
-    const int grid = resident_grid(kern, NT, smem, hl.sms, items);
-    kern<<<grid, NT, smem, s>>>(op, rows, count, nw, cpc, subs, wc, ar, out, token, err);
+    const size_t smem = window_smem<V, NT>(cpc, own);
+    if (own) {
+        auto kern = k_num_window<V, NT, true>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int grid = resident_grid(kern, NT, smem, hl.sms, items);
+        kern<<<grid, NT, smem, s>>>(op, rows, count, nw, cpc, subs, wc, ar, out, token, err);
+    } else {
+        auto kern = k_num_window<V, NT, false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int grid = resident_grid(kern, NT, smem, hl.sms, items);
+        kern<<<grid, NT, smem, s>>>(op, rows, count, nw, cpc, subs, wc, ar, out, token, err);
+    }
 }
 
 template <typename V>

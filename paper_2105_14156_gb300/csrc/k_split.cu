@@ -10,7 +10,10 @@
 // every row of B is sorted by column the windows are contiguous already and
 // their bounds come from binary searches (B itself is the sliced copy);
 // otherwise the entries of each row are regrouped by window into a copy
-// (stable within a window).
+// (stable within a window). For the owner-computes dense kernel each window
+// is cut further into one slice per warp, slice q holding the columns of
+// every per-th group of 32 columns from group q on; those slices are always
+// regrouped into a copy.
 #include "device_common.cuh"
 #include "kernels.h"
 
@@ -35,10 +38,21 @@ __device__ __forceinline__ int window_of(int j, int cpc, int nw) {
     return w < nw ? w : nw - 1;
 }
 
+// Slice of column j: its window when per == 1; else one of the window's per
+// slices, each owning every per-th group of 32 columns of the window (so
+// that columns crowded at one end of a window spread over all slices).
+__device__ __forceinline__ int slice_of(int j, int cpc, int nw, int per) {
+    const int w = window_of(j, cpc, nw);
+    if (per == 1) return w;
+    const int off = j >= 0 ? j - w * cpc : 0;
+    return w * per + (((unsigned)off >> 5) % (unsigned)per);
+}
+
 // One warp per row of B: entries per window (shared counters per warp), then
 // their exclusive prefix -> woff[k][0..nw].
 __global__ void __launch_bounds__(kSplitNT) k_split_count(const int64_t *b_rp, const int32_t *b_ci, int64_t b_rows,
-                                                          int64_t b_nnz, int cpc, int nw, int32_t *woff) {
+                                                          int64_t b_nnz, int cpc, int nwin, int per, int32_t *woff) {
+    const int nw = nwin * per;   // slices
     extern __shared__ int s_cnt[];   // [kSplitWarps][nw]
     const int lane = lane_id();
     int *cnt = s_cnt + (threadIdx.x >> 5) * nw;
@@ -50,7 +64,7 @@ __global__ void __launch_bounds__(kSplitNT) k_split_count(const int64_t *b_rp, c
         b_row_ok(b_rp, k, b_nnz, s, t);
         for (int64_t e0 = s; e0 < t; e0 += 32) {
             const int64_t e = e0 + lane;
-            const int q = e < t ? window_of(__ldg(b_ci + e), cpc, nw) : -1;
+            const int q = e < t ? slice_of(__ldg(b_ci + e), cpc, nwin, per) : -1;
             const unsigned peers = __match_any_sync(kFull, q);
             if (e < t && (peers & lanemask_lt()) == 0) atomicAdd(cnt + q, __popc(peers));
         }
@@ -71,8 +85,10 @@ __global__ void __launch_bounds__(kSplitNT) k_split_count(const int64_t *b_rp, c
 // One warp per row of B: stable regrouping of the row's entries by window.
 template <typename V>
 __global__ void __launch_bounds__(kSplitNT) k_split_scatter(const int64_t *b_rp, const int32_t *b_ci, const V *b_val,
-                                                            int64_t b_rows, int64_t b_nnz, int cpc, int nw,
-                                                            const int32_t *woff, int32_t *out_ci, V *out_val) {
+                                                            int64_t b_rows, int64_t b_nnz, int cpc, int nwin,
+                                                            int per, const int32_t *woff, int32_t *out_ci,
+                                                            V *out_val) {
+    const int nw = nwin * per;   // slices
     extern __shared__ int s_cur[];   // [kSplitWarps][nw]
     const int lane = lane_id();
     int *cur = s_cur + (threadIdx.x >> 5) * nw;
@@ -90,7 +106,7 @@ __global__ void __launch_bounds__(kSplitNT) k_split_scatter(const int64_t *b_rp,
             if (valid) {
                 j = __ldg(b_ci + e);
                 v = b_val[e];
-                q = window_of(j, cpc, nw);
+                q = slice_of(j, cpc, nwin, per);
             }
             const unsigned peers = __match_any_sync(kFull, q);
             const int base = valid ? cur[q] : 0;
@@ -150,6 +166,9 @@ __global__ void __launch_bounds__(256) k_split_bsearch(const int64_t *b_rp, cons
     }
 }
 
+// The counting pass keeps one counter per slice and warp in shared memory.
+int window_plan_max_slices() { return (int)((size_t)max_smem_per_block() / (4 * kSplitWarps)) - 1; }
+
 size_t window_plan_bytes(const RawOperands &op, int nw, size_t vsz) {
     size_t b = 0;
     auto add = [&](size_t n) { b = ((b + 255) & ~size_t(255)) + n; };
@@ -162,10 +181,12 @@ size_t window_plan_bytes(const RawOperands &op, int nw, size_t vsz) {
     return b + 256;
 }
 
-int launch_window_plan(int dtype, const RawOperands &op, int nw, int cpc, void *ws, BSlices &sl, int sms,
-                       cudaStream_t s, int *host_word) {
+int launch_window_plan(int dtype, const RawOperands &op, int nwin, int per, int cpc, void *ws, BSlices &sl,
+                       int sms, cudaStream_t s, int *host_word) {
+    const int nw = nwin * per;   // slices
     sl.nslices = nw;
     sl.cpc = cpc;
+    sl.per_win = per;
     sl.woff = nullptr;
     sl.ci = nullptr;
     sl.val = nullptr;
@@ -186,13 +207,17 @@ int launch_window_plan(int dtype, const RawOperands &op, int nw, int cpc, void *
     const int64_t cap_blocks = (int64_t)sms * 8;
     const int64_t blocks = (op.b_rows + kSplitWarps - 1) / kSplitWarps;
     const int grid = (int)(blocks < cap_blocks ? blocks : cap_blocks);
-    // sorted rows of B need no copy
-    cudaMemsetAsync(unsorted, 0, sizeof(int), s);
-    k_check_sorted<<<grid, kSplitNT, 0, s>>>(op.b_rp, op.b_ci, op.b_rows, op.b_nnz, unsorted);
-    cudaMemcpyAsync(host_word, unsorted, sizeof(int), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
+    // sorted rows of B need no copy when each window is one slice
     sl.woff = woff;
-    if (*host_word == 0) {
+    int sorted = 0;
+    if (per == 1) {
+        cudaMemsetAsync(unsorted, 0, sizeof(int), s);
+        k_check_sorted<<<grid, kSplitNT, 0, s>>>(op.b_rp, op.b_ci, op.b_rows, op.b_nnz, unsorted);
+        cudaMemcpyAsync(host_word, unsorted, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        sorted = *host_word == 0;
+    }
+    if (sorted) {
         const int64_t pairs = op.b_rows * (int64_t)(nw + 1);
         const int64_t bb = (pairs + 255) / 256;
         k_split_bsearch<<<(int)(bb < cap_blocks ? bb : cap_blocks), 256, 0, s>>>(op.b_rp, op.b_ci, op.b_rows,
@@ -207,16 +232,16 @@ int launch_window_plan(int dtype, const RawOperands &op, int nw, int cpc, void *
         cudaFuncSetAttribute(k_split_scatter<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_split_scatter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
-    k_split_count<<<grid, kSplitNT, smem, s>>>(op.b_rp, op.b_ci, op.b_rows, op.b_nnz, cpc, nw, woff);
+    k_split_count<<<grid, kSplitNT, smem, s>>>(op.b_rp, op.b_ci, op.b_rows, op.b_nnz, cpc, nwin, per, woff);
     if (dtype)
         k_split_scatter<double><<<grid, kSplitNT, smem, s>>>(op.b_rp, op.b_ci, (const double *)op.b_val, op.b_rows,
-                                                              op.b_nnz, cpc, nw, woff, sci, (double *)sval);
+                                                              op.b_nnz, cpc, nwin, per, woff, sci, (double *)sval);
     else
         k_split_scatter<float><<<grid, kSplitNT, smem, s>>>(op.b_rp, op.b_ci, (const float *)op.b_val, op.b_rows,
-                                                             op.b_nnz, cpc, nw, woff, sci, (float *)sval);
+                                                             op.b_nnz, cpc, nwin, per, woff, sci, (float *)sval);
     sl.ci = sci;
     sl.val = sval;
-    return 3;
+    return per == 1 ? 3 : 2;
 }
 
 }  // namespace smash

@@ -218,20 +218,26 @@ void launch_num_tiny(int dtype, const RawOperands &op, const int *rows, int coun
 // window of cpc columns; woff[B.rows][nslices+1] (nslices > 1 only).
 struct BSlices {
     int nslices = 0;
-    int cpc = 0;
+    int cpc = 0;        // columns of a window
+    int per_win = 1;    // slices per window (> 1: one per warp, owner computes; nslices = windows * per_win)
     const int32_t *woff = nullptr;
     const int32_t *ci = nullptr;
     const void *val = nullptr;
 };
 size_t window_plan_bytes(const RawOperands &op, int nw, size_t vsz);
+// Most slices of B the slicing pass supports.
+int window_plan_max_slices();
 // host_word: pinned host int (the sortedness of B is read back). Returns the
 // number of kernels launched.
-int launch_window_plan(int dtype, const RawOperands &op, int nw, int cpc, void *ws, BSlices &sl, int sms,
+// nw windows of cpc columns, per slices per window (1: the window itself).
+int launch_window_plan(int dtype, const RawOperands &op, int nw, int per, int cpc, void *ws, BSlices &sl, int sms,
                        cudaStream_t s, int *host_word);
 // Widest column window (a multiple of kSubCols, at most kMaxWinCols) of the
 // numeric dense kernel at `blocks_per_sm` resident blocks per SM; 0: none.
 constexpr int kMaxWinCols = 65536;
-int num_window_cols(int dtype, int blocks_per_sm);
+int num_window_cols(int dtype, int blocks_per_sm, bool own);
+// Warps of a block of the numeric dense kernel at blocks_per_sm blocks per SM.
+int window_warps(int blocks_per_sm);
 // Arena mode of the dense kernel (learned path, capacity mode): no counts;
 // each (row, window) item reserves room for its columns in one arena by an
 // atomic add on *top, writes them there in order and records (offset, count)

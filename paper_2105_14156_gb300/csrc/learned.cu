@@ -490,8 +490,8 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
     //    predicted capacities; the other rows get staging ranges
     const int nd = bp.counts[kBinDense];
     const int *drows = pl.bb.rows + bp.offsets[kBinDense];   // valid until the next plan_buffers()
-    int cpc = 0, nw = 0;
-    const bool use_arena = nd > 0 && dense_windows(h, op, dt, bp.sums[16 + kBinDense], cpc, nw);
+    int cpc = 0, nw = 0, per = 1;
+    const bool use_arena = nd > 0 && dense_windows(h, op, dt, bp.sums[16 + kBinDense], cpc, nw, per);
     WinArena ar;
     const int *arena_rows = nullptr;
     if (use_arena) {

@@ -90,7 +90,8 @@ class Params(ctypes.Structure):
                 ("spill_blocks_per_sm", ctypes.c_int32), ("sym_dense_ratio", ctypes.c_int32),
                 ("dense_blocks", ctypes.c_int32), ("sym_dense_blocks", ctypes.c_int32),
                 ("warp_rows", ctypes.c_int32), ("bulk_copy", ctypes.c_int32), ("group_rows", ctypes.c_int32),
-                ("row_window", ctypes.c_int32), ("row_window_tbits", ctypes.c_int32)]
+                ("row_window", ctypes.c_int32), ("row_window_tbits", ctypes.c_int32),
+                ("dense_owner", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

@@ -218,7 +218,8 @@ def test_learned_row_windows(handle, trained, margin, values):
 
 @pytest.mark.parametrize("margin", [0.15, -0.9, 3.0])
 @pytest.mark.parametrize("dense_blocks", [2, 4])
-def test_learned_dense_rows_in_arena(handle, trained, margin, dense_blocks):
+@pytest.mark.parametrize("owner", [0, 1])
+def test_learned_dense_rows_in_arena(handle, trained, margin, dense_blocks, owner):
     """Dense rows of the learned path: column-window items write into the arena
     (several windows per row); an arena too small for them (margin -0.9) sends
     the rows to the exact fallback."""
@@ -228,7 +229,7 @@ def test_learned_dense_rows_in_arena(handle, trained, margin, dense_blocks):
     A = random_csr(300, 200, 0.1, 81, values="f64")
     B = random_csr(200, 30000, 0.01, 82, values="f64")
     defaults = handle.params.as_dict()
-    handle.set_params(dense_ratio=1 << 20, dense_blocks=dense_blocks)
+    handle.set_params(dense_ratio=1 << 20, dense_blocks=dense_blocks, dense_owner=owner)
     try:
         C, stats, owner = handle.spgemm_learned(smash.to_device(A), smash.to_device(B), model, margin=margin)
         Ch = C.to_host()

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 DEFAULT = dict(hash_kind=1, max_load=0.5, sym_max_tbits=15, num_max_tbits=14, group_shift=4, dense_ratio=4,
                bitmap_ratio=4, spill_blocks_per_sm=1, sym_dense_ratio=64, dense_blocks=0,
-               sym_dense_blocks=0, warp_rows=1, bulk_copy=0, group_rows=0, row_window=0, row_window_tbits=6)
+               sym_dense_blocks=0, warp_rows=1, bulk_copy=0, group_rows=0, row_window=16, row_window_tbits=7, dense_owner=0)
 
 # Parameter sets that force each path.
 PATHS = {
@@ -31,6 +31,8 @@ PATHS = {
     "dense_counted_in_numeric": dict(dense_ratio=1 << 20, sym_dense_ratio=0),
     "dense_two_blocks_per_sm": dict(dense_ratio=1 << 20, dense_blocks=2),
     "dense_one_block_per_sm": dict(dense_ratio=1 << 20, dense_blocks=1),
+    "dense_owner_computes": dict(dense_ratio=1 << 20, dense_owner=1),
+    "dense_owner_four_blocks_per_sm": dict(dense_ratio=1 << 20, dense_owner=1, dense_blocks=4, num_max_tbits=5),
     "symbolic_dense_one_block_per_sm": dict(sym_dense_ratio=1 << 20, sym_dense_blocks=1),
     "symbolic_dense_eight_blocks_per_sm": dict(sym_dense_ratio=1 << 20, sym_dense_blocks=8),
     "group_per_row": dict(group_shift=0),
@@ -38,6 +40,7 @@ PATHS = {
     "bulk_copy_out": dict(bulk_copy=1),
     "group_rows_listed": dict(group_rows=1),
     "warp_rows_wide": dict(group_shift=6),
+    "no_row_windows": dict(row_window=0),
     "row_windows": dict(row_window=16),
     "row_windows_wide": dict(row_window=32, row_window_tbits=8),
     "row_windows_high_bits": dict(row_window=8, hash_kind=2),
@@ -171,17 +174,37 @@ def test_congruent_columns_defeat_low_bits(handle):
 @pytest.mark.parametrize("ncols,dense_blocks", [(3000, 1), (20000, 1), (40000, 1), (110000, 1), (110000, 4),
                                                 (40000, 2), (70001, 4)])
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
-def test_dense_rows_windows(handle, ncols, dense_blocks, dtype):
+@pytest.mark.parametrize("owner", [0, 1])
+def test_dense_rows_windows(handle, ncols, dense_blocks, dtype, owner):
     """Dense rows split into one or many column windows (the last one ragged),
-    at 1, 2 or 4 blocks per SM (wider or narrower windows)."""
+    at 1, 2 or 4 blocks per SM (wider or narrower windows), merged by atomic
+    adds or by the warps that own the columns (many products per column: lanes
+    of one step often hit the same column)."""
     A = random_csr(96, 64, 0.3, 51, values=dtype)
     B = random_csr(64, ncols, 800.0 / ncols, 52, values=dtype)
-    C = run(handle, A, B, dense_ratio=1 << 20, dense_blocks=dense_blocks)
+    C = run(handle, A, B, dense_ratio=1 << 20, dense_blocks=dense_blocks, dense_owner=owner)
     assert_matches_oracle(C, A, B)
 
 
+@pytest.mark.parametrize("dense_blocks", [1, 2, 4])
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
-def test_dense_windows_zero_values_and_cancellations(handle, dtype):
+def test_dense_owner_unsorted_duplicate_b(handle, dense_blocks, dtype):
+    """Owner-computes windows over a B whose rows are unsorted and repeat
+    columns (B regrouped by warp slice; equal columns of one row of B land in
+    the same step), and small-integer values that must sum exactly."""
+    A = random_csr(80, 64, 0.3, 151, values=dtype)
+    B = random_csr(64, 30000, 0.03, 152, values=dtype, sort_cols=False, dup_frac=0.3)
+    C = run(handle, A, B, dense_ratio=1 << 20, dense_blocks=dense_blocks, dense_owner=1)
+    assert_matches_oracle(C, A, B)
+    Ai = random_csr(80, 64, 0.3, 153, values="int")
+    Bi = random_csr(64, 30000, 0.03, 154, values="int", sort_cols=False, dup_frac=0.3)
+    Ci = run(handle, Ai, Bi, dense_ratio=1 << 20, dense_blocks=dense_blocks, dense_owner=1)
+    assert_matches_oracle(Ci, Ai, Bi, exact=True)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("owner", [0, 1])
+def test_dense_windows_zero_values_and_cancellations(handle, dtype, owner):
     """Window columns whose products are all zero (+0.0 or -0.0) or cancel
     exactly keep their entries: the structure comes from which columns were
     hit, never from the values."""
@@ -191,7 +214,7 @@ def test_dense_windows_zero_values_and_cancellations(handle, dtype):
     for M, seed in ((A, 57), (B, 58)):
         idx = np.random.default_rng(seed).integers(0, 4, M.val.size)
         M.val[:] = pick[idx].astype(M.val.dtype)
-    C = run(handle, A, B, dense_ratio=1 << 20, dense_blocks=2)
+    C = run(handle, A, B, dense_ratio=1 << 20, dense_blocks=2, dense_owner=owner)
     assert_matches_oracle(C, A, B)
     # every C entry whose products are all zero is still present
     assert np.sum(C.val == 0) > 0
