@@ -545,7 +545,7 @@ int run_bins(smash_handle *h, const RawOperands &op, int64_t n, int dt, const Nu
                 LaunchTimer lt(h, bs, "num_warp", b, 128, counts[b], sums[b], sums[16 + b], sums[32 + b]);
                 launch_num_warp(dt, op, rows, counts[b], tok, hl, rule.inv_load, kept, h->params.bulk_copy, out, err,
                                 bs);
-            } else if (use_group_rows(h, hl, dt)) {
+            } else if (op.b_nnz < INT_MAX && use_group_rows(h, hl, dt)) {
                 LaunchTimer lt(h, bs, "num_group", b, group_threads(hl), counts[b], sums[b], sums[16 + b],
                                sums[32 + b]);
                 launch_num_group(dt, op, rows, counts[b], tok, hl, rule.inv_load, kept, out, err, bs);

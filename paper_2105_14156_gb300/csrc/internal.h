@@ -594,7 +594,7 @@ inline int group_threads(const HashLaunch &hl) {
 }
 
 // Whether a bin of tables of 2^hl.tbits slots runs the register-enumerating
-// warp-row kernel (k_warp.cu): one warp per row, and its shared memory fits.
+// warp-row kernel (k_warp.cuh): one warp per row, and its shared memory fits.
 // dtype < 0: the symbolic phase.
 inline bool use_warp_rows(const smash_handle *h, const HashLaunch &hl, int dtype) {
     if (!h->params.warp_rows || group_threads(hl) != 32) return false;
@@ -602,7 +602,7 @@ inline bool use_warp_rows(const smash_handle *h, const HashLaunch &hl, int dtype
     return need <= (size_t)max_smem_per_block();
 }
 
-// Whether a bin runs the numeric group-row kernel (k_group.cu): a block of
+// Whether a bin runs the numeric group-row kernel (k_group.cuh): a block of
 // 64 or more threads per row, and its shared memory fits.
 inline bool use_group_rows(const smash_handle *h, const HashLaunch &hl, int dtype) {
     if (!h->params.group_rows || group_threads(hl) < 64) return false;

@@ -1,7 +1,7 @@
 // Group rows: one block of GS threads (64 to 1024) per row of C, for the bins
 // whose tables hold a thousand columns or more.
 //
-// The numeric phase of the warp rows (k_warp.cu), with the row's products
+// The numeric phase of the warp rows (k_warp.cuh), with the row's products
 // spread over the block's warps (group_enum in warp_enum.cuh: a batch of A's
 // entries staged in shared memory, one contiguous range of the batch's
 // products per warp). Each product is inserted with compare-and-swap first
@@ -13,6 +13,10 @@
 // Rows known to repeat no column (exact mode) or whose products fit their
 // capacity (capacity mode) skip the table: their products are staged as
 // they come, sorted the same way, and equal columns summed after the sort.
+//
+// Included by k_group_f32.cu and k_group_f64.cu, one value type each (two
+// translation units compiled side by side).
+#pragma once
 #include <climits>
 
 #include "device_common.cuh"
@@ -293,7 +297,7 @@ static int group_threads_of(int tbits, int shift) {
 }
 
 template <typename V>
-static size_t group_smem_gs(int tbits, int L, int gs) {
+[[maybe_unused]] static size_t group_smem_gs(int tbits, int L, int gs) {
     const int T = 1 << tbits, NB = T >> 1;
     switch (gs) {
         case 64: return group_row_bytes<V, 64>(T, L, NB);
@@ -302,13 +306,6 @@ static size_t group_smem_gs(int tbits, int L, int gs) {
         case 512: return group_row_bytes<V, 512>(T, L, NB);
         default: return group_row_bytes<V, 1024>(T, L, NB);
     }
-}
-
-size_t num_group_smem(int dtype, int tbits, float inv_load, int group_shift) {
-    const int gs = group_threads_of(tbits, group_shift);
-    const int L = group_lcap(tbits, inv_load, gs);
-    if (gs < 64 || L > 16 * gs) return SIZE_MAX;   // (one row per block, at most 16 entries per thread)
-    return dtype ? group_smem_gs<double>(tbits, L, gs) : group_smem_gs<float>(tbits, L, gs);
 }
 
 template <typename V, typename IT, int K, int GS>
@@ -358,15 +355,8 @@ static void num_group_typed(const RawOperands &r, const int *rows, int count, in
     const int gs = group_threads_of(hl.tbits, hl.group_shift);
     const int L = group_lcap(hl.tbits, inv_load, gs);
     const size_t smem = num_group_smem(sizeof(V) == 8, hl.tbits, inv_load, hl.group_shift);
-    if (r.b_nnz < INT_MAX) num_group_gs<V, int32_t>(op, rows, count, token, hl, L, gs, rec, out, err, s, smem);
-    else num_group_gs<V, int64_t>(op, rows, count, token, hl, L, gs, rec, out, err, s, smem);
-}
-
-void launch_num_group(int dtype, const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
-                      float inv_load, const RowGather *rec, const NumOut &out, int *err, cudaStream_t s) {
-    if (count <= 0) return;
-    if (dtype) num_group_typed<double>(r, rows, count, token, hl, inv_load, rec, out, err, s);
-    else num_group_typed<float>(r, rows, count, token, hl, inv_load, rec, out, err, s);
+    // (B with 2^31 entries or more takes the staged kernel: the planner checks)
+    num_group_gs<V, int32_t>(op, rows, count, token, hl, L, gs, rec, out, err, s, smem);
 }
 
 }  // namespace smash

@@ -14,6 +14,11 @@
 // counting sort by the high bits of the column groups them by bucket in the
 // table's own memory, each entry's rank inside its bucket gives its place, and
 // the row streams to C in column order.
+//
+// Included by k_warp_f32.cu (the symbolic kernel, float values, the launch
+// entries) and k_warp_f64.cu (double values): two translation units
+// compiled side by side.
+#pragma once
 #include <climits>
 
 #include "device_common.cuh"
@@ -98,7 +103,10 @@ __host__ __device__ constexpr size_t warp_row_bytes(int T, int L, int NB) {
 // staged the same way and its equal columns are summed after the sort
 // (expand, sort, merge): cheaper than hashing when few columns repeat, which
 // is what such a capacity says.
-template <typename V, typename IT, int K, int NW>
+// MODE: 0 exact mode, 1 capacity mode, 2 either, with the bulk copy-out and
+// the Version 1 write-back available (the first two leave out the code the
+// mode cannot reach: a smaller kernel, fewer instruction-cache misses).
+template <typename V, typename IT, int K, int NW, int MODE>
 __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int *rows, int count, int *token,
                                                       int tbits, HashCfg hc, int lcap, int nb, int bsh,
                                                       const RowGather *rec, int bulk, NumOutT<V> out, int *err) {
@@ -136,8 +144,9 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
         // capacity (the size model sees few repeated columns); its products
         // are staged as they are and equal columns summed after the sort.
         const long long f_i = rec && ok ? rec[i].f : -1;
-        const bool direct = !out.row_nnz && f_i >= 0 && n_exp <= lcap && f_i == (long long)n_exp;
-        const bool merge = out.row_nnz && f_i >= 0 && f_i <= (long long)n_exp && f_i <= lcap && 2 * f_i <= T;
+        const bool cap = MODE == 1 || (MODE == 2 && out.row_nnz != nullptr);
+        const bool direct = !cap && f_i >= 0 && n_exp <= lcap && f_i == (long long)n_exp;
+        const bool merge = cap && f_i >= 0 && f_i <= (long long)n_exp && f_i <= lcap && 2 * f_i <= T;
         if (direct || merge) {
             warp_enum<V, IT, true>(op, ab, ae, es, err, [&](bool act, int j, V a, V b, int p) {
                 if (act && p < lcap) {
@@ -166,7 +175,7 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
         full = __any_sync(kFull, full);
         const int tot = cnt;
         bool over;
-        if (out.row_nnz) {
+        if (cap) {
             over = full || tot > n_exp || tot > lcap;
             // (a merged row's length is known after the merge)
             if (lane == 0 && (over || !merge)) out.row_nnz[i] = over ? -1 : tot;
@@ -290,7 +299,7 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
                 keys[q] = kEmpty;
                 vals[q] = V(0);
             }
-        } else if (hc.kind == 2 && !direct) {
+        } else if (MODE == 2 && hc.kind == 2 && !direct) {
             // Version 1's write-back: the order-preserving hash (the high bits
             // of the column) leaves the table almost sorted in slot order, so
             // the occupied slots are compacted in order (in place: a chunk is
@@ -407,7 +416,7 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
             //    array, the ragged ends by the lanes that hold them (Version 3's
             //    bulk copy-out); otherwise every lane stores its entries
             constexpr int UK = 4, UV = 16 / (int)sizeof(V);
-            if (bulk && tot + UK <= T) {
+            if (MODE == 2 && bulk && tot + UK <= T) {
                 int pos[K];
 #pragma unroll
                 for (int x = 0; x < K; ++x) {
@@ -478,7 +487,7 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
             for (int s = lane; s < NB; s += 32) bc[s] = 0;
         __syncwarp();
     }
-    if (bulk && lane == 0) bulk_wait_all();
+    if (MODE == 2 && bulk && lane == 0) bulk_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -508,29 +517,6 @@ static int warp_grid(K kernel, size_t smem, int sms, int count) {
     return (int)(want < cap ? want : cap);
 }
 
-size_t sym_warp_smem(int tbits) {
-    return (size_t)kWarpRowWarps * (((size_t)4 << tbits) + sizeof(EntryScratch<float>));
-}
-
-void launch_sym_warp(const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
-                     int *nnz_out, int *err, cudaStream_t s) {
-    if (count <= 0) return;
-    const Operands<float> op = warp_operands<float>(r);
-    const size_t smem = sym_warp_smem(hl.tbits);
-    const HashCfg hc{hl.hash_kind, hl.colbits};
-    if (r.b_nnz < INT_MAX) {
-        auto kern = k_sym_warp<int32_t, kWarpRowWarps>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<warp_grid(kern, smem, hl.sms, count), kWarpRowWarps * 32, smem, s>>>(op, rows, count, token,
-                                                                                  hl.tbits, hc, nnz_out, err);
-    } else {
-        auto kern = k_sym_warp<int64_t, kWarpRowWarps>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<warp_grid(kern, smem, hl.sms, count), kWarpRowWarps * 32, smem, s>>>(op, rows, count, token,
-                                                                                  hl.tbits, hc, nnz_out, err);
-    }
-}
-
 // List room L: the most columns a row of the bin may hold (T * max_load,
 // rounded up to 32, at most T); NB = T / 2 buckets over the column range.
 static int warp_lcap(int tbits, float inv_load) {
@@ -540,16 +526,7 @@ static int warp_lcap(int tbits, float inv_load) {
     return L < 32 ? 32 : (L > T ? T : L);
 }
 
-static int warp_buckets(int tbits) { return (1 << tbits) >> 1; }
-
-size_t num_warp_smem(int dtype, int tbits, float inv_load) {
-    const int T = 1 << tbits;
-    const int L = warp_lcap(tbits, inv_load);
-    if (L > kWarpMaxList) return SIZE_MAX;   // more entries than the write-out's registers hold
-    const int NB = warp_buckets(tbits);
-    const size_t per = dtype ? warp_row_bytes<double>(T, L, NB) : warp_row_bytes<float>(T, L, NB);
-    return (size_t)kWarpRowWarps * per;
-}
+[[maybe_unused]] static int warp_buckets(int tbits) { return (1 << tbits) >> 1; }
 
 template <typename V, typename IT, int K>
 static void num_warp_go(const Operands<V> &op, const int *rows, int count, int *token, const HashLaunch &hl,
@@ -562,7 +539,9 @@ static void num_warp_go(const Operands<V> &op, const int *rows, int count, int *
     // bulk copies need 16-byte aligned destinations: C's arrays must start
     // on a 16-byte boundary (the row offsets are handled in the kernel)
     const int bulk = (bulk_copy && (uintptr_t)out.c_ci % 16 == 0 && (uintptr_t)out.c_val % 16 == 0) ? 1 : 0;
-    auto kern = k_num_warp<V, IT, K, kWarpRowWarps>;
+    const int mode = (bulk || hl.hash_kind == 2) ? 2 : out.row_nnz ? 1 : 0;
+    auto kern = mode == 0 ? k_num_warp<V, IT, K, kWarpRowWarps, 0>
+              : mode == 1 ? k_num_warp<V, IT, K, kWarpRowWarps, 1> : k_num_warp<V, IT, K, kWarpRowWarps, 2>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const HashCfg hc{hl.hash_kind, hl.colbits};
     kern<<<warp_grid(kern, smem, hl.sms, count), kWarpRowWarps * 32, smem, s>>>(op, rows, count, token, hl.tbits, hc,
@@ -590,14 +569,6 @@ static void num_warp_typed(const RawOperands &r, const int *rows, int count, int
     const size_t smem = num_warp_smem(sizeof(V) == 8, hl.tbits, inv_load);
     if (r.b_nnz < INT_MAX) num_warp_k<V, int32_t>(op, rows, count, token, hl, L, rec, bulk_copy, out, err, s, smem);
     else num_warp_k<V, int64_t>(op, rows, count, token, hl, L, rec, bulk_copy, out, err, s, smem);
-}
-
-void launch_num_warp(int dtype, const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
-                     float inv_load, const RowGather *rec, int bulk_copy, const NumOut &out, int *err,
-                     cudaStream_t s) {
-    if (count <= 0) return;
-    if (dtype) num_warp_typed<double>(r, rows, count, token, hl, inv_load, rec, bulk_copy, out, err, s);
-    else num_warp_typed<float>(r, rows, count, token, hl, inv_load, rec, bulk_copy, out, err, s);
 }
 
 }  // namespace smash

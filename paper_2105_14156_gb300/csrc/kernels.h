@@ -166,7 +166,7 @@ struct NumOut {
 void launch_num_hash(int dtype, const RawOperands &op, const int *rows, int count, int *token,
                      const HashLaunch &hl, float inv_load, int bitmap_ratio, const NumOut &out, int *err,
                      cudaStream_t s);
-// Warp rows (k_warp.cu): one warp per row, products enumerated from
+// Warp rows (k_warp.cuh): one warp per row, products enumerated from
 // registers, compare-and-swap-first probing, list-driven write-out. The
 // *_smem functions give the dynamic shared memory of one block.
 size_t sym_warp_smem(int tbits);
@@ -179,7 +179,7 @@ void launch_sym_warp(const RawOperands &op, const int *rows, int count, int *tok
 void launch_num_warp(int dtype, const RawOperands &op, const int *rows, int count, int *token,
                      const HashLaunch &hl, float inv_load, const RowGather *rec, int bulk_copy, const NumOut &out,
                      int *err, cudaStream_t s);
-// Group rows (k_group.cu): a block of 64-1024 threads per row, the numeric
+// Group rows (k_group.cuh): a block of 64-1024 threads per row, the numeric
 // phase of the warp rows spread over the block's warps.
 size_t num_group_smem(int dtype, int tbits, float inv_load, int group_shift);
 void launch_num_group(int dtype, const RawOperands &op, const int *rows, int count, int *token,

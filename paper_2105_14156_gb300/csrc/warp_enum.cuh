@@ -1,5 +1,5 @@
 // Register-staged product enumeration of one warp and compare-and-swap-first
-// insertion, shared by the warp-row kernels (k_warp.cu) and the batched
+// insertion, shared by the warp-row kernels (k_warp.cuh) and the batched
 // kernel (k_batched.cu).
 //
 // Lane l of each batch of 32 entries of A_i holds entry l (where the row of B
