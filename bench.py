@@ -312,9 +312,9 @@ def kernel_bytes(t, vb, nnz_b, total_products):
     B's bytes shared out over the launch groups by their products."""
     rows, a_nnz, prods, c_nnz = t["rows"], t["a_nnz"], t["products"], t["c_nnz"]
     share = prods / total_products if total_products else 0.0
-    if t["name"] in ("sym_hash", "sym_warp", "sym_tiny", "sym_dense", "sym_spill", "num_dense_count"):
+    if t["name"] in ("sym_hash", "sym_warp", "sym_rowwin", "sym_tiny", "sym_dense", "sym_spill", "num_dense_count"):
         return 12 * rows + 4 * a_nnz + 4 * nnz_b * share
-    if t["name"] in ("num_hash", "num_warp", "num_group", "num_tiny", "num_spill", "num_dense_window"):
+    if t["name"] in ("num_hash", "num_warp", "num_rowwin", "num_group", "num_tiny", "num_spill", "num_dense_window"):
         return 16 * rows + (4 + vb) * (a_nnz + c_nnz) + (4 + vb) * nnz_b * share
     return None
 
