@@ -204,8 +204,8 @@ __global__ void __launch_bounds__(GS) k_num_group(Operands<V> op, const int *row
 #pragma unroll
                 for (int x = 0; x < K; ++x) {
                     if (t + GS * x < tot) {
-                        out.c_ci[c0 + pp[x]] = kk[x];
-                        out.c_val[c0 + pp[x]] = vv[x];
+                        __stcs(out.c_ci + (c0 + pp[x]), kk[x]);
+                        __stcs(out.c_val + (c0 + pp[x]), vv[x]);
                     }
                 }
                 __syncthreads();
@@ -242,8 +242,8 @@ __global__ void __launch_bounds__(GS) k_num_group(Operands<V> op, const int *row
                         if (first) {
                             V v = vals[tot + q];
                             for (int y = q + 1; y < tot && keys[tot + y] == sk; ++y) v += vals[tot + y];
-                            out.c_ci[c0 + d] = sk;
-                            out.c_val[c0 + d] = v;
+                            __stcs(out.c_ci + (c0 + d), sk);
+                            __stcs(out.c_val + (c0 + d), v);
                         }
                         run_tot += ct;
                     }

@@ -417,8 +417,8 @@ __global__ void __launch_bounds__(NT) k_num_window(Operands<V> op, const int *ro
                         acc[col] = V(0);
                         const int64_t pos = cb + pre + __popc(wq & lanemask_lt());
                         if (ok) {
-                            dst_ci[pos] = lo + col;
-                            dst_val[pos] = v;
+                            __stcs(dst_ci + (pos), lo + col);
+                            __stcs(dst_val + (pos), v);
                         }
                     }
                 }
@@ -440,8 +440,8 @@ __global__ void __launch_bounds__(NT) k_num_window(Operands<V> op, const int *ro
                         const V v = acc[col];
                         acc[col] = V(0);
                         if (ok) {
-                            dst_ci[cb + o] = lo + col;
-                            dst_val[cb + o] = v;
+                            __stcs(dst_ci + (cb + o), lo + col);
+                            __stcs(dst_val + (cb + o), v);
                         }
                     }
                 }
@@ -591,8 +591,8 @@ __global__ void __launch_bounds__(NT) k_num_spill(Operands<V> op, const int *row
                             const long long pos =
                                 done + pre[d >> 5] + __popc(bm[d >> 5] & ((1u << (d & 31)) - 1u));
                             if (pos < n_exp) {
-                                out.c_ci[c0 + pos] = k[u];
-                                out.c_val[c0 + pos] = v[u];
+                                __stcs(out.c_ci + (c0 + pos), k[u]);
+                                __stcs(out.c_val + (c0 + pos), v[u]);
                             }
                         }
                     }

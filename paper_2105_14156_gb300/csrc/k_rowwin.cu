@@ -441,8 +441,8 @@ __global__ void __launch_bounds__(NW * 32) k_num_rowwin(Operands<V> op, const in
                 const int r = k >> rw.cb;
                 if (mt.rok[r]) {
                     const int64_t g = mt.rbase[r] + pp[x];
-                    out.c_ci[g] = k & cmask;
-                    out.c_val[g] = v;
+                    __stcs(out.c_ci + (g), k & cmask);
+                    __stcs(out.c_val + (g), v);
                 }
             }
         }

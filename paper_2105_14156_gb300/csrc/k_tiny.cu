@@ -165,8 +165,8 @@ __global__ void __launch_bounds__(NT) k_num_tiny(Operands<V> op, const int *rows
             continue;
         }
         for (int x = 0; x < n; ++x) {
-            out.c_ci[c0 + x] = keys[x * NT];
-            out.c_val[c0 + x] = vals[x * NT];
+            __stcs(out.c_ci + (c0 + x), keys[x * NT]);
+            __stcs(out.c_val + (c0 + x), vals[x * NT]);
         }
     }
 }

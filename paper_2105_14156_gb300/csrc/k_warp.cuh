@@ -288,8 +288,8 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
                     V v = vals[tot + q];
                     for (int y = q + 1; y < tot && keys[tot + y] == sk; ++y) v += vals[tot + y];
                     const int d = run_tot + __popc(m & lanemask_lt());
-                    out.c_ci[c0 + d] = sk;
-                    out.c_val[c0 + d] = v;
+                    __stcs(out.c_ci + (c0 + d), sk);
+                    __stcs(out.c_val + (c0 + d), v);
                 }
                 run_tot += __popc(m);
             }
@@ -339,8 +339,8 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
                 quiet = __any_sync(kFull, swapped) ? 0 : quiet + 1;
             }
             for (int q = lane; q < tot; q += 32) {
-                out.c_ci[c0 + q] = keys[q];
-                out.c_val[c0 + q] = vals[q];
+                __stcs(out.c_ci + (c0 + q), keys[q]);
+                __stcs(out.c_val + (c0 + q), vals[q]);
             }
             __syncwarp();
             for (int s0 = lane; s0 < T; s0 += 32) {
@@ -361,8 +361,8 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
             int rank = 0;
             for (int m = 0; m < tot; ++m) rank += __shfl_sync(kFull, k, m) < k ? 1 : 0;
             if (lane < tot) {
-                out.c_ci[c0 + rank] = k;
-                out.c_val[c0 + rank] = v;
+                __stcs(out.c_ci + (c0 + rank), k);
+                __stcs(out.c_val + (c0 + rank), v);
             }
         } else {
             // 1. the entries into registers, their slots back to EMPTY / 0,
@@ -454,8 +454,8 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
                 for (int x = 0; x < K; ++x) {
                     if (pos[x] >= 0) {
                         const int64_t g = c0 + pos[x];
-                        if (g < gk0 || g >= gk1) out.c_ci[g] = kk[x];
-                        if (g < gv0 || g >= gv1) out.c_val[g] = vv[x];
+                        if (g < gk0 || g >= gk1) __stcs(out.c_ci + (g), kk[x]);
+                        if (g < gv0 || g >= gv1) __stcs(out.c_val + (g), vv[x]);
                     }
                 }
                 if (lane == 0) bulk_wait_read();
@@ -469,8 +469,8 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
                         const int s0 = b ? bc[b - 1] : 0;
                         int rk = 0;
                         for (int y = s0; y < e; ++y) rk += keys[y] < kk[x] ? 1 : 0;
-                        out.c_ci[c0 + s0 + rk] = kk[x];
-                        out.c_val[c0 + s0 + rk] = vv[x];
+                        __stcs(out.c_ci + (c0 + s0 + rk), kk[x]);
+                        __stcs(out.c_val + (c0 + s0 + rk), vv[x]);
                     }
                 }
                 __syncwarp();

@@ -9,6 +9,10 @@
 
 namespace smash {
 
+// Entries of C are written once and not read again by the kernels, so they
+// go out with streaming stores (__stcs: evicted from L2 first), which leaves
+// L2 to the rows of B that the products gather.
+//
 // Output of a numeric launch. Exact mode (row_nnz == nullptr): c_rp is C's
 // row pointer and every row must have exactly c_rp[i+1]-c_rp[i] entries.
 // Capacity mode (learned sizing): c_rp gives each row a capacity; a row that
@@ -62,8 +66,8 @@ __device__ __forceinline__ void writeout_warp_rank(int *keys, V *vals, int T, in
     int rank = 0;
     for (int m = 0; m < tot; ++m) rank += (__shfl_sync(kFull, k, m) < k) ? 1 : 0;
     if (lane < tot && rank < n_exp) {
-        out.c_ci[c0 + rank] = k;
-        out.c_val[c0 + rank] = v;
+        __stcs(out.c_ci + (c0 + rank), k);
+        __stcs(out.c_val + (c0 + rank), v);
     }
     __syncwarp();
 }
@@ -114,8 +118,8 @@ __device__ __forceinline__ void writeout_bitonic(int *keys, V *vals, int T, int 
     }
     const int nw = n < n_exp ? n : n_exp;
     for (int s = t; s < nw; s += GS) {
-        out.c_ci[c0 + s] = keys[s];
-        out.c_val[c0 + s] = vals[s];
+        __stcs(out.c_ci + (c0 + s), keys[s]);
+        __stcs(out.c_val + (c0 + s), vals[s]);
     }
 }
 
@@ -177,8 +181,8 @@ __device__ __forceinline__ void writeout_bucket(int *keys, V *vals, int T, int *
         for (int x = s0; x < e; ++x) r += gk[x] < k ? 1 : 0;
         const int pos = s0 + r;
         if (pos < n_exp) {
-            out.c_ci[c0 + pos] = k;
-            out.c_val[c0 + pos] = gv[q];
+            __stcs(out.c_ci + (c0 + pos), k);
+            __stcs(out.c_val + (c0 + pos), gv[q]);
         }
     }
 }
@@ -223,8 +227,8 @@ __device__ __forceinline__ void writeout_bitmap(const int *keys, const V *vals, 
             const int w = k >> 5;
             const int pos = pre[w] + __popc(bm[w] & ((1u << (k & 31)) - 1u));
             if (pos < n_exp) {
-                out.c_ci[c0 + pos] = k;
-                out.c_val[c0 + pos] = vals[s];
+                __stcs(out.c_ci + (c0 + pos), k);
+                __stcs(out.c_val + (c0 + pos), vals[s]);
             }
         }
     }
