@@ -552,7 +552,7 @@ int run_bins(smash_handle *h, const RawOperands &op, int64_t n, int dt, const Nu
             } else {
                 LaunchTimer lt(h, bs, "num_hash", b, group_threads(hl), counts[b], sums[b], sums[16 + b],
                                sums[32 + b]);
-                launch_num_hash(dt, op, rows, counts[b], tok, hl, rule.inv_load, h->params.bitmap_ratio, out, err,
+                launch_num_hash(dt, op, rows, counts[b], tok, hl, rule.inv_load, h->params.bitmap_ratio, kept, out, err,
                                 bs);
             }
         }

@@ -14,6 +14,7 @@
 
 #include <climits>
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace smash {
@@ -425,6 +426,7 @@ __device__ __forceinline__ void group_products(const Operands<V> &op, int64_t ab
         k_next = __ldg(op.a_ci + ab + t);
         if constexpr (NUM) av_next = op.a_val[ab + t];
     }
+    int pbase = 0;   // products of the earlier batches
     for (int64_t base = ab; base < ae; base += GS) {
         int len = 0;
         int64_t bs = 0;
@@ -505,12 +507,21 @@ __device__ __forceinline__ void group_products(const Operands<V> &op, int64_t ab
 #pragma unroll
                 for (int u = 0; u < kProdUnroll; ++u) {
                     if (act[u]) {
-                        if ((unsigned)jv[u] < (unsigned)op.ncols) f(jv[u], av_u[u], bv[u]);
-                        else raise_err(err, kErrBadIndex);
+                        if ((unsigned)jv[u] < (unsigned)op.ncols) {
+                            // (a callback of four arguments also gets the product's
+                            // index among the row's products)
+                            if constexpr (std::is_invocable_v<F, int, V, V, int>)
+                                f(jv[u], av_u[u], bv[u], pbase + pb + 32 * u + lane);
+                            else
+                                f(jv[u], av_u[u], bv[u]);
+                        } else {
+                            raise_err(err, kErrBadIndex);
+                        }
                     }
                 }
             }
         }
+        pbase += total;
         // no barrier here: the next batch stages its entries only after the
         // first barrier of its scan, which every warp reaches after its walk
     }

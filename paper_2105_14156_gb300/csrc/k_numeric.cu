@@ -30,7 +30,8 @@ namespace smash {
 template <typename V, int GS, int NT>
 __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows, int count, int *token,
                                                  int tbits, HashCfg hc, int bsh, int bcap, int bm_words,
-                                                 int bitmap_ratio, NumOutT<V> out, int *err) {
+                                                 int bitmap_ratio, const RowGather *rec, NumOutT<V> out,
+                                                 int *err) {
     // bsh >= 0: bucket-rank write-out (its T/4 counters and room for bcap
     // grouped pairs follow each group's table); bsh < 0: bitonic.
     using G = Group<GS, NT>;
@@ -75,33 +76,65 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
         G::sync();
         int64_t ab = 0, ae = 0;
         if (ok) a_row_range(op, i, ab, ae, err);
-        int cnt = 0, ovf = 0;
-        group_products<V, true, GS, NT>(op, ab, ae, sc, err, [&](int j, V a, V bkj) {
-            bool ins;
-            const int h = hash_find_or_insert<false>(keys, tbits, hc, j, ins);
-            if (h >= 0) {
-                atomicAdd(vals + h, a * bkj);
-                if (ins) {
-                    ++cnt;
-                    if (bsh >= 0) atomicAdd(bc + (j >> bsh), 1);   // bucket counts for the write-out
-                }
-            } else if (out.row_nnz) {
-                ovf = 1;
-            } else {
-                raise_err(err, kErrTableFull);
-            }
-        });
-        // one reduction of (overflow flags, inserts): a row has at most
-        // T <= 2^14 distinct columns, so the inserts fit the low 16 bits
+        // Rows with nothing to merge skip the table (exact mode: the row's
+        // length equals its product count), and so do rows whose products fit
+        // their room (capacity mode: expanded, sorted and merged by the
+        // bucket write-out): each product is staged at its index. Float
+        // values only: with double values the larger kernel slowed the hashed
+        // rows more than the staged rows gained (R-MAT 16, float64).
+        constexpr bool kStage = sizeof(V) == 4;
+        const long long f_i = kStage && rec && ok ? rec[i].f : -1;
+        const bool direct =
+            kStage && !out.row_nnz && bsh >= 0 && f_i >= 0 && f_i == (long long)n_exp && f_i <= bcap;
+        const bool merge = kStage && out.row_nnz && bsh >= 0 && !use_bm && f_i >= 0 && f_i <= (long long)n_exp &&
+                           2 * f_i <= T && f_i <= bcap;
         int tot, o;
-        if constexpr (GS == 32) {
-            tot = warp_sum(cnt);
-            o = __any_sync(kFull, ovf);
-            __syncwarp();
+        if (direct || merge) {
+            group_products<V, true, GS, NT>(op, ab, ae, sc, err, [&](int j, V a, V bkj, int p) {
+                if ((unsigned)p < (unsigned)T) {
+                    keys[p] = j;
+                    vals[p] = a * bkj;
+                    atomicAdd(bc + (j >> bsh), 1);   // bucket counts for the write-out
+                }
+            });
+            tot = (int)f_i;
+            o = 0;
         } else {
-            const int packed = G::template sum<int>(cnt | (ovf << 16), sc.red);
-            tot = packed & 0xffff;
-            o = packed >> 16;
+            int cnt = 0, ovf = 0;
+            group_products<V, true, GS, NT>(op, ab, ae, sc, err, [&](int j, V a, V bkj) {
+                bool ins;
+                const int h = hash_find_or_insert<false>(keys, tbits, hc, j, ins);
+                if (h >= 0) {
+                    atomicAdd(vals + h, a * bkj);
+                    if (ins) {
+                        ++cnt;
+                        if (bsh >= 0) atomicAdd(bc + (j >> bsh), 1);   // bucket counts for the write-out
+                    }
+                } else if (out.row_nnz) {
+                    ovf = 1;
+                } else {
+                    raise_err(err, kErrTableFull);
+                }
+            });
+            // one reduction of (overflow flags, inserts): a row has at most
+            // T <= 2^14 distinct columns, so the inserts fit the low 16 bits
+            if constexpr (GS == 32) {
+                tot = warp_sum(cnt);
+                o = __any_sync(kFull, ovf);
+                __syncwarp();
+            } else {
+                const int packed = G::template sum<int>(cnt | (ovf << 16), sc.red);
+                tot = packed & 0xffff;
+                o = packed >> 16;
+            }
+        }
+        if (merge) {
+            // (the runs are the row's entries, at most its room)
+            const int runs = writeout_bucket_merge<V, GS, NT>(keys, vals, T, bc, gk, gv, bsh, tot, out, c0, sc.red);
+            if (t == 0) out.row_nnz[i] = runs;
+            clean = true;
+            G::sync();
+            continue;
         }
         bool over = false;
         if (out.row_nnz) {
@@ -695,7 +728,8 @@ static int resident_grid(K kernel, int nt, size_t smem, int sms, long long want_
 
 template <typename V, int GS>
 static void num_hash_go(const Operands<V> &op, const int *rows, int count, int *token, const HashLaunch &hl,
-                        float inv_load, int bitmap_ratio, const NumOutT<V> &out, int *err, cudaStream_t s) {
+                        float inv_load, int bitmap_ratio, const RowGather *rec, const NumOutT<V> &out, int *err,
+                        cudaStream_t s) {
     // one group per block from 64 threads up (block barriers, no named ones)
     constexpr int NT = GS < 64 ? 256 : GS;
     constexpr int groups = NT / GS;
@@ -726,30 +760,32 @@ static void num_hash_go(const Operands<V> &op, const int *rows, int count, int *
     const HashCfg hc{hl.hash_kind, hl.colbits};
     // buckets: T/4 of them over the column range, by the high bits
     const int bsh = !buckets ? -1 : hl.colbits > hl.tbits - 2 ? hl.colbits - (hl.tbits - 2) : 0;
-    kern<<<grid, NT, smem, s>>>(op, rows, count, token, hl.tbits, hc, bsh, bcap, bm_words, bitmap_ratio, out, err);
+    kern<<<grid, NT, smem, s>>>(op, rows, count, token, hl.tbits, hc, bsh, bcap, bm_words, bitmap_ratio, rec, out,
+                                err);
 }
 
 template <typename V>
 static void num_hash_typed(const RawOperands &r, const int *rows, int count, int *token, const HashLaunch &hl,
-                           float inv_load, int bitmap_ratio, const NumOut &o, int *err, cudaStream_t s) {
+                           float inv_load, int bitmap_ratio, const RowGather *rec, const NumOut &o, int *err,
+                           cudaStream_t s) {
     const Operands<V> op = num_operands<V>(r);
     const NumOutT<V> out = num_out<V>(o);
     switch (threads_per_row(hl.tbits, hl.group_shift)) {
-        case 32: num_hash_go<V, 32>(op, rows, count, token, hl, inv_load, bitmap_ratio, out, err, s); break;
-        case 64: num_hash_go<V, 64>(op, rows, count, token, hl, inv_load, bitmap_ratio, out, err, s); break;
-        case 128: num_hash_go<V, 128>(op, rows, count, token, hl, inv_load, bitmap_ratio, out, err, s); break;
-        case 256: num_hash_go<V, 256>(op, rows, count, token, hl, inv_load, bitmap_ratio, out, err, s); break;
-        case 512: num_hash_go<V, 512>(op, rows, count, token, hl, inv_load, bitmap_ratio, out, err, s); break;
-        default: num_hash_go<V, 1024>(op, rows, count, token, hl, inv_load, bitmap_ratio, out, err, s); break;
+        case 32: num_hash_go<V, 32>(op, rows, count, token, hl, inv_load, bitmap_ratio, rec, out, err, s); break;
+        case 64: num_hash_go<V, 64>(op, rows, count, token, hl, inv_load, bitmap_ratio, rec, out, err, s); break;
+        case 128: num_hash_go<V, 128>(op, rows, count, token, hl, inv_load, bitmap_ratio, rec, out, err, s); break;
+        case 256: num_hash_go<V, 256>(op, rows, count, token, hl, inv_load, bitmap_ratio, rec, out, err, s); break;
+        case 512: num_hash_go<V, 512>(op, rows, count, token, hl, inv_load, bitmap_ratio, rec, out, err, s); break;
+        default: num_hash_go<V, 1024>(op, rows, count, token, hl, inv_load, bitmap_ratio, rec, out, err, s); break;
     }
 }
 
 void launch_num_hash(int dtype, const RawOperands &r, const int *rows, int count, int *token,
-                     const HashLaunch &hl, float inv_load, int bitmap_ratio, const NumOut &out, int *err,
-                     cudaStream_t s) {
+                     const HashLaunch &hl, float inv_load, int bitmap_ratio, const RowGather *rec, const NumOut &out,
+                     int *err, cudaStream_t s) {
     if (count <= 0) return;
-    if (dtype) num_hash_typed<double>(r, rows, count, token, hl, inv_load, bitmap_ratio, out, err, s);
-    else num_hash_typed<float>(r, rows, count, token, hl, inv_load, bitmap_ratio, out, err, s);
+    if (dtype) num_hash_typed<double>(r, rows, count, token, hl, inv_load, bitmap_ratio, rec, out, err, s);
+    else num_hash_typed<float>(r, rows, count, token, hl, inv_load, bitmap_ratio, rec, out, err, s);
 }
 
 int dense_bitmap_max_cols() {

@@ -163,9 +163,11 @@ struct NumOut {
     int64_t c_nnz;
     int *row_nnz = nullptr;  // capacity mode (learned sizing) when set, see k_numeric.cu
 };
+// rec (may be null): per-row product counts; rows with nothing to merge
+// (exact mode) or whose products fit their room (capacity mode) skip the table.
 void launch_num_hash(int dtype, const RawOperands &op, const int *rows, int count, int *token,
-                     const HashLaunch &hl, float inv_load, int bitmap_ratio, const NumOut &out, int *err,
-                     cudaStream_t s);
+                     const HashLaunch &hl, float inv_load, int bitmap_ratio, const RowGather *rec, const NumOut &out,
+                     int *err, cudaStream_t s);
 // Warp rows (k_warp.cuh): one warp per row, products enumerated from
 // registers, compare-and-swap-first probing, list-driven write-out. The
 // *_smem functions give the dynamic shared memory of one block.

@@ -187,6 +187,91 @@ __device__ __forceinline__ void writeout_bucket(int *keys, V *vals, int T, int *
     }
 }
 
+// ----- write-out: bucket sort and merge of expanded products -----------------
+// For rows whose products were staged as they came (capacity mode, the
+// products fit the row's room): the same grouping by bucket as
+// writeout_bucket, then each product's place in the column-sorted sequence
+// (equal columns ordered by their grouped position) in keys[0..tot),
+// vals[0..tot) (the table is empty by then), then one pass over the sequence
+// that sums each run of equal columns into one entry of C. Returns the number
+// of entries (runs); keys / vals are EMPTY / 0 again afterwards. Needs
+// tot <= cap of the grouped pairs and tot <= T.
+template <typename V, int GS, int NT>
+__device__ __forceinline__ int writeout_bucket_merge(int *keys, V *vals, int T, int *bc, int *gk, V *gv, int sh,
+                                                     int tot, const NumOutT<V> &out, int64_t c0, int *red) {
+    using G = Group<GS, NT>;
+    const int t = G::tid();
+    const int NB = T >> 2;
+    int n;   // products counted into the buckets (a product with a bad column was not staged)
+    {
+        const int per = (NB + GS - 1) / GS;
+        const int b0 = min(t * per, NB), b1 = min(b0 + per, NB);
+        int loc = 0;
+        for (int b = b0; b < b1; ++b) loc += bc[b];
+        int run = G::template excl_scan<int>(loc, red, &n);
+        for (int b = b0; b < b1; ++b) {
+            const int c = bc[b];
+            bc[b] = run;
+            run += c;
+        }
+    }
+    G::sync();
+    // grouped by bucket; the staged slots go back to EMPTY / 0
+    for (int s = t; s < tot; s += GS) {
+        const int k = keys[s];
+        if (k != kEmpty) {
+            const int p = atomicAdd(bc + (k >> sh), 1);
+            gk[p] = k;
+            gv[p] = vals[s];
+            keys[s] = kEmpty;
+            vals[s] = V(0);
+        }
+    }
+    G::sync();
+    // bc[b] is now the end of bucket b; place every product
+    for (int q = t; q < n; q += GS) {
+        const int k = gk[q];
+        const int b = k >> sh;
+        const int e = bc[b];
+        const int s0 = b ? bc[b - 1] : 0;
+        int r = 0;
+        for (int x = s0; x < e; ++x) {
+            const int kx = gk[x];
+            r += (kx < k || (kx == k && x < q)) ? 1 : 0;
+        }
+        keys[s0 + r] = k;
+        vals[s0 + r] = gv[q];
+    }
+    G::sync();
+    // runs of equal columns: the first of each run sums it and takes the
+    // next place of the row
+    int runs = 0;
+    for (int q0 = 0; q0 < n; q0 += GS) {
+        const int q = q0 + t;
+        bool first = false;
+        int k = 0;
+        if (q < n) {
+            k = keys[q];
+            first = q == 0 || keys[q - 1] != k;
+        }
+        int cnt;
+        const int d = runs + G::template excl_scan<int>(first ? 1 : 0, red, &cnt);
+        if (first) {
+            V v = vals[q];
+            for (int y = q + 1; y < n && keys[y] == k; ++y) v += vals[y];
+            __stcs(out.c_ci + (c0 + d), k);
+            __stcs(out.c_val + (c0 + d), v);
+        }
+        runs += cnt;
+    }
+    G::sync();
+    for (int q = t; q < n; q += GS) {
+        keys[q] = kEmpty;
+        vals[q] = V(0);
+    }
+    return runs;
+}
+
 // Exclusive prefix of popcounts over words [0, nwords) of bm (contiguous
 // chunk per thread); returns the total.
 template <int GS, int NT>

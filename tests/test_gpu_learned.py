@@ -324,3 +324,26 @@ def test_bound_sized_one_pass_matches_oracle(handle, values):
     assert_matches_oracle(Ch, A, A)
     assert stats["overflow_rows"] == 0
     assert stats["c_nnz"] == Ch.col_idx.size
+
+@pytest.mark.parametrize("values", ["f32", "f64"])
+@pytest.mark.parametrize("group_shift", [4, 2])
+def test_bound_sized_thread_group_merge(handle, values, group_shift):
+    """Capacity mode in the thread-group rows: every row's ~1200 products fit
+    its room (the bound min(flop_i, cols)), so they are staged, sorted and
+    merged (about a fifth of them repeat a column) instead of hashed."""
+    from paper_2105_14156_gb300 import smash
+    from tests.helpers import random_csr
+    A = random_csr(3001, 300, 0.02, 195, values=values)
+    B = random_csr(300, 3000, 0.067, 196, values=values)
+    defaults = handle.params.as_dict()
+    handle.set_params(group_shift=group_shift)
+    try:
+        dA, dB = smash.to_device(A), smash.to_device(B)
+        C, stats, owner = handle.spgemm_learned(dA, dB, None)
+        handle.check()
+        Ch = C.to_host()
+        owner.free()
+    finally:
+        handle.set_params(**defaults)
+    assert_matches_oracle(Ch, A, B)
+    assert stats["overflow_rows"] == 0

@@ -267,6 +267,33 @@ def test_row_windows_integer_values_exact(handle):
     assert_matches_oracle(C, A, A, exact=True)
 
 
+def disjoint_block_b(nrows, width, keep, seed, values):
+    """B whose row k holds `keep` columns of [k*width, (k+1)*width): no two rows
+    share a column, so every row of A*B repeats no column."""
+    rng = np.random.default_rng(seed)
+    rows, cols = [], []
+    for k in range(nrows):
+        c = np.sort(rng.choice(width, keep, replace=False)) + k * width
+        rows.append(np.full(keep, k))
+        cols.append(c)
+    from paper_2105_14156_gb300.rmat import csr_from_coo
+    rp, ci = csr_from_coo(nrows, nrows * width, np.concatenate(rows), np.concatenate(cols))
+    v = rng.uniform(-1, 1, ci.size)
+    return Csr(nrows, nrows * width, rp, ci, v.astype(np.float32) if values == "f32" else v)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("group_shift", [4, 2])
+def test_thread_group_rows_without_repeats(handle, dtype, group_shift):
+    """Rows of 500-1000 products that repeat no column (B's rows have disjoint
+    columns): in exact mode, after the symbolic phase, their products skip the
+    thread-group table and are sorted straight into C."""
+    A = random_csr(3001, 300, 0.02, 191, values=dtype)
+    B = disjoint_block_b(300, 200, 150, 192, dtype)
+    C = run(handle, A, B, group_shift=group_shift)
+    assert_matches_oracle(C, A, B)
+
+
 def test_tiny_rows_integer_values_exact(handle):
     """Small-integer float32 data: the thread-per-row merge is exact."""
     A = rmat(12, 2, GRAPH500_ABCD, seed=85, values="int4")
