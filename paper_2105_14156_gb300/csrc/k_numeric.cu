@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
             } else if (use_bm) {
                 writeout_bitmap<V, GS, NT>(keys, vals, T, bm, pre, bm_words, n_exp, out, c0, sc.red);
             } else if (bsh >= 0 && tot <= bcap) {
-                writeout_bucket<V, GS, NT>(keys, vals, T, bc, gk, gv, bsh, tot, n_exp, out, c0, sc.red);
+                writeout_bucket<V, GS, NT>(keys, vals, T, bc, gk, gv, bsh, tot, n_exp, out, c0, sc.red,
+                                           direct ? tot : T);
                 clean = true;
             } else {
                 writeout_bitonic<V, GS, NT>(keys, vals, T, n_exp, out, c0, sc.red);

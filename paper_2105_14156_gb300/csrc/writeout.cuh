@@ -134,7 +134,11 @@ __device__ __forceinline__ void writeout_bitonic(int *keys, V *vals, int T, int 
 // the number of smaller columns in its bucket. Needs tot <= cap.
 template <typename V, int GS, int NT>
 __device__ __forceinline__ void writeout_bucket(int *keys, V *vals, int T, int *bc, int *gk, V *gv, int sh, int tot,
-                                                int n_exp, const NumOutT<V> &out, int64_t c0, int *red) {
+                                                int n_exp, const NumOutT<V> &out, int64_t c0, int *red,
+                                                int span = -1) {
+    // span: the slots that may be occupied (the whole table unless the
+    // entries were staged in its first slots)
+    if (span < 0) span = T;
     using G = Group<GS, NT>;
     const int t = G::tid();
     const int NB = T >> 2;
@@ -153,10 +157,10 @@ __device__ __forceinline__ void writeout_bucket(int *keys, V *vals, int T, int *
     }
     G::sync();
     // four slots per thread per round, so that their atomics overlap
-    for (int s0 = t; s0 < T; s0 += 4 * GS) {
+    for (int s0 = t; s0 < span; s0 += 4 * GS) {
         int k[4], p[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) k[u] = s0 + u * GS < T ? keys[s0 + u * GS] : kEmpty;
+        for (int u = 0; u < 4; ++u) k[u] = s0 + u * GS < span ? keys[s0 + u * GS] : kEmpty;
 #pragma unroll
         for (int u = 0; u < 4; ++u) p[u] = k[u] != kEmpty ? atomicAdd(bc + (k[u] >> sh), 1) : 0;
 #pragma unroll
@@ -243,26 +247,27 @@ __device__ __forceinline__ int writeout_bucket_merge(int *keys, V *vals, int T, 
         vals[s0 + r] = gv[q];
     }
     G::sync();
-    // runs of equal columns: the first of each run sums it and takes the
-    // next place of the row
-    int runs = 0;
-    for (int q0 = 0; q0 < n; q0 += GS) {
-        const int q = q0 + t;
-        bool first = false;
-        int k = 0;
-        if (q < n) {
-            k = keys[q];
-            first = q == 0 || keys[q - 1] != k;
+    // runs of equal columns: each thread takes a contiguous chunk of the
+    // sequence, counts the run heads in it, one scan of the counts gives each
+    // chunk its first place in the row, and each head sums its run (reading
+    // past its chunk when the run goes on) and takes the next place
+    int runs;
+    {
+        const int per = (n + GS - 1) / GS;
+        const int q0 = min(t * per, n), q1 = min(q0 + per, n);
+        int heads = 0;
+        for (int q = q0; q < q1; ++q) heads += (q == 0 || keys[q - 1] != keys[q]) ? 1 : 0;
+        int d = G::template excl_scan<int>(heads, red, &runs);
+        for (int q = q0; q < q1; ++q) {
+            const int k = keys[q];
+            if (q == 0 || keys[q - 1] != k) {
+                V v = vals[q];
+                for (int y = q + 1; y < n && keys[y] == k; ++y) v += vals[y];
+                __stcs(out.c_ci + (c0 + d), k);
+                __stcs(out.c_val + (c0 + d), v);
+                ++d;
+            }
         }
-        int cnt;
-        const int d = runs + G::template excl_scan<int>(first ? 1 : 0, red, &cnt);
-        if (first) {
-            V v = vals[q];
-            for (int y = q + 1; y < n && keys[y] == k; ++y) v += vals[y];
-            __stcs(out.c_ci + (c0 + d), k);
-            __stcs(out.c_val + (c0 + d), v);
-        }
-        runs += cnt;
     }
     G::sync();
     for (int q = t; q < n; q += GS) {
