@@ -51,6 +51,8 @@ WORKLOADS = {
     "rmat16_f64": "R-MAT scale 16 (65536 x 65536), edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), "
                   "float64 values U[-1,1], C = A*A (A and B separate copies)",
     "rmat10_int": "R-MAT scale 10, edge factor 8, (0.57,0.19,0.19,0.05), float32 integer values {1..4}, C = A*A",
+    "rmat17_f32": "R-MAT scale 17, edge factor 16, (0.57,0.19,0.19,0.05), float32 U[-1,1], C = A*A "
+                  "(a smaller case of the scale-18 workload, for captures)",
     "rmat18_f32": "R-MAT scale 18, edge factor 16, (0.57,0.19,0.19,0.05), float32 U[-1,1], C = A*A",
 }
 PATHS = {"learned": "learned sizing (row-size network) + autotuned planner",

@@ -232,6 +232,8 @@ def workload(name: str):
         return rmat(10, 8, GRAPH500_ABCD, seed=1, values="int4")
     if name == "rmat16_f64":
         return rmat(16, 16, GRAPH500_ABCD, seed=1, values="f64")
+    if name == "rmat17_f32":
+        return rmat(17, 16, GRAPH500_ABCD, seed=1, values="f32")
     if name == "rmat18_f32":
         return rmat(18, 16, GRAPH500_ABCD, seed=1, values="f32")
     if name == "rmat20_f32":
