@@ -93,9 +93,10 @@ typedef struct {
                                 stores its entries (measured faster for rows of a few hundred entries) */
     int32_t group_rows;      /* numeric rows served by a block of 64-1024 threads: 1: the products of a row
                                 spread over the block's warps, compare-and-swap-first probing, list-driven
-                                write-out (and no table for rows without repeated columns); 0 (default): the
-                                staged enumeration with a write-out that scans the whole table (measured
-                                faster on R-MAT products) */
+                                write-out (and no table for rows without repeated columns; B with fewer
+                                than 2^31 entries, else the default kernel runs); 0 (default): the staged
+                                enumeration with a write-out that scans the whole table (measured faster on
+                                R-MAT products) */
     int32_t row_window;      /* rows of a bin served together by one warp with one shared-memory table
                                 whose tags are (row, column) (the paper's windows of rows): 0 disables,
                                 else 2..32 rows per window (fewer where the window would hold more
