@@ -207,6 +207,68 @@ struct RowClaim {
     }
 };
 
+// RowClaim that also fetches the claimed row's entry of the row list early:
+// prefetch(), called halfway through a row (when the claim's atomic has long
+// returned), loads rows[next] into a register, so that the next row starts
+// with its row index at hand instead of a load that waits on the atomic's
+// result. Larger groups hand the claim and the row index on through shared
+// memory in publish(), which the caller makes before the row's closing group
+// barrier (after prefetch()). next() returns the row of the bin list and its
+// row of A in *i.
+template <typename G>
+struct RowClaimPf {
+    int *token;
+    const int *rows;
+    int (*s_row)[G::kGroups];
+    int (*s_rowi)[G::kGroups];
+    int nx = 0;     // group thread 0: the claimed next row
+    int nxi = -1;   // group thread 0: its entry of the row list (-1: not fetched)
+    int par = 0;
+
+    __device__ __forceinline__ RowClaimPf(int *tok, const int *rws, int (*s)[G::kGroups], int (*si)[G::kGroups])
+        : token(tok), rows(rws), s_row(s), s_rowi(si) {
+        if (G::tid() == 0) nx = atomicAdd(token, 1);
+        if constexpr (G::kWarps > 1) {
+            if (G::tid() == 0) {
+                s_row[0][G::gid()] = nx;
+                s_rowi[0][G::gid()] = -1;
+            }
+            G::sync();
+        }
+    }
+
+    __device__ __forceinline__ int next(int count, int *i) {
+        int r, ri;
+        if constexpr (G::kWarps == 1) {
+            r = __shfl_sync(kFull, nx, 0);
+            ri = __shfl_sync(kFull, nxi, 0);
+        } else {
+            r = s_row[par][G::gid()];
+            ri = s_rowi[par][G::gid()];
+            par ^= 1;
+        }
+        *i = ri >= 0 ? ri : (r < count ? __ldg(rows + r) : 0);
+        if (G::tid() == 0 && r < count) {
+            nx = atomicAdd(token, 1);
+            nxi = -1;
+        }
+        return r;
+    }
+
+    __device__ __forceinline__ void prefetch(int count) {
+        if (G::tid() == 0 && nx < count) nxi = __ldg(rows + nx);
+    }
+
+    __device__ __forceinline__ void publish() {
+        if constexpr (G::kWarps > 1) {
+            if (G::tid() == 0) {
+                s_row[par][G::gid()] = nx;
+                s_rowi[par][G::gid()] = nxi;
+            }
+        }
+    }
+};
+
 // ---------------------------------------------------------------------------
 // Hash slot of column j in a table of 2^tbits slots.
 struct HashCfg {

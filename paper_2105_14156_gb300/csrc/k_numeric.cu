@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
     // grouped pairs follow each group's table); bsh < 0: bitonic.
     using G = Group<GS, NT>;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_row[2][G::kGroups];
+    __shared__ int s_row[2][G::kGroups], s_rowi[2][G::kGroups];
     const int T = 1 << tbits;
     if (bsh < 0) bcap = 0;
     // group layout (hash_group_bytes): keys, values, bucket counters, then the
@@ -54,14 +54,18 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
     int *pre = (int *)(bm + bm_words);
     const int t = G::tid();
     bool clean = false;   // the table is EMPTY / 0 (left so by the bucket write-out)
-    RowClaim<G> claim(token, s_row);
+    RowClaimPf<G> claim(token, rows, s_row, s_rowi);
     for (;;) {
-        const int r = claim.next(count);
+        int i;
+        const int r = claim.next(count, &i);
         if (r >= count) break;
-        const int i = rows[r];
+        // the row's bounds in C and A and its product count, loaded together
+        const int64_t cs = out.c_rp[i], ct = out.c_rp[i + 1];
+        int64_t ab = __ldg(op.a_rp + i), ae = __ldg(op.a_rp + i + 1);
+        const long long f_rec = rec ? rec[i].f : -1;
         int64_t c0;
         int n_exp;
-        const bool ok = out_range(out, i, c0, n_exp, err);
+        const bool ok = row_bounds_ok(cs, ct, out.c_nnz, c0, n_exp, err);
         const bool use_bm = (GS == NT) && bm_words > 0 && (long long)bm_words <= (long long)bitmap_ratio * n_exp;
         if (!clean) {
             for (int s = t; s < T; s += GS) {
@@ -74,8 +78,7 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
         if (use_bm)
             for (int w = t; w < bm_words; w += GS) bm[w] = 0u;
         G::sync();
-        int64_t ab = 0, ae = 0;
-        if (ok) a_row_range(op, i, ab, ae, err);
+        if (!ok || !a_bounds_ok(ab, ae, op.a_nnz, err)) ab = ae = 0;
         // Rows with nothing to merge skip the table (exact mode: the row's
         // length equals its product count), and so do rows whose products fit
         // their room (capacity mode: expanded, sorted and merged by the
@@ -83,7 +86,7 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
         // values only: with double values the larger kernel slowed the hashed
         // rows more than the staged rows gained (R-MAT 16, float64).
         constexpr bool kStage = sizeof(V) == 4;
-        const long long f_i = kStage && rec && ok ? rec[i].f : -1;
+        const long long f_i = kStage && ok ? f_rec : -1;
         const bool direct =
             kStage && !out.row_nnz && bsh >= 0 && f_i >= 0 && f_i == (long long)n_exp && f_i <= bcap;
         const bool merge = kStage && out.row_nnz && bsh >= 0 && !use_bm && f_i >= 0 && f_i <= (long long)n_exp &&
@@ -128,11 +131,13 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
                 o = packed >> 16;
             }
         }
+        claim.prefetch(count);
         if (merge) {
             // (the runs are the row's entries, at most its room)
             const int runs = writeout_bucket_merge<V, GS, NT>(keys, vals, T, bc, gk, gv, bsh, tot, out, c0, sc.red);
             if (t == 0) out.row_nnz[i] = runs;
             clean = true;
+            claim.publish();
             G::sync();
             continue;
         }
@@ -158,6 +163,7 @@ __global__ void __launch_bounds__(NT) k_num_hash(Operands<V> op, const int *rows
                 writeout_bitonic<V, GS, NT>(keys, vals, T, n_exp, out, c0, sc.red);
             }
         }
+        claim.publish();
         G::sync();
     }
 }

@@ -128,22 +128,25 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
     }
     for (int s = lane; s < NB; s += 32) bc[s] = 0;
     __syncwarp();
-    RowClaim<G> claim(token, s_row);
+    RowClaimPf<G> claim(token, rows, s_row, nullptr);
     for (;;) {
-        const int r = claim.next(count);
+        int i;
+        const int r = claim.next(count, &i);
         if (r >= count) break;
-        const int i = rows[r];
+        // the row's bounds in C and A and its product count, loaded together
+        const int64_t cs = out.c_rp[i], ct = out.c_rp[i + 1];
+        int64_t ab = __ldg(op.a_rp + i), ae = __ldg(op.a_rp + i + 1);
+        const long long f_rec = rec ? rec[i].f : -1;
         int64_t c0;
         int n_exp;
-        const bool ok = out_range(out, i, c0, n_exp, err);
-        int64_t ab = 0, ae = 0;
-        if (ok) a_row_range(op, i, ab, ae, err);
+        const bool ok = row_bounds_ok(cs, ct, out.c_nnz, c0, n_exp, err);
+        if (!ok || !a_bounds_ok(ab, ae, op.a_nnz, err)) ab = ae = 0;
         int cnt = 0, full = 0;
         // direct: exact mode, the row's length equals its product count (no
         // repeated column). merge: capacity mode, the row's products fit its
         // capacity (the size model sees few repeated columns); its products
         // are staged as they are and equal columns summed after the sort.
-        const long long f_i = rec && ok ? rec[i].f : -1;
+        const long long f_i = ok ? f_rec : -1;
         const bool cap = MODE == 1 || (MODE == 2 && out.row_nnz != nullptr);
         const bool direct = !cap && f_i >= 0 && n_exp <= lcap && f_i == (long long)n_exp;
         const bool merge = cap && f_i >= 0 && f_i <= (long long)n_exp && f_i <= lcap && 2 * f_i <= T;
@@ -172,6 +175,7 @@ __global__ void __launch_bounds__(NW * 32) k_num_warp(Operands<V> op, const int 
                 cnt += __popc(m);
             });
         }
+        claim.prefetch(count);
         full = __any_sync(kFull, full);
         const int tot = cnt;
         bool over;

@@ -27,6 +27,28 @@ struct NumOutT {
     int *row_nnz;
 };
 
+// The same checks on bounds already loaded: a row [s, t) of C, a row [ab, ae)
+// of A (raise the error and return false when malformed).
+__device__ __forceinline__ bool row_bounds_ok(int64_t s, int64_t t, int64_t c_nnz, int64_t &c0, int &n, int *err) {
+    if (s < 0 || t < s || t > c_nnz || t - s > INT_MAX) {
+        raise_err(err, kErrBadRowPtr);
+        c0 = 0;
+        n = 0;
+        return false;
+    }
+    c0 = s;
+    n = (int)(t - s);
+    return true;
+}
+
+__device__ __forceinline__ bool a_bounds_ok(int64_t ab, int64_t ae, int64_t a_nnz, int *err) {
+    if (ab < 0 || ae < ab || ae > a_nnz) {
+        raise_err(err, kErrBadRowPtr);
+        return false;
+    }
+    return true;
+}
+
 template <typename V>
 __device__ __forceinline__ bool out_range(const NumOutT<V> &o, int64_t i, int64_t &c0, int &n, int *err) {
     const int64_t s = o.c_rp[i], t = o.c_rp[i + 1];
