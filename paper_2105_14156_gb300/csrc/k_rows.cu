@@ -91,8 +91,17 @@ __device__ __forceinline__ void bin_rows(bool valid, int64_t i, int64_t len, lon
         bb.bin[i] = (uint8_t)b;
         if (nnz_out && b == kBinEmpty) nnz_out[i] = 0;
     }
-    const long long wp = warp_sum(valid ? f : 0ll);
-    const long long wm = warp_max(valid ? f : 0ll);
+    // warps whose values all fit 26 bits reduce with the 32-bit warp
+    // reductions (sums of 32 of them fit 31 bits), the others with shuffles
+    const bool small = __all_sync(kFull, !valid || (len < (1 << 26) && f < (1ll << 26) && size < (1ll << 26)));
+    auto wsum = [&](long long v) -> long long {
+        return small ? (long long)__reduce_add_sync(kFull, (unsigned)v) : warp_sum(v);
+    };
+    auto wmax = [&](long long v) -> long long {
+        return small ? (long long)__reduce_max_sync(kFull, (unsigned)v) : warp_max(v);
+    };
+    const long long wp = wsum(valid ? f : 0ll);
+    const long long wm = wmax(valid ? f : 0ll);
     if (lane == 0) {
         atomicAdd((unsigned long long *)&st.prod, (unsigned long long)wp);
         atomicMax(&st.maxrow, wm);
@@ -102,10 +111,10 @@ __device__ __forceinline__ void bin_rows(bool valid, int64_t i, int64_t len, lon
         const bool mine = valid && b == b0;
         const unsigned m = __ballot_sync(kFull, mine);
         todo &= ~m;
-        const long long s0 = warp_sum(mine ? (long long)len : 0ll);
-        const long long s1 = warp_sum(mine ? f : 0ll);
-        const long long s2 = warp_sum(mine ? size : 0ll);
-        const long long mx = warp_max(mine ? size : 0ll);
+        const long long s0 = wsum(mine ? (long long)len : 0ll);
+        const long long s1 = wsum(mine ? f : 0ll);
+        const long long s2 = wsum(mine ? size : 0ll);
+        const long long mx = wmax(mine ? size : 0ll);
         if (lane == 0) {
             atomicAdd(&st.cnt[b0], __popc(m));
             atomicMax(&st.max[b0], mx);

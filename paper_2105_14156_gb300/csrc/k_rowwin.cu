@@ -258,10 +258,17 @@ __global__ void __launch_bounds__(NW * 32) k_num_rowwin(Operands<V> op, const in
         bool ok = false;
         long long f = -1;
         if (lane < nrows) {
+            // the row's bounds in C and A and its product count, loaded together
             wr.i = rows[r0 + lane];
-            ok = out_range(out, wr.i, c0, n_exp, err);
-            if (ok) a_row_range(op, wr.i, wr.ab, wr.ae, err);
-            f = rec && ok ? rec[wr.i].f : -1;
+            const int64_t cs = out.c_rp[wr.i], ct = out.c_rp[wr.i + 1];
+            int64_t ab = __ldg(op.a_rp + wr.i), ae = __ldg(op.a_rp + wr.i + 1);
+            const long long f_rec = rec ? rec[wr.i].f : -1;
+            ok = row_bounds_ok(cs, ct, out.c_nnz, c0, n_exp, err);
+            if (ok && a_bounds_ok(ab, ae, op.a_nnz, err)) {
+                wr.ab = ab;
+                wr.ae = ae;
+            }
+            f = ok ? f_rec : -1;
         }
         // staged (expand) when every row's products can go as they are: no
         // repeated column in exact mode, within the capacity in capacity mode

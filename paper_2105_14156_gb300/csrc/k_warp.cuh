@@ -62,11 +62,11 @@ __global__ void __launch_bounds__(NW * 32) k_sym_warp(Operands<float> op, const 
     const int lane = lane_id();
     for (int s = lane; s < T; s += 32) keys[s] = kEmpty;
     __syncwarp();
-    RowClaim<G> claim(token, s_row);
+    RowClaimPf<G> claim(token, rows, s_row, nullptr);
     for (;;) {
-        const int r = claim.next(count);
+        int i;
+        const int r = claim.next(count, &i);
         if (r >= count) break;
-        const int i = rows[r];
         int64_t ab, ae;
         a_row_range(op, i, ab, ae, err);
         int cnt = 0, full = 0;
@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(NW * 32) k_sym_warp(Operands<float> op, const 
             if (act && cas_insert(keys, tbits, hc, j, ins) < 0) full = 1;
             cnt += __popc(__ballot_sync(kFull, ins));
         });
+        claim.prefetch(count);
         if (__any_sync(kFull, full) && lane == 0) raise_err(err, kErrTableFull);
         if (lane == 0) nnz_out[i] = cnt;
         __syncwarp();
