@@ -17,9 +17,10 @@
  *    the structure of C is every (i, j) reached by at least one product.
  *  - rows == 0 and nnz == 0 are legal. A.cols must equal B.rows.
  *  - Limits: rows, cols < 2^31; every row of B holds fewer than 2^21
- *    entries. Violations, out-of-range indices and malformed row pointers are
- *    detected by the kernels' bounds checks and reported as
- *    SMASH_ERR_INVALID_ARG; no out-of-range access is made.
+ *    entries. Out-of-range indices and malformed row pointers are detected by
+ *    the kernels' bounds checks and reported as SMASH_ERR_INVALID_ARG, a row
+ *    of B over the limit as SMASH_ERR_UNSUPPORTED; no out-of-range access is
+ *    made.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *  - No C++ exception crosses this interface; every call returns a status.
  *  - The library never frees memory it did not allocate. Scratch memory is

@@ -350,6 +350,30 @@ def test_bad_column_index_is_reported(handle):
     assert_matches_oracle(run(handle, A, B2), A, B2)
 
 
+@pytest.mark.parametrize("dense", [0, 1 << 20])
+def test_row_of_b_too_long_is_reported(handle, dense):
+    """A row of B with 2^21 entries is outside the stated limits: the call
+    reports SMASH_ERR_UNSUPPORTED (found by the kernels' checks, no access
+    past the row), whether the rows that reach it are hashed or dense, and
+    the handle stays usable."""
+    from paper_2105_14156_gb300 import smash
+    from paper_2105_14156_gb300.rmat import csr_from_coo
+    n = 1 << 21
+    # row 0 of B: 2^21 entries over 16 columns (repeats are separate terms)
+    brows = np.concatenate([np.zeros(n, np.int64), np.ones(3, np.int64)])
+    bcols = np.concatenate([np.arange(n, dtype=np.int64) % 16, np.array([0, 5, 9])])
+    rp, ci = csr_from_coo(2, 16, brows, bcols, merge=False)
+    B = Csr(2, 16, rp, ci, np.ones(ci.size))
+    arp, aci = csr_from_coo(3, 2, np.array([0, 1, 2]), np.array([0, 1, 1]))
+    A = Csr(3, 2, arp, aci, np.ones(aci.size))
+    with pytest.raises(smash.SmashError) as ei:
+        run(handle, A, B, dense_ratio=dense)
+    assert ei.value.status == 3
+    A2 = random_csr(50, 40, 0.2, 13, values="f64")
+    B2 = random_csr(40, 30, 0.2, 14, values="f64")
+    assert_matches_oracle(run(handle, A2, B2), A2, B2)
+
+
 def test_shape_mismatch(handle):
     from paper_2105_14156_gb300 import smash
     A = random_csr(10, 9, 0.3, 1)
