@@ -121,6 +121,77 @@ def chunked_copies(pairs, streams, main, chunk_bytes=64 << 20):
         main.wait_stream(cs)
 
 
+E2E_BLOCKS = 4
+
+
+def end_to_end(h, args, A, B, flop, model, margin, stream, dev, blocks):
+    """Median seconds of the product through the public API with host buffers:
+    every step copies A and B from pinned host memory and C back to pinned host
+    memory inside the timed region. blocks > 1: A is cut into that many row
+    blocks of about equal products, each multiplied by its own call; a block's
+    C goes back to the host on a copy stream while the next block computes
+    (C's row pointer shifted by the entries of the blocks before it)."""
+    import torch
+    from paper_2105_14156_gb300 import smash
+    cum = np.concatenate([[0], np.cumsum(flop)])
+    cuts = [0] + [int(np.searchsorted(cum, cum[-1] * q / blocks)) for q in range(1, blocks)] + [A.rows]
+    cuts = sorted(set(min(max(c, 0), A.rows) for c in cuts))
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    # inputs: B whole; A's columns and values whole, its row pointer per block (rebased to 0)
+    h_in = [pin(B.row_ptr), pin(B.col_idx), pin(B.val), pin(A.col_idx), pin(A.val)]
+    h_rp = [pin(A.row_ptr[r0:r1 + 1] - A.row_ptr[r0]) for r0, r1 in zip(cuts[:-1], cuts[1:])]
+    h2d = sum(t.numel() * t.element_size() for t in h_in + h_rp)
+    copy_streams = [torch.cuda.Stream(dev) for _ in range(4)]
+    times, out_host, d2h = [], None, 0
+    for k in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d_in = [torch.empty(t.shape, dtype=t.dtype, device=dev) for t in h_in]
+        d_rp = [torch.empty(t.shape, dtype=t.dtype, device=dev) for t in h_rp]
+        chunked_copies(list(zip(d_in + d_rp, h_in + h_rp)), copy_streams, stream)
+        dB = smash.DeviceCsr(B.rows, B.cols, d_in[0], d_in[1], d_in[2])
+        keep, off = [], 0
+        for q, (r0, r1) in enumerate(zip(cuts[:-1], cuts[1:])):
+            a0, a1 = int(A.row_ptr[r0]), int(A.row_ptr[r1])
+            dA = smash.DeviceCsr(r1 - r0, A.cols, d_rp[q], d_in[3][a0:a1], d_in[4][a0:a1])
+            owner = None
+            if args.path == "plain":
+                C = h.spgemm(dA, dB, stream)
+            else:
+                C, _, owner = h.spgemm_learned(dA, dB, model if args.path == "learned" else None, margin=margin,
+                                               stream=stream)
+            if out_host is None:
+                # sized on the untimed first step (the product's nnz is fixed)
+                out_host = [torch.zeros(A.rows + 1, dtype=torch.int64).pin_memory(),
+                            torch.empty(int(1.2 * sum(flop)) + 1, dtype=torch.int32).pin_memory(),
+                            torch.empty(int(1.2 * sum(flop)) + 1, dtype=C.val.dtype).pin_memory()]
+            n = C.nnz
+            rp = C.row_ptr[1:] + off if off else C.row_ptr[1:]
+            cs = copy_streams[q % len(copy_streams)]
+            cs.wait_stream(stream)
+            with torch.cuda.stream(cs):
+                out_host[0][r0 + 1:r1 + 1].copy_(rp, non_blocking=True)
+                out_host[1][off:off + n].copy_(C.col_idx, non_blocking=True)
+                out_host[2][off:off + n].copy_(C.val, non_blocking=True)
+            keep.append((C, rp, owner))
+            off += n
+        for cs in copy_streams:
+            stream.wait_stream(cs)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        d2h = 8 * (A.rows + 1) + (4 + out_host[2].element_size()) * off
+        if k > 0:
+            times.append(dt)
+        for C, rp, owner in keep:
+            if owner is not None:
+                owner.free()
+        del keep, d_in, d_rp, dB
+    # (untimed) the assembled row pointer ends at the entries copied
+    assert int(out_host[0][A.rows]) == off
+    return {"seconds": statistics.median(times), "h2d": h2d, "d2h": d2h, "blocks": len(cuts) - 1,
+            "c": (out_host[0], out_host[1][:off], out_host[2][:off])}
+
+
 def recorded_traffic(kernel: str, workload: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
     taken on the current kernel sources (else None)."""
@@ -487,44 +558,20 @@ def main():
         roofline["smem_atomic"] = {"achieved": arate, "peak": apeak, "unit": "Gop/s", "frac": arate / apeak,
                                    "peak_source": "measured (profiles/smem_atomics_gb300.md, random slots)"}
 
-    # end to end through the public API with host buffers
-    pinned = {}
-    for name, M in (("A", A), ("B", B)):
-        pinned[name] = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
-                        for x in (M.row_ptr, M.col_idx, M.val)]
-    h2d = sum(t.numel() * t.element_size() for lst in pinned.values() for t in lst)
-    copy_streams = [torch.cuda.Stream(dev) for _ in range(4)]
-    e2e_times, d2h, out_host = [], 0, None
-    for k in range(args.e2e_steps + 1):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        dev_in = {name: [torch.empty(t.shape, dtype=t.dtype, device=dev) for t in lst] for name, lst in pinned.items()}
-        chunked_copies([(d, h_) for name in ("A", "B") for d, h_ in zip(dev_in[name], pinned[name])],
-                       copy_streams, stream)
-        dAe = smash.DeviceCsr(A.rows, A.cols, *dev_in["A"])
-        dBe = smash.DeviceCsr(B.rows, B.cols, *dev_in["B"])
-        owner = None
-        if args.path == "plain":
-            Ce = h.spgemm(dAe, dBe, stream)
-        else:
-            Ce, _, owner = h.spgemm_learned(dAe, dBe, model if args.path == "learned" else None, margin=margin,
-                                            stream=stream)
-        if out_host is None or out_host[1].numel() != Ce.nnz:
-            out_host = [torch.empty(Ce.rows + 1, dtype=torch.int64).pin_memory(),
-                        torch.empty(Ce.nnz, dtype=torch.int32).pin_memory(),
-                        torch.empty(Ce.nnz, dtype=Ce.val.dtype).pin_memory()]
-        chunked_copies(list(zip(out_host, (Ce.row_ptr, Ce.col_idx, Ce.val))), copy_streams, stream)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        d2h = sum(t.numel() * t.element_size() for t in out_host)
-        if k > 0:
-            e2e_times.append(dt)
-        del Ce
-        if owner is not None:
-            owner.free()
-        del dAe, dBe, dev_in
-    e2e_s = replica_max(statistics.median(e2e_times), dist, dev)
-    del out_host, pinned
+    # end to end through the public API with host buffers: one call on the
+    # whole of A, and the same product cut into row blocks of A whose results
+    # go back to the host while the next block computes
+    single = end_to_end(h, args, A, B, flop, model, margin, stream, dev, blocks=1)
+    piped = end_to_end(h, args, A, B, flop, model, margin, stream, dev, blocks=E2E_BLOCKS)
+    # the blocked product equals the single call's: structure exactly, values up to
+    # the order of the atomic adds
+    (rp1, ci1, v1), (rp2, ci2, v2) = single["c"], piped["c"]
+    assert torch.equal(rp1, rp2) and torch.equal(ci1, ci2), "row-blocked product differs from the single call"
+    assert torch.allclose(v1.double(), v2.double(), rtol=1e-5, atol=1e-6), "row-blocked values differ"
+    del single["c"], piped["c"]
+    e2e_s = replica_max(piped["seconds"], dist, dev)
+    e2e_single_s = replica_max(single["seconds"], dist, dev)
+    h2d, d2h = piped["h2d"], piped["d2h"]
 
     step_bytes = metrics.spgemm_bytes(A.rows, A.nnz, B.rows, B.nnz, A.rows, c_nnz, vb)
     achieved_step = step_bytes / (ms / 1e3) / 1e9
@@ -545,7 +592,11 @@ def main():
         "kernels": [{k: t[k] for k in ("name", "bin", "launches", "rows", "products", "ms")} for t in
                     sorted(kt, key=lambda t: -t["ms"])[:10]],
         "e2e": {"value": replica_gflops(world, products, e2e_s), "unit": "GFLOP/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "method": "%d row blocks of A, one public call each; each block's C is copied to pinned host "
+                          "memory while the next block computes" % E2E_BLOCKS,
+                "single_call": {"value": replica_gflops(world, products, e2e_single_s), "unit": "GFLOP/s",
+                                "h2d_bytes_per_step": single["h2d"], "d2h_bytes_per_step": single["d2h"]}},
         "clocks": clocks,
         "gpu_launches": launches,
     }

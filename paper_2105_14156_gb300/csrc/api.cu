@@ -68,9 +68,14 @@ int smash_create(smash_handle **out, int device, const smash_params *params) {
     h->alloc = default_alloc;
     h->free_fn = default_free;
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device);
-    if (cudaMallocHost((void **)&h->host, kHostWords * 8 * 8) != cudaSuccess) {
+    if (cudaHostAlloc((void **)&h->host, kHostWords * 8 * 8, cudaHostAllocMapped) != cudaSuccess) {
         delete h;
         return SMASH_ERR_ALLOC;
+    }
+    if (cudaHostGetDevicePointer((void **)&h->host_dev, h->host, 0) != cudaSuccess) {
+        cudaFreeHost(h->host);
+        delete h;
+        return SMASH_ERR_CUDA;
     }
     if (ensure(h, h->err, 256, 0) != SMASH_OK || cudaMemset(h->err.ptr, 0, h->err.bytes) != cudaSuccess) {
         cudaFreeHost(h->host);
@@ -210,8 +215,7 @@ int spgemm_symbolic(smash_handle *h, const smash_csr *A, const smash_csr *B, int
         launch_scan_rowptr(pl.nnz, n, c_row_ptr, pl.total, pl.scan, s);
     }
     if ((st = last_cuda_status())) return st;
-    if (cudaMemcpyAsync(h->host, pl.total, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return SMASH_ERR_CUDA;
+    if (read_small(h, 0, pl.total, sizeof(long long), s)) return SMASH_ERR_CUDA;
     st = read_flags(h, s, true);
     *c_nnz = h->host[0];
     h->stats.c_nnz = h->host[0];
@@ -418,7 +422,7 @@ int window_plan(smash_handle *h, const RawOperands &op, int dt, int cpc, int nw,
     {
         LaunchTimer lt(h, s, "dense_plan", -1, 256, op.b_rows, 0, 0, op.b_nnz, 0);
         lt.add_kernels(launch_window_plan(dt, op, nw, per, cpc, (char *)h->split.ptr + 256, sl, h->sms, s,
-                                          (int *)((char *)h->host + 1536)));
+                                          (int *)((char *)h->host + 1536), (int *)((char *)h->host_dev + 1536)));
     }
     pc.valid = true;
     pc.b_rp = op.b_rp;

@@ -83,7 +83,8 @@ struct smash_handle {
     smash::DevBuf arena;      // learned path: dense rows' windows
     smash::DevBuf learn;      // learned path: per-row arrays
     smash::DevBuf err;        // kNumErr ints (+ scratch words)
-    long long *host = nullptr;  // pinned host staging
+    long long *host = nullptr;  // pinned host staging (mapped)
+    long long *host_dev = nullptr;  // the same buffer as the kernels see it
     smash_stats stats{};
     // Streams that run the bins of one phase side by side (created on first
     // use): a bin's kernel starts on SMs that the kernels before it release,
@@ -424,16 +425,24 @@ inline int plan_buffers(smash_handle *h, int64_t n, bool symbolic, cudaStream_t 
     return SMASH_OK;
 }
 
+// Reads `bytes` (a multiple of 4) of device memory at src into the handle's
+// pinned host buffer at byte offset off, by a kernel that writes the mapped
+// buffer: no copy engine, so a small read never queues behind the caller's
+// bulk copies on other streams. Does not wait.
+inline int read_small(smash_handle *h, size_t off, const void *src, size_t bytes, cudaStream_t s) {
+    LaunchTimer lt(h, s, "read_small", -1, 256, 0, 0, 0, 0);
+    launch_read_small(src, (char *)h->host_dev + off, bytes, s);
+    return cudaPeekAtLastError() == cudaSuccess ? SMASH_OK : SMASH_ERR_CUDA;
+}
+
 // Copy bin counts (16 int), offsets (17 int), maxsize (16 ll), stats (4 ll)
 // to the pinned host buffer and wait.
 inline int fetch_bins(smash_handle *h, const Plan &pl, cudaStream_t s, int *counts, int *offsets, long long *maxsize,
                long long *stats, long long *sums) {
     char *hb = (char *)h->host;
-    if (cudaMemcpyAsync(hb, pl.bb.counts, 16 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(hb + 64, pl.bb.offsets, 17 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(hb + 256, pl.bb.maxsize, 20 * sizeof(long long), cudaMemcpyDeviceToHost, s) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(hb + 512, pl.bb.sums, 48 * sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    if (read_small(h, 0, pl.bb.counts, 16 * sizeof(int), s) || read_small(h, 64, pl.bb.offsets, 17 * sizeof(int), s) ||
+        read_small(h, 256, pl.bb.maxsize, 20 * sizeof(long long), s) ||
+        read_small(h, 512, pl.bb.sums, 48 * sizeof(long long), s))
         return SMASH_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SMASH_ERR_CUDA;
     memcpy(counts, hb, 16 * sizeof(int));
@@ -454,8 +463,7 @@ inline int fetch_bins(smash_handle *h, const Plan &pl, cudaStream_t s, int *coun
 
 inline int read_flags(smash_handle *h, cudaStream_t s, bool clear) {
     char *hb = (char *)h->host + 1024;
-    if (cudaMemcpyAsync(hb, h->err.ptr, kNumErr * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return SMASH_ERR_CUDA;
+    if (read_small(h, 1024, h->err.ptr, kNumErr * sizeof(int), s)) return SMASH_ERR_CUDA;
     if (clear && cudaMemsetAsync(h->err.ptr, 0, kNumErr * sizeof(int), s) != cudaSuccess) return SMASH_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SMASH_ERR_CUDA;
     const int st = status_from_flags((const long long *)hb);

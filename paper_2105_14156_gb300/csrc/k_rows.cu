@@ -208,6 +208,16 @@ __global__ void __launch_bounds__(256) k_rowinfo_cached(RawOperands op, const in
     st.flush(bb);
 }
 
+// Small reads for the host: device words into mapped host memory.
+__global__ void __launch_bounds__(256) k_read_small(const unsigned *src, unsigned *dst, int words) {
+    for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+}
+
+void launch_read_small(const void *src, void *dst_mapped, size_t bytes, cudaStream_t s) {
+    const int words = (int)(bytes / 4);
+    if (words > 0) k_read_small<<<1, 256, 0, s>>>((const unsigned *)src, (unsigned *)dst_mapped, words);
+}
+
 // Short rows: one thread per row. Long rows: appended to long_list.
 template <bool LEARN>
 __global__ void __launch_bounds__(256) k_rowinfo(RawOperands op, const int64_t *c_rp, int64_t c_nnz, BinRule rule,

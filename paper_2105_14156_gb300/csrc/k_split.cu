@@ -182,7 +182,7 @@ size_t window_plan_bytes(const RawOperands &op, int nw, size_t vsz) {
 }
 
 int launch_window_plan(int dtype, const RawOperands &op, int nwin, int per, int cpc, void *ws, BSlices &sl,
-                       int sms, cudaStream_t s, int *host_word) {
+                       int sms, cudaStream_t s, int *host_word, int *host_word_dev) {
     const int nw = nwin * per;   // slices
     sl.nslices = nw;
     sl.cpc = cpc;
@@ -213,7 +213,7 @@ int launch_window_plan(int dtype, const RawOperands &op, int nwin, int per, int 
     if (per == 1) {
         cudaMemsetAsync(unsorted, 0, sizeof(int), s);
         k_check_sorted<<<grid, kSplitNT, 0, s>>>(op.b_rp, op.b_ci, op.b_rows, op.b_nnz, unsorted);
-        cudaMemcpyAsync(host_word, unsorted, sizeof(int), cudaMemcpyDeviceToHost, s);
+        launch_read_small(unsorted, host_word_dev, sizeof(int), s);
         cudaStreamSynchronize(s);
         sorted = *host_word == 0;
     }

@@ -163,6 +163,9 @@ struct NumOut {
     int64_t c_nnz;
     int *row_nnz = nullptr;  // capacity mode (learned sizing) when set, see k_numeric.cu
 };
+// Copy of `bytes` (a multiple of 4) of device memory into mapped host memory
+// by a kernel (k_rows.cu).
+void launch_read_small(const void *src, void *dst_mapped, size_t bytes, cudaStream_t s);
 // rec (may be null): per-row product counts; rows with nothing to merge
 // (exact mode) or whose products fit their room (capacity mode) skip the table.
 void launch_num_hash(int dtype, const RawOperands &op, const int *rows, int count, int *token,
@@ -229,11 +232,12 @@ struct BSlices {
 size_t window_plan_bytes(const RawOperands &op, int nw, size_t vsz);
 // Most slices of B the slicing pass supports.
 int window_plan_max_slices();
-// host_word: pinned host int (the sortedness of B is read back). Returns the
-// number of kernels launched.
+// host_word: pinned, mapped host int (the sortedness of B is read back),
+// host_word_dev: the same int as the kernels see it. Returns the number of
+// kernels launched.
 // nw windows of cpc columns, per slices per window (1: the window itself).
 int launch_window_plan(int dtype, const RawOperands &op, int nw, int per, int cpc, void *ws, BSlices &sl, int sms,
-                       cudaStream_t s, int *host_word);
+                       cudaStream_t s, int *host_word, int *host_word_dev);
 // Widest column window (a multiple of kSubCols, at most kMaxWinCols) of the
 // numeric dense kernel at `blocks_per_sm` resident blocks per SM; 0: none.
 constexpr int kMaxWinCols = 65536;

@@ -253,8 +253,7 @@ int smash_training_rows(smash_handle *h, const smash_csr *A, const smash_csr *B,
         launch_training_rows(n, pl.nnz, bound, ftmp, keep, pos, total, scan, feats, targets, h->sms, s);
     }
     if ((st = last_cuda_status())) return st;
-    if (cudaMemcpyAsync(h->host, total, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return SMASH_ERR_CUDA;
+    if (read_small(h, 0, total, sizeof(long long), s)) return SMASH_ERR_CUDA;
     st = read_flags(h, s, true);
     *count = h->host[0];
     return st;
@@ -524,8 +523,7 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
         launch_scan_rowptr(cap, n, stage_rp, ctr, scan, s);
     }
     if ((st = last_cuda_status())) return st;
-    if (cudaMemcpyAsync(h->host, ctr, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
+    if (read_small(h, 0, ctr, sizeof(long long), s) || cudaStreamSynchronize(s) != cudaSuccess)
         return SMASH_ERR_CUDA;
     const long long staged = h->host[0];
     ls.staged_nnz = staged + (use_arena ? ar.cap : 0);
@@ -550,8 +548,7 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
         launch_overflow_list(row_nnz, n, list, (int *)(ctr + 1), ovf, s);
         if (use_arena) launch_mark_rows(arena_rows, nd, row_nnz, ovf, s);
     }
-    if (cudaMemcpyAsync(h->host, ctr + 1, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
+    if (read_small(h, 0, ctr + 1, sizeof(long long), s) || cudaStreamSynchronize(s) != cudaSuccess)
         return SMASH_ERR_CUDA;
     const int novf = (int)(h->host[0] & 0xffffffff);
     ls.overflow_rows = novf;
@@ -565,8 +562,7 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
         LaunchTimer lt(h, s, "scan_rowptr", -1, 512, n, 0, 0, 0, 3);
         launch_scan_rowptr(row_nnz, n, C->row_ptr, ctr + 2, scan, s);
     }
-    if (cudaMemcpyAsync(h->host, ctr + 2, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
+    if (read_small(h, 0, ctr + 2, sizeof(long long), s) || cudaStreamSynchronize(s) != cudaSuccess)
         return SMASH_ERR_CUDA;
     const long long cnnz = h->host[0];
     C->nnz = cnnz;
