@@ -26,6 +26,10 @@
  *  - The library never frees memory it did not allocate. Scratch memory is
  *    owned by the handle (grown on demand through the handle's allocator).
  *  - A handle is not thread-safe: one host thread per handle at a time.
+ *  - Calls that return host values (spgemm_symbolic's nnz, spgemm_learned's
+ *    sizes) wait on the call's stream only, and read their small counts back
+ *    through mapped pinned memory, not through copies: copies the caller runs
+ *    on other streams overlap them instead of delaying them.
  */
 #ifndef SMASH_H
 #define SMASH_H
