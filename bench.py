@@ -428,6 +428,8 @@ def main():
     ap.add_argument("--path", default="learned", choices=sorted(PATHS))
     ap.add_argument("--cpu-products", type=float, default=1e8)
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-blocks", type=int, default=E2E_BLOCKS,
+                    help="row blocks of A in the end-to-end measurement (1: one call)")
     ap.add_argument("--variants", default="all", choices=["all", "none"])
     ap.add_argument("--variant-steps", type=int, default=10)
     ap.add_argument("--no-autotune", action="store_true")
@@ -562,7 +564,7 @@ def main():
     # whole of A, and the same product cut into row blocks of A whose results
     # go back to the host while the next block computes
     single = end_to_end(h, args, A, B, flop, model, margin, stream, dev, blocks=1)
-    piped = end_to_end(h, args, A, B, flop, model, margin, stream, dev, blocks=E2E_BLOCKS)
+    piped = end_to_end(h, args, A, B, flop, model, margin, stream, dev, blocks=max(1, args.e2e_blocks))
     # the blocked product equals the single call's: structure exactly, values up to
     # the order of the atomic adds
     (rp1, ci1, v1), (rp2, ci2, v2) = single["c"], piped["c"]
@@ -594,7 +596,7 @@ def main():
         "e2e": {"value": replica_gflops(world, products, e2e_s), "unit": "GFLOP/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "method": "%d row blocks of A, one public call each; each block's C is copied to pinned host "
-                          "memory while the next block computes" % E2E_BLOCKS,
+                          "memory while the next block computes" % piped["blocks"],
                 "single_call": {"value": replica_gflops(world, products, e2e_single_s), "unit": "GFLOP/s",
                                 "h2d_bytes_per_step": single["h2d"], "d2h_bytes_per_step": single["d2h"]}},
         "clocks": clocks,
