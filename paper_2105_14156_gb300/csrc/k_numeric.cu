@@ -27,9 +27,11 @@
 namespace smash {
 
 // ----- shared-memory hash rows -----------------------------------------------
-template <typename V, int GS, int NT>
 // (the register cap of 64 lets 2048 threads per SM be resident: measured
-// faster than the uncapped kernel at 72 registers and 43 % of the warps)
+// faster than the uncapped kernel at 72 registers and 43 % of the warps).
+// CAP: capacity mode (out.row_nnz set); each mode leaves out the code the
+// other needs.
+template <typename V, int GS, int NT, bool CAP>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_num_hash(Operands<V> op, const int *rows, int count, int *token,
                                                  int tbits, HashCfg hc, int bsh, int bcap, int bm_words,
                                                  int bitmap_ratio, const RowGather *rec, NumOutT<V> out,
@@ -90,8 +92,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_num_hash(Operands<V> op, cons
         constexpr bool kStage = sizeof(V) == 4;
         const long long f_i = kStage && ok ? f_rec : -1;
         const bool direct =
-            kStage && !out.row_nnz && bsh >= 0 && f_i >= 0 && f_i == (long long)n_exp && f_i <= bcap;
-        const bool merge = kStage && out.row_nnz && bsh >= 0 && !use_bm && f_i >= 0 && f_i <= (long long)n_exp &&
+            kStage && !CAP && bsh >= 0 && f_i >= 0 && f_i == (long long)n_exp && f_i <= bcap;
+        const bool merge = kStage && CAP && bsh >= 0 && !use_bm && f_i >= 0 && f_i <= (long long)n_exp &&
                            2 * f_i <= T && f_i <= bcap;
         int tot, o;
         if (direct || merge) {
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_num_hash(Operands<V> op, cons
                         ++cnt;
                         if (bsh >= 0) atomicAdd(bc + (j >> bsh), 1);   // bucket counts for the write-out
                     }
-                } else if (out.row_nnz) {
+                } else if (CAP) {
                     ovf = 1;
                 } else {
                     raise_err(err, kErrTableFull);
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_num_hash(Operands<V> op, cons
             continue;
         }
         bool over = false;
-        if (out.row_nnz) {
+        if (CAP) {
             over = o != 0 || tot > n_exp;
             if (t == 0) out.row_nnz[i] = over ? -1 : tot;
             n_exp = tot;
@@ -763,7 +765,7 @@ static void num_hash_go(const Operands<V> &op, const int *rows, int count, int *
     if (bcap > 0 && num_hash_smem<V>(hl.tbits, GS, bm_words, bcap) > lim) bcap = 0;
     const bool buckets = bcap > 0;
     const size_t smem = num_hash_smem<V>(hl.tbits, GS, bm_words, bcap);
-    auto kern = k_num_hash<V, GS, NT>;
+    auto kern = out.row_nnz ? k_num_hash<V, GS, NT, true> : k_num_hash<V, GS, NT, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int grid = resident_grid(kern, NT, smem, hl.sms, (count + groups - 1) / groups);
     const HashCfg hc{hl.hash_kind, hl.colbits};
