@@ -546,102 +546,254 @@ void launch_overflow_list(const int *row_nnz, int64_t n, int *list, int *count, 
     k_overflow_list<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(row_nnz, n, list, count, ovf);
 }
 
-// Copy each staged row that fitted to its place in C. Work is split by output
-// position: a warp owns a chunk of kCompactChunk consecutive entries of C. It
-// finds the first row reaching into the chunk by a 32-way search on C's row
-// pointer (each round the lanes test 32 evenly spaced rows, so four rounds
-// cover a million rows), loads the row pointers, staging offsets and
-// overflow flags of the next 32 rows in one coalesced round trip, and walks
-// those rows copying each overlap with all lanes, four loads per lane issued
-// before their stores (equal work per warp whatever the row lengths).
-constexpr int64_t kCompactChunk = 2048;
+// Copy each staged row that fitted to its place in C, split by output
+// position so that every warp moves the same number of entries whatever the
+// row lengths. Two kernels:
+//  * k_compact_walk, for outputs where long stretches belong to rows written
+//    elsewhere (the column-window arena's rows, overflowing rows): a warp
+//    owns kWalkChunk consecutive entries of C, finds the first row reaching
+//    into them by a 32-way search on C's row pointer (each round the lanes
+//    test 32 evenly spaced rows, so four rounds cover a million rows), and
+//    walks the rows 32 at a time (their bounds, staging offsets and flags in
+//    one coalesced round trip), copying each overlap with all lanes, four
+//    loads per lane issued before their stores; a skipped row costs one step.
+//  * k_compact_rows, for outputs made almost wholly of staged rows: a block
+//    owns kCompactChunk consecutive entries, takes its first and last rows
+//    from a table (k_chunk_rows) and lists, for each row in between, its start
+//    relative to the chunk and the distance from its place in C to its staged
+//    copy (a sentinel for a skipped row) in shared memory. Each warp takes an
+//    eighth of the chunk, lanes on consecutive entries (the stores line up
+//    with 128-byte lines); a lane finds an entry's row by a galloping search
+//    from its previous entry's row, and eight float (four double) loads are
+//    issued before their stores. A chunk spanning more rows than the list
+//    holds (many rows of a few entries) is walked as in k_compact_walk.
+constexpr int64_t kWalkChunk = 2048;
+constexpr int64_t kCompactChunk = 8192;
+constexpr int kCompactNT = 256;
+constexpr int kCompactRows = 1024;
+constexpr int kCompactBatch = 8;
+constexpr int64_t kCompactSkip = INT64_MIN;
 
-template <typename V>
-__global__ void __launch_bounds__(256) k_compact_rows(int64_t n, int64_t c_nnz, const int64_t *__restrict__ stage_rp,
-                                                      const uint8_t *__restrict__ ovf, const int32_t *__restrict__ sci,
-                                                      const V *__restrict__ sval, const int64_t *__restrict__ c_rp,
-                                                      int32_t *__restrict__ cci, V *__restrict__ cval) {
+// Last row r in [0, n) with c_rp[r] <= p (c_rp[0] = 0 <= p < c_rp[n]); all
+// lanes of the warp take part and return it.
+__device__ __forceinline__ int64_t compact_find_row(const int64_t *__restrict__ c_rp, int64_t n, int64_t p) {
     const int lane = lane_id();
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t nchunks = (c_nnz + kCompactChunk - 1) / kCompactChunk;
-    for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < nchunks; ch += warps) {
-        const int64_t p0 = ch * kCompactChunk;
-        const int64_t p1 = p0 + kCompactChunk < c_nnz ? p0 + kCompactChunk : c_nnz;
-        // last row r with c_rp[r] <= p0, in [lo, hi) (c_rp[0] = 0 <= p0, c_rp[n] = c_nnz > p0)
-        int64_t lo = 0, hi = n;
-        while (hi - lo > 1) {
-            const int64_t step = (hi - lo + 31) / 32;
-            const int64_t x = lo + lane * step;
-            const bool le = x < hi && __ldg(c_rp + x) <= p0;
-            const int cnt = __popc(__ballot_sync(kFull, le));   // rows lo, lo+step, ... that start at or before p0
-            const int64_t nlo = lo + (int64_t)(cnt - 1) * step;
-            const int64_t nhi = nlo + step < hi ? nlo + step : hi;
-            lo = nlo;
-            hi = nhi;
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t x = lo + lane * step;
+        const bool le = x < hi && __ldg(c_rp + x) <= p;
+        const int cnt = __popc(__ballot_sync(kFull, le));   // rows lo, lo+step, ... that start at or before p
+        const int64_t nlo = lo + (int64_t)(cnt - 1) * step;
+        const int64_t nhi = nlo + step < hi ? nlo + step : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    return lo;
+}
+
+// Copies C entries [p0, p1) row by row with one warp, from row r_first (the
+// row holding p0) on.
+template <typename V>
+__device__ void compact_walk(int64_t n, int64_t p0, int64_t p1, int64_t r_first, const int64_t *__restrict__ stage_rp,
+                             const uint8_t *__restrict__ ovf, const int32_t *__restrict__ sci,
+                             const V *__restrict__ sval, const int64_t *__restrict__ c_rp, int32_t *__restrict__ cci,
+                             V *__restrict__ cval) {
+    const int lane = lane_id();
+    int64_t p = p0;
+    for (int64_t r0 = r_first; p < p1 && r0 < n; r0 += 32) {
+        // rows r0 .. r0+31: lane l holds row r0+l's bounds, staging offset and flag
+        const int64_t rl = r0 + lane;
+        int64_t rb = p1, re = p1, sb = 0;
+        bool skip = true;
+        if (rl < n) {
+            rb = __ldg(c_rp + rl);
+            re = __ldg(c_rp + rl + 1);
+            sb = __ldg(stage_rp + rl);
+            skip = ovf[rl] != 0;
         }
-        int64_t p = p0;
-        for (int64_t r0 = lo; p < p1 && r0 < n; r0 += 32) {
-            // rows r0 .. r0+31: lane l holds row r0+l's bounds, staging offset and flag
-            const int64_t rl = r0 + lane;
-            int64_t rb = c_nnz, re = c_nnz, sb = 0;
-            bool skip = true;
-            if (rl < n) {
-                rb = __ldg(c_rp + rl);
-                re = __ldg(c_rp + rl + 1);
-                sb = __ldg(stage_rp + rl);
-                skip = ovf[rl] != 0;
-            }
-            for (int j = 0; j < 32 && p < p1; ++j) {
-                const int64_t b0 = __shfl_sync(kFull, rb, j), e0 = __shfl_sync(kFull, re, j);
-                const int64_t s0 = __shfl_sync(kFull, sb, j);
-                const bool sk = __shfl_sync(kFull, skip ? 1 : 0, j) != 0;
-                const int64_t a = p > b0 ? p : b0;
-                const int64_t b = p1 < e0 ? p1 : e0;
-                if (b > a && !sk) {
-                    const int64_t src = s0 + (a - b0);
-                    const int m = (int)(b - a);
-                    for (int k0 = 0; k0 < m; k0 += 128) {
-                        int32_t ci[4];
-                        V va[4];
+        for (int j = 0; j < 32 && p < p1; ++j) {
+            const int64_t b0 = __shfl_sync(kFull, rb, j), e0 = __shfl_sync(kFull, re, j);
+            const int64_t s0 = __shfl_sync(kFull, sb, j);
+            const bool sk = __shfl_sync(kFull, skip ? 1 : 0, j) != 0;
+            const int64_t a = p > b0 ? p : b0;
+            const int64_t b = p1 < e0 ? p1 : e0;
+            if (b > a && !sk) {
+                const int64_t src = s0 + (a - b0);
+                const int m = (int)(b - a);
+                for (int k0 = 0; k0 < m; k0 += 128) {
+                    int32_t ci[4];
+                    V va[4];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int k = k0 + 32 * u + lane;
-                            if (k < m) {
-                                ci[u] = __ldg(sci + src + k);
-                                va[u] = __ldg(sval + src + k);
-                            }
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = k0 + 32 * u + lane;
+                        if (k < m) {
+                            ci[u] = __ldg(sci + src + k);
+                            va[u] = __ldg(sval + src + k);
                         }
+                    }
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int k = k0 + 32 * u + lane;
-                            if (k < m) {
-                                cci[a + k] = ci[u];
-                                cval[a + k] = va[u];
-                            }
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = k0 + 32 * u + lane;
+                        if (k < m) {
+                            cci[a + k] = ci[u];
+                            cval[a + k] = va[u];
                         }
                     }
                 }
-                if (e0 > p) p = e0;
             }
+            if (e0 > p) p = e0;
         }
     }
 }
 
-void launch_compact_rows(int dtype, int64_t n, const int64_t *stage_rp, const int *row_nnz_final,
-                         const uint8_t *ovf, const int32_t *stage_ci, const void *stage_val, const int64_t *c_rp,
-                         int32_t *c_ci, void *c_val, int64_t c_nnz, int sms, cudaStream_t s) {
-    (void)row_nnz_final;
+template <typename V>
+__global__ void __launch_bounds__(256) k_compact_walk(int64_t n, int64_t c_nnz, const int64_t *__restrict__ stage_rp,
+                                                      const uint8_t *__restrict__ ovf, const int32_t *__restrict__ sci,
+                                                      const V *__restrict__ sval, const int64_t *__restrict__ c_rp,
+                                                      int32_t *__restrict__ cci, V *__restrict__ cval) {
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nchunks = (c_nnz + kWalkChunk - 1) / kWalkChunk;
+    for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < nchunks; ch += warps) {
+        const int64_t p0 = ch * kWalkChunk;
+        const int64_t p1 = p0 + kWalkChunk < c_nnz ? p0 + kWalkChunk : c_nnz;
+        compact_walk(n, p0, p1, compact_find_row(c_rp, n, p0), stage_rp, ovf, sci, sval, c_rp, cci, cval);
+    }
+}
+
+// Row holding the first entry of each chunk of kCompactChunk entries of C (a
+// thread per row marks the chunks that start inside it).
+__global__ void __launch_bounds__(256) k_chunk_rows(int64_t n, const int64_t *__restrict__ c_rp, int *__restrict__ first) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        const int64_t b = __ldg(c_rp + r), e = __ldg(c_rp + r + 1);
+        for (int64_t k = (b + kCompactChunk - 1) / kCompactChunk; k * kCompactChunk < e; ++k) first[k] = (int)r;
+    }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kCompactNT, 4) k_compact_rows(int64_t n, int64_t c_nnz, const int64_t *__restrict__ stage_rp,
+                                                             const uint8_t *__restrict__ ovf,
+                                                             const int32_t *__restrict__ sci, const V *__restrict__ sval,
+                                                             const int64_t *__restrict__ c_rp, const int *__restrict__ first,
+                                                             int32_t *__restrict__ cci, V *__restrict__ cval) {
+    constexpr int kB = sizeof(V) == 4 ? kCompactBatch : kCompactBatch / 2;
+    __shared__ int s_start[kCompactRows];
+    __shared__ int64_t s_delta[kCompactRows];
+    __shared__ int64_t s_last;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
+    const int64_t nchunks = (c_nnz + kCompactChunk - 1) / kCompactChunk;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int64_t p0 = ch * kCompactChunk;
+        const int64_t p1 = p0 + kCompactChunk < c_nnz ? p0 + kCompactChunk : c_nnz;
+        // rows holding entries p0 and p1 - 1 (rl may also be the row starting at p1)
+        const int64_t rf = __ldg(first + ch);
+        int64_t rl;
+        if (ch + 1 < nchunks) {
+            rl = __ldg(first + ch + 1);
+        } else {
+            if (warp == 0) {
+                const int64_t r = compact_find_row(c_rp, n, p1 - 1);
+                if (lane == 0) s_last = r;
+            }
+            __syncthreads();
+            rl = s_last;
+        }
+        const int nr = (int)(rl - rf + 1 < (int64_t)kCompactRows + 1 ? rl - rf + 1 : (int64_t)kCompactRows + 1);
+        if (nr <= kCompactRows) {
+            for (int k = tid; k < nr; k += kCompactNT) {
+                const int64_t r = rf + k;
+                const int64_t b = __ldg(c_rp + r);
+                s_start[k] = b > p0 ? (int)(b - p0) : 0;
+                s_delta[k] = ovf[r] ? kCompactSkip : __ldg(stage_rp + r) - b;
+            }
+            __syncthreads();
+            const int m = (int)(p1 - p0);
+            constexpr int kPerWarp = (int)(kCompactChunk / (kCompactNT / 32));
+            int k = 0;  // row of the lane's previous entry: entries rise, so rows do
+            for (int q0 = warp * kPerWarp; q0 < (warp + 1) * kPerWarp && q0 < m; q0 += 32 * kB) {
+                int32_t ci[kB];
+                V va[kB];
+                bool ok[kB];
+#pragma unroll
+                for (int u = 0; u < kB; ++u) {
+                    const int q = q0 + u * 32 + lane;
+                    ok[u] = false;
+                    if (q < m) {
+                        if (k + 1 < nr && s_start[k + 1] <= q) {
+                            // gallop from k + 1, then bisect: last row with start <= q
+                            int lo = k + 1, step = 1;
+                            while (lo + step < nr && s_start[lo + step] <= q) {
+                                lo += step;
+                                step <<= 1;
+                            }
+                            int hi = lo + step < nr ? lo + step : nr;
+                            while (hi - lo > 1) {
+                                const int mid = (lo + hi) >> 1;
+                                if (s_start[mid] <= q) lo = mid;
+                                else hi = mid;
+                            }
+                            k = lo;
+                        }
+                        const int64_t d = s_delta[k];
+                        if (d != kCompactSkip) {
+                            ok[u] = true;
+                            ci[u] = __ldcs(sci + p0 + q + d);
+                            va[u] = __ldcs(sval + p0 + q + d);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kB; ++u) {
+                    const int q = q0 + u * 32 + lane;
+                    if (ok[u]) {
+                        __stcs(cci + p0 + q, ci[u]);
+                        __stcs(cval + p0 + q, va[u]);
+                    }
+                }
+            }
+        } else {
+            const int64_t per = (p1 - p0 + kCompactNT / 32 - 1) / (kCompactNT / 32);
+            const int64_t a = p0 + warp * per;
+            const int64_t b = a + per < p1 ? a + per : p1;
+            if (a < b) compact_walk(n, a, b, compact_find_row(c_rp, n, a), stage_rp, ovf, sci, sval, c_rp, cci, cval);
+        }
+        __syncthreads();
+    }
+}
+
+size_t compact_table_bytes(int64_t c_nnz) {
+    return sizeof(int) * (size_t)((c_nnz + kCompactChunk - 1) / kCompactChunk);
+}
+
+void launch_compact_rows(int dtype, int64_t n, const int64_t *stage_rp, const uint8_t *ovf, const int32_t *stage_ci,
+                         const void *stage_val, const int64_t *c_rp, int32_t *c_ci, void *c_val, int64_t c_nnz,
+                         int *table, int sms, cudaStream_t s) {
     if (n == 0 || c_nnz <= 0) return;
+    if (!table) {
+        const int64_t blocks = ((c_nnz + kWalkChunk - 1) / kWalkChunk + 7) / 8;
+        const int64_t cap = (int64_t)sms * 8;
+        const int grid = (int)(blocks < cap ? blocks : cap);
+        if (dtype)
+            k_compact_walk<double><<<grid, 256, 0, s>>>(n, c_nnz, stage_rp, ovf, stage_ci, (const double *)stage_val,
+                                                        c_rp, c_ci, (double *)c_val);
+        else
+            k_compact_walk<float><<<grid, 256, 0, s>>>(n, c_nnz, stage_rp, ovf, stage_ci, (const float *)stage_val,
+                                                       c_rp, c_ci, (float *)c_val);
+        return;
+    }
+    k_chunk_rows<<<rowinfo_grid(n, sms), 256, 0, s>>>(n, c_rp, table);
     const int64_t chunks = (c_nnz + kCompactChunk - 1) / kCompactChunk;
-    const int64_t blocks = (chunks + 7) / 8;
-    const int64_t cap = (int64_t)sms * 8;
-    const int grid = (int)(blocks < cap ? blocks : cap);
+    const int64_t cap = (int64_t)sms * 4;
+    const int grid = (int)(chunks < cap ? chunks : cap);
     if (dtype)
-        k_compact_rows<double><<<grid, 256, 0, s>>>(n, c_nnz, stage_rp, ovf, stage_ci, (const double *)stage_val,
-                                                    c_rp, c_ci, (double *)c_val);
+        k_compact_rows<double><<<grid, kCompactNT, 0, s>>>(n, c_nnz, stage_rp, ovf, stage_ci,
+                                                           (const double *)stage_val, c_rp, table, c_ci,
+                                                           (double *)c_val);
     else
-        k_compact_rows<float><<<grid, 256, 0, s>>>(n, c_nnz, stage_rp, ovf, stage_ci, (const float *)stage_val,
-                                                   c_rp, c_ci, (float *)c_val);
+        k_compact_rows<float><<<grid, kCompactNT, 0, s>>>(n, c_nnz, stage_rp, ovf, stage_ci,
+                                                          (const float *)stage_val, c_rp, table, c_ci,
+                                                          (float *)c_val);
 }
 
 void launch_bin_scatter(int64_t n, BinBuffers bb, cudaStream_t s) {

@@ -78,9 +78,14 @@ void launch_learned_bin(const RawOperands &op, const BinRule &rule, BinBuffers b
 // Learned path helpers (k_rows.cu): rows with row_nnz < 0 -> list; copy the
 // staged rows that fitted into C.
 void launch_overflow_list(const int *row_nnz, int64_t n, int *list, int *count, uint8_t *ovf, cudaStream_t s);
-void launch_compact_rows(int dtype, int64_t n, const int64_t *stage_rp, const int *row_nnz_final,
-                         const uint8_t *ovf, const int32_t *stage_ci, const void *stage_val, const int64_t *c_rp,
-                         int32_t *c_ci, void *c_val, int64_t c_nnz, int sms, cudaStream_t s);
+// Bytes of the chunk table launch_compact_rows takes for a C of c_nnz entries.
+size_t compact_table_bytes(int64_t c_nnz);
+// table: compact_table_bytes(c_nnz) bytes of scratch for the block copy (most
+// rows staged), or null for the row walk (long stretches of C written
+// elsewhere: the arena's rows).
+void launch_compact_rows(int dtype, int64_t n, const int64_t *stage_rp, const uint8_t *ovf, const int32_t *stage_ci,
+                         const void *stage_val, const int64_t *c_rp, int32_t *c_ci, void *c_val, int64_t c_nnz,
+                         int *table, int sms, cudaStream_t s);
 
 // k_mlp.cu: row-size predictor (see the file for the network).
 constexpr int kMlpParams = 4673;

@@ -572,9 +572,13 @@ int spgemm_learned(smash_handle *h, const smash_csr *A, const smash_csr *B, smas
         C->val = h->alloc(vsz * (size_t)cnnz, h->ctx);
         if (!C->col_idx || !C->val) return SMASH_ERR_ALLOC;
         {
-            LaunchTimer lt(h, s, "compact_rows", -1, 256, n, 0, 0, cnnz);
-            launch_compact_rows(dt, n, stage_rp, row_nnz, ovf, stage_ci, stage_val, C->row_ptr, C->col_idx, C->val,
-                                cnnz, h->sms, s);
+            // without an arena nearly every row was staged: block copy, its chunk
+            // table in the planning scratch (free by now) when it fits there
+            int *table = !use_arena && compact_table_bytes(cnnz) <= sizeof(RowGather) * (size_t)n ? (int *)gather
+                                                                                                   : nullptr;
+            LaunchTimer lt(h, s, "compact_rows", -1, 256, n, 0, 0, cnnz, table ? 2 : 1);
+            launch_compact_rows(dt, n, stage_rp, ovf, stage_ci, stage_val, C->row_ptr, C->col_idx, C->val, cnnz,
+                                table, h->sms, s);
         }
         if (use_arena) {
             LaunchTimer lt(h, s, "compact_arena", -1, 256, nd, 0, 0, cnnz);

@@ -347,3 +347,44 @@ def test_bound_sized_thread_group_merge(handle, values, group_shift):
         handle.set_params(**defaults)
     assert_matches_oracle(Ch, A, B)
     assert stats["overflow_rows"] == 0
+
+
+def _vstack(*mats):
+    from paper_2105_14156_gb300.rmat import Csr
+    rp = [np.zeros(1, np.int64)]
+    base = 0
+    for m in mats:
+        rp.append(m.row_ptr[1:] + base)
+        base += m.nnz
+    return Csr(sum(m.rows for m in mats), mats[0].cols, np.concatenate(rp),
+               np.concatenate([m.col_idx for m in mats]), np.concatenate([m.val for m in mats]))
+
+
+@pytest.mark.parametrize("margin", [0.15, -0.6, 3.0, None])
+@pytest.mark.parametrize("values", ["f32", "f64"])
+def test_learned_compaction_mixed_row_lengths(handle, trained, margin, values):
+    """The copy of staged rows into C over stretches of rows of a few entries
+    (a stretch of output spans more rows than a block lists, so its warps walk
+    the rows), rows of a few hundred entries (rows listed in shared memory),
+    rows of ~16,000 entries (stretches inside one row, skipped whole when the
+    row is written elsewhere), empty rows between, and overflowing rows the
+    copy skips (negative margin); None sizes every row by its bound."""
+    from paper_2105_14156_gb300 import smash
+    from tests.helpers import random_csr
+    model, _, _ = trained
+    A = _vstack(random_csr(20000, 2000, 0.00025, 401, values=values),
+                random_csr(1500, 2000, 0.015, 402, values=values),
+                random_csr(4, 2000, 3.0, 406, values=values),
+                random_csr(20000, 2000, 0.00025, 403, values=values),
+                random_csr(700, 2000, 0.015, 404, values=values))
+    B = random_csr(2000, 80000, 0.000125, 405, values=values)
+    C, stats, owner = handle.spgemm_learned(smash.to_device(A), smash.to_device(B),
+                                            None if margin is None else model,
+                                            **({} if margin is None else {"margin": margin}))
+    handle.check()
+    Ch = C.to_host()
+    owner.free()
+    assert_matches_oracle(Ch, A, B)
+    assert stats["c_nnz"] == Ch.col_idx.size
+    if margin is not None and margin < 0:
+        assert stats["overflow_rows"] > 0
