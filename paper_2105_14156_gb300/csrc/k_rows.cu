@@ -145,7 +145,7 @@ __device__ __forceinline__ long long row_size(int64_t i, long long f, const RawO
 // Learned planning, second pass: one warp per 32 rows through the predictor
 // (mlp_forward_warp), capacity cap_i = cap_of(y_i, margin, min(flop_i,
 // cols(B))), bin of the row by cap_i.
-__global__ void __launch_bounds__(256) k_learned_bin(RawOperands op, BinRule rule, BinBuffers bb, LearnArgs la,
+__global__ void __launch_bounds__(256, 4) k_learned_bin(RawOperands op, BinRule rule, BinBuffers bb, LearnArgs la,
                                                      int64_t nrows) {
     __shared__ RowStats st;
     extern __shared__ __align__(16) float s_mlp[];   // the predictor's weights (mlp.cuh)

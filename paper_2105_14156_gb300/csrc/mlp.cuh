@@ -50,35 +50,34 @@ __device__ __forceinline__ void row_features(long long na, long long f, long lon
 }
 
 // Shared-memory copy of the inference weights (fp32) laid out for the
-// forward pass below: W1 rows padded to 8 with b1 in slot 6, W2 transposed,
-// then b2, w3, b3 and the feature normalisation (mean[6], inv_std[6]).
+// forward passes below: W1 rows padded to 8 with b1 in slot 6, b2, w3, b3 and
+// the feature normalisation (mean[6], inv_std[6]); then, for mlp_forward
+// only, W2 transposed.
 constexpr int kSmW1 = 0;                       // [64][8]
-constexpr int kSmW2T = kSmW1 + kHid * 8;       // [64][64], W2T[v][u] = W2[u][v]
-constexpr int kSmB2 = kSmW2T + kHid * kHid;
+constexpr int kSmB2 = kSmW1 + kHid * 8;
 constexpr int kSmW3 = kSmB2 + kHid;
 constexpr int kSmB3 = kSmW3 + kHid;
 constexpr int kSmNorm = kSmB3 + 4;
-constexpr int kSmFloats = kSmNorm + 2 * kFeat;
-// Tensor-core pass (mlp_forward_warp): W2 as bf16 in the order of the mma
-// B fragments, frag[kt][nt][lane] = {b0, b1} (4 x 8 x 32 uint2), after the
-// fp32 part; then one h1 tile per warp of the block, 32 rows x 64 bf16 with a
-// row stride of 36 words (conflict-free A-fragment reads).
-constexpr int kSmW2Frag = kSmFloats;                  // in 4-byte words
+constexpr int kSmSmall = kSmNorm + 2 * kFeat;  // end of the part both passes read
+constexpr int kSmW2T = kSmSmall;               // [64][64], W2T[v][u] = W2[u][v]
+constexpr int kSmFloats = kSmW2T + kHid * kHid;
+static_assert(kSmSmall % 4 == 0, "16-byte alignment of W2T and of the bf16 fragments");
+
+// Tensor-core pass (mlp_forward_warp): the part both passes read, then W2 as
+// bf16 in the order of the mma B fragments, frag[kt][nt][lane] = {b0, b1}
+// (4 x 8 x 32 uint2); then one h1 tile per warp of the block, 32 rows x 64
+// bf16 with a row stride of 36 words (conflict-free A-fragment reads).
+constexpr int kSmW2Frag = kSmSmall;                   // in 4-byte words
 constexpr int kH1Stride = 36;                         // words per row of an h1 tile
 constexpr int kSmH1 = kSmW2Frag + 4 * 8 * 32 * 2;
 constexpr int kH1Words = 32 * kH1Stride;              // per warp
 __host__ __device__ constexpr int mlp_tc_words(int warps) { return kSmH1 + warps * kH1Words; }
-static_assert(kSmFloats % 4 == 0, "alignment of the bf16 fragments");
 
-__device__ __forceinline__ void load_mlp(float *sm, const __nv_bfloat16 *wb, const float *norm) {
+__device__ __forceinline__ void load_mlp_small(float *sm, const __nv_bfloat16 *wb, const float *norm) {
     for (int k = threadIdx.x; k < kHid * 8; k += blockDim.x) {
         const int v = k >> 3, c = k & 7;
         sm[kSmW1 + k] = c < kFeat ? __bfloat162float(wb[kOffW1 + v * kFeat + c])
                                   : (c == kFeat ? __bfloat162float(wb[kOffB1 + v]) : 0.f);
-    }
-    for (int k = threadIdx.x; k < kHid * kHid; k += blockDim.x) {
-        const int v = k / kHid, u = k % kHid;
-        sm[kSmW2T + k] = __bfloat162float(wb[kOffW2 + u * kHid + v]);
     }
     for (int k = threadIdx.x; k < kHid; k += blockDim.x) {
         sm[kSmB2 + k] = __bfloat162float(wb[kOffB2 + k]);
@@ -88,11 +87,20 @@ __device__ __forceinline__ void load_mlp(float *sm, const __nv_bfloat16 *wb, con
     if (threadIdx.x < 2 * kFeat) sm[kSmNorm + threadIdx.x] = norm[threadIdx.x];
 }
 
-// The same plus W2's B fragments for mlp_forward_warp. Fragment (kt, nt) of
-// lane l = 4g + q: b0 = W2[n][k0], W2[n][k0+1] and b1 = W2[n][k0+8],
-// W2[n][k0+9] with n = 8 nt + g, k0 = 16 kt + 2q (B[k][n] = W2[n][k]).
+__device__ __forceinline__ void load_mlp(float *sm, const __nv_bfloat16 *wb, const float *norm) {
+    load_mlp_small(sm, wb, norm);
+    for (int k = threadIdx.x; k < kHid * kHid; k += blockDim.x) {
+        const int v = k / kHid, u = k % kHid;
+        sm[kSmW2T + k] = __bfloat162float(wb[kOffW2 + u * kHid + v]);
+    }
+}
+
+// The part both passes read plus W2's B fragments for mlp_forward_warp.
+// Fragment (kt, nt) of lane l = 4g + q: b0 = W2[n][k0], W2[n][k0+1] and b1 =
+// W2[n][k0+8], W2[n][k0+9] with n = 8 nt + g, k0 = 16 kt + 2q (B[k][n] =
+// W2[n][k]).
 __device__ __forceinline__ void load_mlp_tc(float *sm, const __nv_bfloat16 *wb, const float *norm) {
-    load_mlp(sm, wb, norm);
+    load_mlp_small(sm, wb, norm);
     uint32_t *fr = (uint32_t *)(sm + kSmW2Frag);
     for (int k = threadIdx.x; k < 4 * 8 * 32; k += blockDim.x) {
         const int lane = k & 31, nt = (k >> 5) & 7, kt = k >> 8;
