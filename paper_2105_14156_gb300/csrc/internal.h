@@ -518,13 +518,17 @@ inline void destroy_streams(smash_handle *h) {
     h->fork_ev = nullptr;
 }
 
-// Order in which the bins of a phase are launched: most products first, so
-// that the largest kernels start first and the small ones fill their tails.
+// Order in which the bins of a phase are launched (round-robin over the
+// streams): largest tables first (the dense and spill bins, then the shared
+// bins from the largest down), so that the kernels whose blocks each hold a
+// long row start early and the many short blocks of the small bins fill the
+// end, rather than a few long blocks running alone at the end of the phase.
 inline int bin_order(const long long *sums, int *order) {
     int n = 0;
     for (int b = 1; b < kNumBins; ++b) order[n++] = b;
+    auto key = [&](int b) { return sums[16 + b] > 0 ? (long long)b : -1ll; };
     for (int x = 1; x < n; ++x)
-        for (int y = x; y > 0 && sums[16 + order[y]] > sums[16 + order[y - 1]]; --y) {
+        for (int y = x; y > 0 && key(order[y]) > key(order[y - 1]); --y) {
             const int t = order[y];
             order[y] = order[y - 1];
             order[y - 1] = t;
